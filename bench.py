@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""CLAMP throughput benchmark: voxel-looks/s per MACE iteration on one GB300.
+
+Workload (default ``cfg2``): 128x128x64 complex64 volume, L = 16 looks, column-
+surface scene (reflectance U[0.2, 1]) with circular speckle per look, pupil
+radius 0.4 Nyquist, periodic Hann range window, 15 dB SNR, residual CNN prior
+(5 layers, 3x3x3, 32 channels, FP32).  A step is one CLAMP iteration (Alg. 2
+loop body): the forward FFT passes of all looks, the exact line search, the
+prior agent, and the fused prox + Mann pass.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl clamp|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+(the only reference there is) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-looks/s per MACE iter; time to CE residual 1e-3, warm-start vs plain init"
+UNIT = "voxel-looks/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="clamp", choices=["clamp", "reference"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2"])
+    ap.add_argument("--e2e-calls", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(wl):
+    return {
+        "workload": f"{wl.nx}x{wl.ny}x{wl.nz} complex64, L={wl.looks} looks, column-surface speckle scene, "
+                    f"pupil R=0.4 Nyquist, Hann range window, 15 dB SNR, residual CNN prior "
+                    f"{len(wl.denoiser.get('weights', []))} layers x 3x3x3 x {wl.denoiser.get('channels')} ch FP32"
+        if wl.denoiser["kind"] == "cnn" else f"{wl.nx}x{wl.ny}x{wl.nz} complex64, L={wl.looks}, Gaussian prior",
+        "nx": wl.nx, "ny": wl.ny, "nz": wl.nz, "looks": wl.looks,
+        "voxel_looks_per_step": wl.nx * wl.ny * wl.nz * wl.looks,
+        "prox_var": wl.prox_var, "noise_var": round(wl.noise_var, 8),
+        "l2": "inputs larger than L2: per-iteration working set ~0.85 GB (y, mu, r, w, scratch) vs 129 MB L2",
+    }
+
+
+# ---------------------------------------------------------------------- oracle (CPU) sample
+
+def oracle_sample(wl, y64, looks_sample: int, slab: int, seed: int = 0):
+    """Times the FP64 oracle on a bounded sample of one CLAMP iteration: the forward
+    agents of ``looks_sample`` looks on the full volume, the prior agent on a
+    ``slab``-deep z-slab (with its receptive-field halo) and the MACE step on the full
+    volume, and scales each part to the whole iteration.  Returns (seconds per
+    iteration estimate, description)."""
+    import numpy as np
+    from oracle import clamp_oracle as O
+    a = O.aperture(wl.pupil, wl.window)
+    st = O.init_state(y64, a)
+    alpha = O.alpha_of(a)
+    t0 = time.perf_counter()
+    for l in range(looks_sample):
+        O.forward_agent(st.mu[l], st.r[l], st.w[l], y64[l], a, wl.noise_var, wl.prox_var, alpha, O.beta_k(1))
+    t_look = (time.perf_counter() - t0) / looks_sample
+    halo = len(wl.denoiser["weights"]) if wl.denoiser["kind"] == "cnn" else 1
+    z0 = wl.nz // 2 - slab // 2
+    crop = st.w[wl.looks, max(0, z0 - halo):z0 + slab + halo]
+    t0 = time.perf_counter()
+    O.apply_prior(crop, wl.denoiser)
+    t_prior = (time.perf_counter() - t0) * wl.nz / slab
+    ups = O.consensus_weights(wl.looks)
+    t0 = time.perf_counter()
+    O.mace_update(st.r, st.w, ups, 0.5)
+    O.convergence_error(st.r, st.w, ups)
+    t_mace = time.perf_counter() - t0
+    t_iter = wl.looks * t_look + t_prior + t_mace
+    desc = (f"{looks_sample} of {wl.looks} looks' forward agents on the full volume, prior agent on a "
+            f"{slab}-of-{wl.nz} z-slab (+{halo} halo), MACE step on the full volume; scaled to one iteration")
+    return t_iter, desc
+
+
+def oracle_threads() -> int:
+    # numpy's FFT is single-threaded; its BLAS (used by the CNN prior) uses every core by default
+    return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.send_signal(signal.SIGTERM)
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, rank 0 only.  Each step runs one
+    work unit of a CLAMP iteration, round robin: one look's forward agent on the full
+    volume, the prior agent on one z-slab (+ halo), or the MACE step; the iteration time
+    is estimated as sum over unit kinds of (mean unit time x units per iteration)."""
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import clamp_oracle as O
+    from paper_2406_13651_gb300 import inputs as I
+    wl = I.make_workload(args.workload, seed=1)
+    a = O.aperture(wl.pupil, wl.window)
+    y64 = O.simulate_data(wl.r_true, wl.speckle, wl.noise, a, wl.noise_var).astype(np.complex64)
+    y64 = y64.astype(np.complex128)
+    del wl.speckle, wl.noise
+    st = O.init_state(y64, a)
+    alpha = O.alpha_of(a)
+    ups = O.consensus_weights(wl.looks)
+    halo = len(wl.denoiser["weights"]) if wl.denoiser["kind"] == "cnn" else 1
+    slab = 2
+    kinds = ["agent", "prior", "mace"]
+    times = {k: [] for k in kinds}
+
+    def unit(i):
+        kind = kinds[i % 3]
+        t0 = time.perf_counter()
+        if kind == "agent":
+            l = (i // 3) % wl.looks
+            O.forward_agent(st.mu[l], st.r[l], st.w[l], y64[l], a, wl.noise_var, wl.prox_var, alpha, O.beta_k(1))
+        elif kind == "prior":
+            z0 = ((i // 3) * slab) % wl.nz
+            lo, hi = max(0, z0 - halo), min(wl.nz, z0 + slab + halo)
+            O.apply_prior(st.w[wl.looks, lo:hi], wl.denoiser)
+        else:
+            O.mace_update(st.r, st.w, ups, 0.5)
+            O.convergence_error(st.r, st.w, ups)
+        return kind, time.perf_counter() - t0
+
+    for i in range(max(args.warmup, 0) and 3):
+        unit(i)
+    t_all = 0.0
+    for i in range(args.steps):
+        kind, t = unit(i)
+        times[kind].append(t)
+        t_all += t
+    mean = {k: (sum(v) / len(v) if v else 0.0) for k, v in times.items()}
+    t_iter = wl.looks * mean["agent"] + (wl.nz / slab) * mean["prior"] + mean["mace"]
+    value = wl.nx * wl.ny * wl.nz * wl.looks / t_iter
+    cores = oracle_threads()
+    desc = (f"each step one unit of an iteration, round robin: one look's forward agent on the full "
+            f"{wl.nx}x{wl.ny}x{wl.nz} volume, the prior agent on a {slab}-plane z-slab (+{halo} halo), or the "
+            f"MACE step; iteration time = {wl.looks} x agent + {wl.nz // slab} x prior slab + MACE")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_all / max(args.steps, 1) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_13651_gb300 import build as B
+    from paper_2406_13651_gb300 import clamp as C
+    from paper_2406_13651_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    C.load()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    # ---- inputs: seeded scene and draws on the host, data simulated on the device
+    wl = I.make_workload(args.workload, seed=1 + rank)
+    L, n = wl.looks, wl.nx * wl.ny * wl.nz
+    p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var)
+    pupil = torch.from_numpy(wl.pupil).to(dev)
+    window = torch.from_numpy(wl.window).to(dev)
+    r_true = torch.from_numpy(wl.r_true.astype(np.float32)).to(dev)
+    spk = torch.from_numpy(wl.speckle.astype(np.complex64)).to(dev)
+    eta = torch.from_numpy(wl.noise.astype(np.complex64)).to(dev)
+    y = C.simulate(p, r_true, spk, eta, pupil, window)
+    del spk, eta
+    y_host = None
+    den = C.Denoiser.from_desc(wl.denoiser)
+    mu, r, w = C.init(p, y, pupil, window)
+    wbar = torch.empty((wl.nz, wl.ny, wl.nx), dtype=torch.float32, device=dev)
+    ws = C.iterate_workspace(p, den)
+    K, W = args.steps, args.warmup
+    ce = torch.zeros(K + W, dtype=torch.float64, device=dev)
+
+    # ---- warm-up
+    C.iterate(p, 1, W, y, pupil, window, den, mu, r, w, wbar, ce_out=ce[:W], ws=ws)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K iterations, per-phase events
+    events = [torch.cuda.Event(enable_timing=True) for _ in range(4 * K)]
+    for e in events:  # torch creates the CUDA event lazily, on first record
+        e.record(stream)
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_start.record(stream)
+        C.iterate(p, W + 1, K, y, pupil, window, den, mu, r, w, wbar, ce_out=ce[W:], ws=ws, events=events)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    agent = sum(events[4 * i].elapsed_time(events[4 * i + 1]) for i in range(K)) / K / 1e3
+    prior = sum(events[4 * i + 1].elapsed_time(events[4 * i + 2]) for i in range(K)) / K / 1e3
+    passc = sum(events[4 * i + 2].elapsed_time(events[4 * i + 3]) for i in range(K)) / K / 1e3
+    t_max = elapsed
+    if world > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ce_last = float(ce[-1].item())
+    finite = bool(torch.isfinite(wbar).all().item())
+
+    # ---- end-to-end: clamp_reconstruct_host on pinned host buffers (copies inside the timed region)
+    e2e_iters = wl.iters
+    y_pin = torch.empty((L, wl.nz, wl.ny, wl.nx), dtype=torch.complex64, pin_memory=True)
+    y_pin.copy_(y.cpu())
+    pupil_pin = torch.from_numpy(wl.pupil).pin_memory()
+    window_pin = torch.from_numpy(wl.window).pin_memory()
+    rout_pin = torch.empty((wl.nz, wl.ny, wl.nx), dtype=torch.float32, pin_memory=True)
+    pe = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var, max_iters=e2e_iters)
+    lib = C.load()
+    import ctypes
+
+    def e2e_call():
+        rep = C.Report(0, 0, 0.0, 0.0, None, None)
+        C._check(lib.clamp_reconstruct_host(ctypes.byref(pe), y_pin.data_ptr(), pupil_pin.data_ptr(),
+                                            window_pin.data_ptr(), den.handle, None, rout_pin.data_ptr(),
+                                            ctypes.byref(rep), stream.cuda_stream), "clamp_reconstruct_host")
+        return rep
+
+    e2e_call()  # warm-up (allocates the device cache)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_calls):
+        e2e_call()
+    torch.cuda.synchronize()
+    e2e_t = (time.perf_counter() - t0) / args.e2e_calls
+    if world > 1:
+        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e_value = n * L * e2e_iters * world / e2e_t
+    h2d = L * n * 8 + wl.nx * wl.ny * 4 + wl.nz * 4
+    d2h = n * 4 + 2 * 8 * e2e_iters
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    import json as _json
+    peaks = {}
+    pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk):
+        peaks = _json.load(open(pk))
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12   # TFLOP/s at the 2070 MHz max SM clock
+
+    value = n * L * K * world / t_max
+    # prior agent: residual CNN FLOPs per voxel (2 per MAC)
+    if wl.denoiser["kind"] == "cnn":
+        ch = wl.denoiser["channels"]
+        nl = len(wl.denoiser["weights"])
+        macs = 27 * (ch + (nl - 2) * ch * ch + ch)
+        flops = 2.0 * macs * n
+        cnn_tflops = flops / prior / 1e12
+        roofline = {"bound": "alu", "kernel": "k_conv3_f32 (all layers of the prior agent)",
+                    "achieved": cnn_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": cnn_tflops / fp32_peak, "traffic": None,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                    "algorithmic": f"{macs} MAC/voxel x {n} voxels per launch set"}
+    else:
+        roofline = None
+    # forward-agent FFT + prox + Mann path: 136 B per voxel-look (two HBM passes per 3D FFT)
+    agent_bytes = 136.0 * n * L
+    agent_gbs = agent_bytes / (agent + passc) / 1e9
+    roof_agent = {"bound": "hbm", "kernel": "forward-agent FFT passes + line search + fused prox/Mann pass",
+                  "achieved": agent_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": agent_gbs / hbm_peak,
+                  "traffic": None, "peak_source": hbm_src,
+                  "algorithmic": "136 B per voxel-look per iteration (two HBM passes per 3D FFT)"}
+    if roofline is None:
+        roofline = roof_agent
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        from oracle import clamp_oracle as O
+        a = O.aperture(wl.pupil, wl.window)
+        y64 = y.cpu().numpy().astype(np.complex128)
+        t_it, desc = oracle_sample(wl, y64, 2, max(4, wl.nz // 8))
+        cpu = {"value": n * L / t_it, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": desc}
+
+    launches_per_iter = 5 + 1 + (len(wl.denoiser.get("weights", [])) if wl.denoiser["kind"] == "cnn" else 1) + 1 + 1
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": workload_desc(wl),
+        "phases_ms": {"forward_agents_fft_and_line_search": agent * 1e3, "prior_agent": prior * 1e3,
+                      "prox_mann_pass": passc * 1e3},
+        "roofline": roofline, "roofline_agent": roof_agent,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "step": f"one clamp_reconstruct_host call: upload y, init, {e2e_iters} iterations, download r*"},
+        "gpu_launches": launches_per_iter * K,
+        "clocks": clk.summary(),
+        "ce_residual_last": ce_last, "finite": finite,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

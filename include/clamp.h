@@ -1,0 +1,199 @@
+/*
+ * clamp.h -- C ABI of the GB300 (sm_103a) CLAMP hot path.
+ *
+ * CLAMP (Allen, Rabb, Buzzard, Bouman, "CLAMP: Majorized Plug-and-Play for
+ * Coherent 3D Lidar Imaging", IEEE TCI 11, 2025) reconstructs a real
+ * reflectance r from L looks y_l = A g_l + eta_l, A = D(a) F (Eq. (A)), by a
+ * MACE iteration (Alg. 2) over L majorized forward agents and one prior agent.
+ *
+ * Conventions for every entry point
+ *  - Volumes are [nz][ny][nx], x fastest.  Complex arrays are interleaved
+ *    (re, im) float32 pairs.  Frequency-domain arrays (y, pupil, window) are in
+ *    unshifted FFT order, DC at index 0.  Per-look arrays are [L][n] with
+ *    n = nx*ny*nz, look-major.
+ *  - Axis lengths must be powers of two in [8, 256]; nx must be a multiple of 16.
+ *  - Unless a function says "host", every array pointer is caller-owned DEVICE
+ *    memory on the current CUDA device; the library never frees it.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    stream-ordered and asynchronous unless documented otherwise.
+ *  - Scratch: `ws` / `ws_bytes` is a caller-owned device buffer, 256-byte
+ *    aligned, of at least the size the matching *_workspace_size query
+ *    returns; the library keeps nothing in it between calls unless stated.
+ *  - Errors: every call returns a clamp_status and never aborts; on failure
+ *    clamp_last_error() gives a message (thread-local).  Invalid arguments are
+ *    rejected before any launch.
+ */
+#ifndef CLAMP_H
+#define CLAMP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum clamp_status {
+  CLAMP_OK = 0,
+  CLAMP_EINVAL = 1,      /* invalid argument (shape, pointer, parameter) */
+  CLAMP_ENOMEM = 2,      /* workspace too small or device allocation failed */
+  CLAMP_ECUDA = 3,       /* CUDA runtime error */
+  CLAMP_ENOTCONV = 4,    /* iteration did not reach the tolerance */
+  CLAMP_ETIMEOUT = 5,    /* a bounded device wait gave up */
+  CLAMP_ENONFINITE = 6,  /* a non-finite value appeared in the state */
+  CLAMP_EUNSUPPORTED = 7 /* size or option not supported by this build */
+} clamp_status;
+
+/* Flags for clamp_params.flags. */
+#define CLAMP_FLAG_MU_INIT_NO_ALPHA 0x1 /* mu_l = A^H y_l (Alg. 2) instead of A^H y_l / alpha (Sec. IV-A) */
+
+/* Problem and iteration parameters (Sec. II-B, Sec. III, Sec. IV-A). */
+typedef struct clamp_params {
+  int32_t nx, ny, nz;   /* volume shape */
+  int32_t looks;        /* L >= 1 forward agents */
+  float noise_var;      /* sigma_w^2 > 0: data-noise variance (Eqs. forward-model, mu-objective) */
+  float prox_var;       /* sigma^2 > 0: forward-agent proximal parameter (Eq. prox) */
+  float rho;            /* Mann parameter in (0, 1) (Eq. mann); the paper uses 0.5 */
+  float prior_weight;   /* upsilon_{L+1} in (0, 1); each look gets (1 - prior_weight)/L (Sec. III-A) */
+  int32_t max_iters;    /* iterations run by clamp_reconstruct */
+  int32_t k0;           /* iterations already done (resume); beta uses k = k0 + 1, k0 + 2, ... */
+  int32_t flags;        /* CLAMP_FLAG_* */
+  int32_t check_every;  /* clamp_reconstruct reads the residual back every this many iterations (tol > 0) */
+  double tol;           /* stop when the convergence error <= tol (0 = run max_iters) */
+} clamp_params;
+
+/* Per-run report of clamp_reconstruct (host memory). */
+typedef struct clamp_report {
+  int32_t iters;        /* iterations run */
+  int32_t converged;    /* 1 if the convergence error reached tol */
+  double ce_residual;   /* last convergence error (Eq. mace-convergence-error) */
+  double mu_residual;   /* last mu-residual, floored form (Eq. residual) */
+  double* ce_hist;      /* optional host array [max_iters], filled when non-NULL */
+  double* mu_hist;      /* optional host array [max_iters], filled when non-NULL */
+} clamp_report;
+
+/* Opaque prior-agent handle (owns its device weights). */
+typedef struct clamp_denoiser clamp_denoiser;
+
+#define CLAMP_DENOISER_FP32 0
+#define CLAMP_DENOISER_BF16 1
+
+const char* clamp_last_error(void);
+const char* clamp_version(void);
+
+/* 1 if `n` is a supported axis length. */
+int32_t clamp_supported_length(int32_t n);
+
+/* Validates a parameter block; CLAMP_OK or CLAMP_EINVAL / CLAMP_EUNSUPPORTED. */
+clamp_status clamp_check_params(const clamp_params* p);
+
+/* Scratch bytes needed by clamp_init, clamp_forward_prox and clamp_mace_step for `p`
+ * (about 24 bytes per voxel-look plus reduction partials).  0 if `p` is invalid. */
+size_t clamp_workspace_size(const clamp_params* p);
+
+/* Scratch bytes clamp_reconstruct needs: state (mu, r, w), the forward-agent
+ * scratch and the denoiser's scratch.  0 if invalid. */
+size_t clamp_reconstruct_workspace_size(const clamp_params* p, const clamp_denoiser* den);
+
+/* Orthonormal 3D DFT F (or F^H when inverse != 0) of `batch` volumes (Eq. (A):
+ * F is the orthonormal DFT, scale 1/sqrt(n) each way).  in, out: complex
+ * [batch][n]; in == out is allowed.  Uses out as its only scratch. */
+clamp_status clamp_fft3(int32_t nx, int32_t ny, int32_t nz, int32_t batch,
+                        const float* in, float* out, int32_t inverse, void* stream);
+
+/* Data simulation (Eqs. forward-model, g-given-r): y_l = a .* F(sqrt(r) .* z_l) + sqrt(sigma_w^2) eta_l
+ * with a = window[kz] * pupil[ky][kx].  r: float [n]; speckle z, noise eta: complex [L][n]
+ * (CN(0,1) draws supplied by the caller); y: complex [L][n] out.  sigma_w^2 = p->noise_var. */
+clamp_status clamp_simulate(const clamp_params* p, const float* r, const float* speckle,
+                            const float* noise, const float* pupil, const float* window,
+                            float* y, void* stream);
+
+/* Initialisation of Alg. 2 as in Sec. IV-A: r0 = (1/L) sum_l |A^H y_l|^2 floored at
+ * 1e-12 max(r0) (or r_init when non-NULL), r_j = w_j = r0 for j = 1..L+1, and
+ * mu_l = A^H y_l / alpha with alpha = mean(a^2).
+ * y: complex [L][n]; pupil [ny][nx]; window [nz]; r_init: float [n] or NULL;
+ * mu: complex [L][n] out; r, w: float [L+1][n] out (row L is the prior agent's). */
+clamp_status clamp_init(const clamp_params* p, const float* y, const float* pupil,
+                        const float* window, const float* r_init, float* mu, float* r, float* w,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/* All L majorized forward agents for CLAMP iteration k >= 1 (Alg. 2, steps 5-9):
+ * c_l = sigma_w^2 r_l / (alpha r_l + sigma_w^2); d = -grad h(mu_l) (Eq. h-gradient);
+ * exact line search gamma (Eq. mu-update); mu_l += gamma d; r_l <- the App. A
+ * quadratic-surrogate prox of w_l with beta = 1 + 2/ln(k+1), anchored at the old r_l.
+ * mu: complex [L][n] in/out; r: float [>= L][n] in/out (rows 0..L-1 used);
+ * w: float [>= L][n] in.  mu_residual: optional DEVICE double out, the look-averaged
+ * floored mu-residual (Eq. residual) at the incoming mu. */
+clamp_status clamp_forward_prox(const clamp_params* p, int32_t k, const float* y,
+                                const float* pupil, const float* window, float* mu, float* r,
+                                const float* w, double* mu_residual, void* ws, size_t ws_bytes,
+                                void* stream);
+
+/* Prior agent r_prior = H(w_prior) (Alg. 2, step 11).  Both float [n]. */
+clamp_status clamp_denoise(const clamp_denoiser* den, const float* w_prior, float* r_prior,
+                           int32_t nx, int32_t ny, int32_t nz, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/* MACE step (Alg. 2, steps 12-14; Eq. mann): wbar_old = sum_j ups_j w_j,
+ * x = 2r - w, w <- w + 2 rho (G(x) - r), wbar = sum_j ups_j w_j (new w).
+ * r: float [L+1][n] agent outputs; w: float [L+1][n] in/out; wbar: float [n] out;
+ * ce_residual: optional DEVICE double out, the convergence error
+ * ||r - G(w)|| / ||G(w)|| (Eq. mace-convergence-error) of the incoming w. */
+clamp_status clamp_mace_step(const clamp_params* p, const float* r, float* w, float* wbar,
+                             double* ce_residual, void* ws, size_t ws_bytes, void* stream);
+
+/* Prior agents. */
+clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser** out);
+/* Residual CNN H(x) = x + CNN(x), 3x3x3 convs, zero padding; layer i maps
+ * c_in -> c_out (1 -> C -> ... -> C -> 1), ReLU after every layer but the last.
+ * weights_host: all layers' [c_out][c_in][3][3][3] float32 concatenated;
+ * biases_host: all layers' [c_out] concatenated.  dtype: CLAMP_DENOISER_FP32 or _BF16. */
+clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channels, int32_t dtype,
+                                       const float* weights_host, const float* biases_host,
+                                       clamp_denoiser** out);
+void clamp_denoiser_destroy(clamp_denoiser* den);
+size_t clamp_denoise_workspace_size(const clamp_denoiser* den, int32_t nx, int32_t ny, int32_t nz);
+
+/* Scratch bytes clamp_iterate needs (forward-agent scratch plus the denoiser's). */
+size_t clamp_iterate_workspace_size(const clamp_params* p, const clamp_denoiser* den);
+
+/* Runs `iters` CLAMP iterations k = k_first, ..., k_first + iters - 1 (the loop body of
+ * Alg. 2: all forward agents, the prior agent on w_{L+1}, the MACE step) on a
+ * caller-held state, so a run can be resumed from {mu, r, w, k}.
+ * mu: complex [L][n], r, w: float [L+1][n] (in/out); wbar: float [n] out (sum_j ups_j w_j
+ * after the last step, the Alg. 2 output).  ce_out, mu_out: optional DEVICE double
+ * arrays [iters] receiving the convergence error and mu-residual of each iteration.
+ * events: optional array of 4 * iters cudaEvent_t handles recorded on `stream` per
+ * iteration: before the forward agents, after their line search, after the prior
+ * agent, after the MACE pass (for timing).  Stream-ordered, no host synchronisation
+ * after argument checks. */
+clamp_status clamp_iterate(const clamp_params* p, int32_t k_first, int32_t iters, const float* y,
+                           const float* pupil, const float* window, const clamp_denoiser* den,
+                           float* mu, float* r, float* w, float* wbar, double* ce_out,
+                           double* mu_out, void* ws, size_t ws_bytes, void* const* events,
+                           void* stream);
+
+/* Full CLAMP reconstruction (Alg. 2) on device buffers: init, then up to
+ * p->max_iters iterations of forward agents + prior agent + MACE step, stopping
+ * early when tol > 0 and the convergence error <= tol (checked every
+ * p->check_every iterations).  r_out: float [n] <- r* = wbar (Alg. 2 output).
+ * ws may be NULL (the call then allocates and frees its scratch).  Synchronises
+ * the stream when report != NULL or tol > 0. */
+clamp_status clamp_reconstruct(const clamp_params* p, const float* y, const float* pupil,
+                               const float* window, const clamp_denoiser* den,
+                               const float* r_init, float* r_out, clamp_report* report,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/* Same on HOST buffers (pageable or pinned): copies y, pupil, window and r_init to
+ * the device, reconstructs, copies r_out back and synchronises.  Device scratch is
+ * kept in a per-device cache between calls (clamp_release_cache frees it). */
+clamp_status clamp_reconstruct_host(const clamp_params* p, const float* y_host,
+                                    const float* pupil_host, const float* window_host,
+                                    const clamp_denoiser* den, const float* r_init_host,
+                                    float* r_out_host, clamp_report* report, void* stream);
+void clamp_release_cache(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLAMP_H */

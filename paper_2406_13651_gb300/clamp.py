@@ -1,0 +1,318 @@
+"""Thin Python binding of the CLAMP C ABI (``include/clamp.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Arrays are torch tensors on the current CUDA device (complex data as
+``torch.complex64`` or trailing-dimension-2 ``float32``), passed by pointer;
+streams are torch streams.  Loading fails loudly when the library has not been
+built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libclamp.so")
+
+CLAMP_OK = 0
+STATUS = {0: "CLAMP_OK", 1: "CLAMP_EINVAL", 2: "CLAMP_ENOMEM", 3: "CLAMP_ECUDA", 4: "CLAMP_ENOTCONV",
+          5: "CLAMP_ETIMEOUT", 6: "CLAMP_ENONFINITE", 7: "CLAMP_EUNSUPPORTED"}
+FLAG_MU_INIT_NO_ALPHA = 0x1
+DENOISER_FP32 = 0
+DENOISER_BF16 = 1
+
+EXPORTS = [
+    "clamp_last_error", "clamp_version", "clamp_supported_length", "clamp_check_params",
+    "clamp_workspace_size", "clamp_reconstruct_workspace_size", "clamp_fft3", "clamp_simulate",
+    "clamp_init", "clamp_forward_prox", "clamp_denoise", "clamp_mace_step",
+    "clamp_denoiser_create_gauss", "clamp_denoiser_create_cnn", "clamp_denoiser_destroy",
+    "clamp_denoise_workspace_size", "clamp_reconstruct", "clamp_reconstruct_host", "clamp_release_cache",
+    "clamp_iterate", "clamp_iterate_workspace_size",
+]
+
+
+class ClampError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    """Mirror of ``clamp_params``."""
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("looks", ctypes.c_int32), ("noise_var", ctypes.c_float), ("prox_var", ctypes.c_float),
+                ("rho", ctypes.c_float), ("prior_weight", ctypes.c_float), ("max_iters", ctypes.c_int32),
+                ("k0", ctypes.c_int32), ("flags", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("tol", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    """Mirror of ``clamp_report``."""
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32), ("ce_residual", ctypes.c_double),
+                ("mu_residual", ctypes.c_double), ("ce_hist", ctypes.POINTER(ctypes.c_double)),
+                ("mu_hist", ctypes.POINTER(ctypes.c_double))]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libclamp.so (raises if it is missing: build it with ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CLAMP CUDA library not built: {path} is missing "
+                           "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+    lib = ctypes.CDLL(path)
+    P, S, V, I, D = ctypes.c_void_p, ctypes.c_size_t, None, ctypes.c_int32, ctypes.c_double
+    PP = ctypes.POINTER(Params)
+    sig = {
+        "clamp_last_error": (ctypes.c_char_p, []),
+        "clamp_version": (ctypes.c_char_p, []),
+        "clamp_supported_length": (I, [I]),
+        "clamp_check_params": (I, [PP]),
+        "clamp_workspace_size": (S, [PP]),
+        "clamp_reconstruct_workspace_size": (S, [PP, P]),
+        "clamp_fft3": (I, [I, I, I, I, P, P, I, P]),
+        "clamp_simulate": (I, [PP, P, P, P, P, P, P, P]),
+        "clamp_init": (I, [PP, P, P, P, P, P, P, P, P, S, P]),
+        "clamp_forward_prox": (I, [PP, I, P, P, P, P, P, P, P, P, S, P]),
+        "clamp_denoise": (I, [P, P, P, I, I, I, P, S, P]),
+        "clamp_mace_step": (I, [PP, P, P, P, P, P, S, P]),
+        "clamp_denoiser_create_gauss": (I, [ctypes.c_float, ctypes.POINTER(P)]),
+        "clamp_denoiser_create_cnn": (I, [I, I, I, P, P, ctypes.POINTER(P)]),
+        "clamp_denoiser_destroy": (V, [P]),
+        "clamp_denoise_workspace_size": (S, [P, I, I, I]),
+        "clamp_reconstruct": (I, [PP, P, P, P, P, P, P, ctypes.POINTER(Report), P, S, P]),
+        "clamp_reconstruct_host": (I, [PP, P, P, P, P, P, P, ctypes.POINTER(Report), P]),
+        "clamp_release_cache": (V, []),
+        "clamp_iterate_workspace_size": (S, [PP, P]),
+        "clamp_iterate": (I, [PP, I, I, P, P, P, P, P, P, P, P, P, P, P, S, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int, where: str):
+    if status != CLAMP_OK:
+        raise ClampError(status, where, load().clamp_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def make_params(nx, ny, nz, looks, noise_var, prox_var, rho=0.5, prior_weight=0.5, max_iters=0, k0=0,
+                flags=0, check_every=10, tol=0.0) -> Params:
+    return Params(nx, ny, nz, looks, noise_var, prox_var, rho, prior_weight, max_iters, k0, flags,
+                  check_every, tol)
+
+
+class Denoiser:
+    """Owns a ``clamp_denoiser`` handle (created on the current CUDA device)."""
+
+    def __init__(self, handle: int, desc: dict):
+        self.handle = handle
+        self.desc = desc
+
+    @classmethod
+    def gauss(cls, sigma: float = 0.8) -> "Denoiser":
+        h = ctypes.c_void_p()
+        _check(load().clamp_denoiser_create_gauss(sigma, ctypes.byref(h)), "clamp_denoiser_create_gauss")
+        return cls(h.value, {"kind": "gauss", "sigma": sigma})
+
+    @classmethod
+    def cnn(cls, weights, biases, dtype: str = "fp32") -> "Denoiser":
+        layers = len(weights)
+        channels = int(weights[0].shape[0])
+        w = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in weights]))
+        b = np.ascontiguousarray(np.concatenate([np.asarray(x, np.float32).ravel() for x in biases]))
+        h = ctypes.c_void_p()
+        dt = DENOISER_BF16 if dtype == "bf16" else DENOISER_FP32
+        _check(load().clamp_denoiser_create_cnn(layers, channels, dt, w.ctypes.data, b.ctypes.data,
+                                                ctypes.byref(h)), "clamp_denoiser_create_cnn")
+        return cls(h.value, {"kind": "cnn", "layers": layers, "channels": channels, "dtype": dtype})
+
+    @classmethod
+    def from_desc(cls, desc: dict) -> "Denoiser":
+        if desc["kind"] == "gauss":
+            return cls.gauss(desc["sigma"])
+        return cls.cnn(desc["weights"], desc["biases"], desc.get("dtype", "fp32"))
+
+    def workspace_size(self, nx, ny, nz) -> int:
+        return load().clamp_denoise_workspace_size(self.handle, nx, ny, nz)
+
+    def close(self):
+        if self.handle:
+            load().clamp_denoiser_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ device-buffer calls
+
+def _ws(nbytes: int):
+    import torch
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device="cuda")
+
+
+def workspace(p: Params):
+    n = load().clamp_workspace_size(ctypes.byref(p))
+    if n == 0:
+        _check(load().clamp_check_params(ctypes.byref(p)), "clamp_workspace_size")
+    return _ws(n)
+
+
+def fft3(x, inverse: bool = False, out=None, stream=None):
+    """Orthonormal 3D DFT of complex64 x [..., nz, ny, nx] (batched over leading dims)."""
+    import torch
+    assert x.dtype == torch.complex64 and x.is_contiguous()
+    nz, ny, nx = x.shape[-3:]
+    batch = x.numel() // (nx * ny * nz)
+    out = torch.empty_like(x) if out is None else out
+    _check(load().clamp_fft3(nx, ny, nz, batch, _ptr(x), _ptr(out), 1 if inverse else 0, _stream(stream)),
+           "clamp_fft3")
+    return out
+
+
+def simulate(p: Params, r, speckle, noise, pupil, window, stream=None):
+    import torch
+    y = torch.empty_like(speckle)
+    _check(load().clamp_simulate(ctypes.byref(p), _ptr(r), _ptr(speckle), _ptr(noise), _ptr(pupil), _ptr(window),
+                                 _ptr(y), _stream(stream)), "clamp_simulate")
+    return y
+
+
+def init(p: Params, y, pupil, window, r_init=None, ws=None, stream=None):
+    """Returns (mu [L][n] complex64, r [L+1][n], w [L+1][n])."""
+    import torch
+    n = p.nx * p.ny * p.nz
+    mu = torch.empty((p.looks, p.nz, p.ny, p.nx), dtype=torch.complex64, device=y.device)
+    r = torch.empty((p.looks + 1, p.nz, p.ny, p.nx), dtype=torch.float32, device=y.device)
+    w = torch.empty_like(r)
+    ws = workspace(p) if ws is None else ws
+    _check(load().clamp_init(ctypes.byref(p), _ptr(y), _ptr(pupil), _ptr(window), _ptr(r_init), _ptr(mu), _ptr(r),
+                             _ptr(w), _ptr(ws), ws.numel(), _stream(stream)), "clamp_init")
+    return mu, r, w
+
+
+def forward_prox(p: Params, k: int, y, pupil, window, mu, r, w, mu_residual=None, ws=None, stream=None):
+    ws = workspace(p) if ws is None else ws
+    _check(load().clamp_forward_prox(ctypes.byref(p), k, _ptr(y), _ptr(pupil), _ptr(window), _ptr(mu), _ptr(r),
+                                     _ptr(w), _ptr(mu_residual), _ptr(ws), ws.numel(), _stream(stream)),
+           "clamp_forward_prox")
+
+
+def denoise(den: Denoiser, w_prior, r_prior, ws=None, stream=None):
+    nz, ny, nx = w_prior.shape[-3:]
+    need = den.workspace_size(nx, ny, nz)
+    if ws is None and need:
+        ws = _ws(need)
+    _check(load().clamp_denoise(den.handle, _ptr(w_prior), _ptr(r_prior), nx, ny, nz, _ptr(ws),
+                                ws.numel() if ws is not None else 0, _stream(stream)), "clamp_denoise")
+
+
+def mace_step(p: Params, r, w, wbar, ce_residual=None, ws=None, stream=None):
+    ws = workspace(p) if ws is None else ws
+    _check(load().clamp_mace_step(ctypes.byref(p), _ptr(r), _ptr(w), _ptr(wbar), _ptr(ce_residual), _ptr(ws),
+                                  ws.numel(), _stream(stream)), "clamp_mace_step")
+
+
+@dataclass
+class Result:
+    r: object
+    iters: int
+    converged: bool
+    ce_hist: np.ndarray
+    mu_hist: np.ndarray
+
+
+def iterate_workspace(p: Params, den: Denoiser):
+    n = load().clamp_iterate_workspace_size(ctypes.byref(p), den.handle)
+    if n == 0:
+        _check(load().clamp_check_params(ctypes.byref(p)), "clamp_iterate_workspace_size")
+    return _ws(n)
+
+
+def iterate(p: Params, k_first: int, iters: int, y, pupil, window, den: Denoiser, mu, r, w, wbar, ce_out=None,
+            mu_out=None, ws=None, events=None, stream=None):
+    """Runs ``iters`` CLAMP iterations on the caller-held state (mu, r, w); wbar receives the output.
+    ``events``: optional list of 4*iters torch.cuda.Event (recorded per iteration around the phases)."""
+    ws = iterate_workspace(p, den) if ws is None else ws
+    ev = None
+    if events is not None:
+        if any(e.cuda_event == 0 for e in events):
+            raise ValueError("events must have been recorded once (torch creates CUDA events lazily)")
+        arr = (ctypes.c_void_p * len(events))(*[e.cuda_event for e in events])
+        ev = ctypes.cast(arr, ctypes.c_void_p)
+    _check(load().clamp_iterate(ctypes.byref(p), k_first, iters, _ptr(y), _ptr(pupil), _ptr(window), den.handle,
+                                _ptr(mu), _ptr(r), _ptr(w), _ptr(wbar), _ptr(ce_out), _ptr(mu_out), _ptr(ws),
+                                ws.numel(), ev, _stream(stream)), "clamp_iterate")
+
+
+def reconstruct_workspace(p: Params, den: Denoiser):
+    n = load().clamp_reconstruct_workspace_size(ctypes.byref(p), den.handle)
+    if n == 0:
+        _check(load().clamp_check_params(ctypes.byref(p)), "clamp_reconstruct_workspace_size")
+    return _ws(n)
+
+
+def reconstruct(p: Params, y, pupil, window, den: Denoiser, r_init=None, ws=None, r_out=None, report=True,
+                stream=None) -> Result:
+    import torch
+    r_out = torch.empty((p.nz, p.ny, p.nx), dtype=torch.float32, device=y.device) if r_out is None else r_out
+    rep = None
+    ce = np.zeros(max(p.max_iters, 1))
+    mh = np.zeros(max(p.max_iters, 1))
+    if report:
+        rep = Report(0, 0, 0.0, 0.0, ce.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     mh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    wsp, wsn = (_ptr(ws), ws.numel()) if ws is not None else (None, 0)
+    _check(load().clamp_reconstruct(ctypes.byref(p), _ptr(y), _ptr(pupil), _ptr(window), den.handle, _ptr(r_init),
+                                    _ptr(r_out), ctypes.byref(rep) if rep else None, wsp, wsn, _stream(stream)),
+           "clamp_reconstruct")
+    it = rep.iters if rep else p.max_iters
+    return Result(r_out, it, bool(rep.converged) if rep else False, ce[:it], mh[:it])
+
+
+def reconstruct_host(p: Params, y: np.ndarray, pupil: np.ndarray, window: np.ndarray, den: Denoiser,
+                     r_init: np.ndarray | None = None, r_out: np.ndarray | None = None, stream=None) -> Result:
+    """Host-buffer reconstruction: numpy in, numpy out (copies inside the call)."""
+    y = np.ascontiguousarray(y, dtype=np.complex64)
+    pupil = np.ascontiguousarray(pupil, dtype=np.float32)
+    window = np.ascontiguousarray(window, dtype=np.float32)
+    ri = None if r_init is None else np.ascontiguousarray(r_init, dtype=np.float32)
+    r_out = np.empty((p.nz, p.ny, p.nx), np.float32) if r_out is None else r_out
+    ce = np.zeros(max(p.max_iters, 1))
+    mh = np.zeros(max(p.max_iters, 1))
+    rep = Report(0, 0, 0.0, 0.0, ce.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                 mh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    _check(load().clamp_reconstruct_host(ctypes.byref(p), y.ctypes.data, pupil.ctypes.data, window.ctypes.data,
+                                         den.handle, None if ri is None else ri.ctypes.data, r_out.ctypes.data,
+                                         ctypes.byref(rep), _stream(stream)), "clamp_reconstruct_host")
+    return Result(r_out, rep.iters, bool(rep.converged), ce[:rep.iters], mh[:rep.iters])

@@ -1,0 +1,608 @@
+// clamp_api.cu -- the C ABI (include/clamp.h): argument checks, workspace
+// layout, per-device set-up and the CLAMP iteration driver (Alg. 2).
+#include "../../include/clamp.h"
+#include "clamp_kernels.cuh"
+#include "denoise.cuh"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+using namespace clamp;
+
+// ---------------------------------------------------------------- errors
+
+static thread_local std::string g_err;
+
+static clamp_status fail(clamp_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+static clamp_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(CLAMP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define API_CUDA(x, where)                             \
+  do {                                                 \
+    cudaError_t _e = (x);                              \
+    if (_e != cudaSuccess) return cuda_fail(_e, where); \
+  } while (0)
+
+extern "C" const char* clamp_last_error(void) { return g_err.c_str(); }
+extern "C" const char* clamp_version(void) { return "clamp-gb300 0.1 (sm_103a)"; }
+
+// ---------------------------------------------------------------- per-device set-up
+
+static std::mutex g_dev_mu;
+static std::set<int> g_dev_ready;
+
+static clamp_status ensure_device() {
+  int dev = -1;
+  API_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  if (g_dev_ready.count(dev)) return CLAMP_OK;
+  API_CUDA(upload_twiddles(), "twiddle upload");
+  g_dev_ready.insert(dev);
+  return CLAMP_OK;
+}
+
+// ---------------------------------------------------------------- validation
+
+extern "C" int32_t clamp_supported_length(int32_t n) {
+  return (n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256) ? 1 : 0;
+}
+
+static clamp_status check_shape(int nx, int ny, int nz) {
+  if (!clamp_supported_length(nx) || !clamp_supported_length(ny) || !clamp_supported_length(nz))
+    return fail(CLAMP_EUNSUPPORTED, "volume %dx%dx%d (nx,ny,nz): axis lengths must be powers of two in [8, 256]",
+                nx, ny, nz);
+  if (nx % LC) return fail(CLAMP_EUNSUPPORTED, "nx=%d must be a multiple of %d", nx, LC);
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_check_params(const clamp_params* p) {
+  if (!p) return fail(CLAMP_EINVAL, "params is NULL");
+  clamp_status s = check_shape(p->nx, p->ny, p->nz);
+  if (s != CLAMP_OK) return s;
+  if (p->looks < 1 || p->looks > 4096) return fail(CLAMP_EINVAL, "looks=%d must be in [1, 4096]", p->looks);
+  if (!(p->noise_var > 0.f) || !isfinite(p->noise_var)) return fail(CLAMP_EINVAL, "noise_var must be > 0");
+  if (!(p->prox_var > 0.f) || !isfinite(p->prox_var)) return fail(CLAMP_EINVAL, "prox_var must be > 0");
+  if (!(p->rho > 0.f && p->rho < 1.f)) return fail(CLAMP_EINVAL, "rho=%g must be in (0, 1)", p->rho);
+  if (!(p->prior_weight > 0.f && p->prior_weight < 1.f))
+    return fail(CLAMP_EINVAL, "prior_weight=%g must be in (0, 1)", p->prior_weight);
+  if (p->max_iters < 0) return fail(CLAMP_EINVAL, "max_iters must be >= 0");
+  if (p->k0 < 0) return fail(CLAMP_EINVAL, "k0 must be >= 0");
+  if (!(p->tol >= 0.0)) return fail(CLAMP_EINVAL, "tol must be >= 0");
+  return CLAMP_OK;
+}
+
+// ---------------------------------------------------------------- workspace layout
+
+namespace {
+struct Arena {
+  size_t off = 0;
+  template <class T>
+  size_t take(long long count) {
+    const size_t o = off;
+    off += ((size_t)count * sizeof(T) + 255) & ~(size_t)255;
+    return o;
+  }
+};
+
+struct AgentLayout {
+  size_t T, U, s1, s2, s4, s3, gamma, mures, num, den, maxp, scal, err;
+  int pz, px, nbc;
+  size_t bytes;
+};
+
+AgentLayout agent_layout(const clamp_params* p) {
+  AgentLayout a{};
+  const long long n = (long long)p->nx * p->ny * p->nz, L = p->looks;
+  a.pz = (p->nx / LC) * p->ny;
+  a.px = (int)((long long)p->nz * p->ny / rows_per_cta(p->nx));
+  a.nbc = passc_blocks(n);
+  Arena ar;
+  a.T = ar.take<float4>(L * n);
+  a.U = ar.take<float2>(L * n);
+  a.s1 = ar.take<double>(L * a.pz);
+  a.s2 = ar.take<double>(L * a.pz);
+  a.s4 = ar.take<double>(L * a.pz);
+  a.s3 = ar.take<double>(L * a.px);
+  a.gamma = ar.take<float>(L);
+  a.mures = ar.take<double>(L);
+  a.num = ar.take<double>(a.nbc);
+  a.den = ar.take<double>(a.nbc);
+  a.maxp = ar.take<float>(a.nbc);
+  a.scal = ar.take<double>(8);
+  a.err = ar.take<int>(8);
+  a.bytes = ar.off;
+  return a;
+}
+
+struct ReconLayout {
+  size_t mu, r, w, ce_ring, mu_ring, agent, den;
+  size_t bytes;
+};
+
+ReconLayout recon_layout(const clamp_params* p, const clamp_denoiser* den) {
+  ReconLayout r{};
+  const long long n = (long long)p->nx * p->ny * p->nz, L = p->looks;
+  Arena ar;
+  r.mu = ar.take<float2>(L * n);
+  r.r = ar.take<float>((L + 1) * n);
+  r.w = ar.take<float>((L + 1) * n);
+  const int ring = p->max_iters > 0 ? p->max_iters : 1;
+  r.ce_ring = ar.take<double>(ring);
+  r.mu_ring = ar.take<double>(ring);
+  r.agent = ar.off;
+  r.den = ar.off + agent_layout(p).bytes;  // the denoiser scratch follows the agent scratch
+  ar.off += agent_layout(p).bytes + ((denoise_ws_bytes(den, p->nx, p->ny, p->nz) + 255) & ~(size_t)255);
+  r.bytes = ar.off;
+  return r;
+}
+
+template <class T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+struct Derived {
+  Geom g;
+  AgentScalars s;
+  double alpha;
+};
+
+// alpha = mean(a^2) for the separable aperture a = window[kz] * pupil[ky][kx] (host, double).
+clamp_status derive(const clamp_params* p, const float* pupil, const float* window, cudaStream_t st, Derived* d) {
+  d->g.nx = p->nx;
+  d->g.ny = p->ny;
+  d->g.nz = p->nz;
+  d->g.L = p->looks;
+  d->g.n = (long long)p->nx * p->ny * p->nz;
+  std::vector<float> hp((size_t)p->nx * p->ny), hw(p->nz);
+  API_CUDA(cudaMemcpyAsync(hp.data(), pupil, hp.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "pupil read");
+  API_CUDA(cudaMemcpyAsync(hw.data(), window, hw.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "window read");
+  API_CUDA(cudaStreamSynchronize(st), "pupil read");
+  double sp = 0, sw = 0;
+  for (float v : hp) {
+    if (!isfinite(v)) return fail(CLAMP_EINVAL, "pupil has a non-finite value");
+    sp += (double)v * v;
+  }
+  for (float v : hw) {
+    if (!isfinite(v)) return fail(CLAMP_EINVAL, "window has a non-finite value");
+    sw += (double)v * v;
+  }
+  const double alpha = (sp / hp.size()) * (sw / hw.size());
+  if (!(alpha > 0)) return fail(CLAMP_EINVAL, "aperture is identically zero (alpha = 0)");
+  d->alpha = alpha;
+  d->s.nv = p->noise_var;
+  d->s.alpha = (float)alpha;
+  d->s.floor = (float)((double)p->noise_var / alpha);
+  d->s.sc_x = (float)(1.0 / sqrt((double)p->nx));
+  d->s.sc_y = (float)(1.0 / sqrt((double)p->ny));
+  d->s.sc_z = (float)(1.0 / sqrt((double)p->nz));
+  return CLAMP_OK;
+}
+
+Partials partials(const AgentLayout& a, void* ws) {
+  Partials p{};
+  p.s1 = at<double>(ws, a.s1);
+  p.s2 = at<double>(ws, a.s2);
+  p.s4 = at<double>(ws, a.s4);
+  p.s3 = at<double>(ws, a.s3);
+  p.pz = a.pz;
+  p.px = a.px;
+  return p;
+}
+
+clamp_status need_ptrs(std::initializer_list<const void*> ptrs, const char* what) {
+  for (const void* q : ptrs)
+    if (!q) return fail(CLAMP_EINVAL, "%s: NULL array argument", what);
+  return CLAMP_OK;
+}
+
+clamp_status check_ws(void* ws, size_t have, size_t need, const char* what) {
+  if (!ws) return fail(CLAMP_EINVAL, "%s: workspace is NULL", what);
+  if (((uintptr_t)ws) & 255) return fail(CLAMP_EINVAL, "%s: workspace must be 256-byte aligned", what);
+  if (have < need) return fail(CLAMP_ENOMEM, "%s: workspace %zu bytes < %zu needed", what, have, need);
+  return CLAMP_OK;
+}
+}  // namespace
+
+#define API_TRY(x)                       \
+  do {                                   \
+    clamp_status _s = (x);               \
+    if (_s != CLAMP_OK) return _s;       \
+  } while (0)
+
+extern "C" size_t clamp_workspace_size(const clamp_params* p) {
+  if (clamp_check_params(p) != CLAMP_OK) return 0;
+  return agent_layout(p).bytes;
+}
+
+extern "C" size_t clamp_reconstruct_workspace_size(const clamp_params* p, const clamp_denoiser* den) {
+  if (clamp_check_params(p) != CLAMP_OK) return 0;
+  return recon_layout(p, den).bytes;
+}
+
+// ---------------------------------------------------------------- entry points
+
+extern "C" clamp_status clamp_fft3(int32_t nx, int32_t ny, int32_t nz, int32_t batch, const float* in, float* out,
+                                   int32_t inverse, void* stream) {
+  API_TRY(check_shape(nx, ny, nz));
+  if (batch < 1) return fail(CLAMP_EINVAL, "batch=%d must be >= 1", batch);
+  API_TRY(need_ptrs({in, out}, "clamp_fft3"));
+  API_TRY(ensure_device());
+  Geom g{nx, ny, nz, batch, (long long)nx * ny * nz};
+  API_CUDA(launch_fft3(g, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), inverse != 0,
+                       (float)(1.0 / sqrt((double)nx)), (float)(1.0 / sqrt((double)ny)),
+                       (float)(1.0 / sqrt((double)nz)), (cudaStream_t)stream),
+           "clamp_fft3 launch");
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_simulate(const clamp_params* p, const float* r, const float* speckle, const float* noise,
+                                       const float* pupil, const float* window, float* y, void* stream) {
+  API_TRY(clamp_check_params(p));
+  API_TRY(need_ptrs({r, speckle, noise, pupil, window, y}, "clamp_simulate"));
+  API_TRY(ensure_device());
+  Geom g{p->nx, p->ny, p->nz, p->looks, (long long)p->nx * p->ny * p->nz};
+  API_CUDA(launch_simulate(g, r, reinterpret_cast<const float2*>(speckle), reinterpret_cast<const float2*>(noise),
+                           pupil, window, (float)sqrt((double)p->noise_var), reinterpret_cast<float2*>(y),
+                           (float)(1.0 / sqrt((double)p->nx)), (float)(1.0 / sqrt((double)p->ny)),
+                           (float)(1.0 / sqrt((double)p->nz)), (cudaStream_t)stream),
+           "clamp_simulate launch");
+  return CLAMP_OK;
+}
+
+static clamp_status do_init(const clamp_params* p, const Derived& d, const float* y, const float* pupil,
+                            const float* window, const float* r_init, float2* mu, float* r, float* w,
+                            const AgentLayout& al, void* ws, cudaStream_t st) {
+  const double mu_scale = (p->flags & CLAMP_FLAG_MU_INIT_NO_ALPHA) ? 1.0 : 1.0 / d.alpha;
+  API_CUDA(launch_adjoint(d.g, reinterpret_cast<const float2*>(y), pupil, window, (float)mu_scale, mu, d.s.sc_x,
+                          d.s.sc_y, d.s.sc_z, st),
+           "adjoint launch");
+  API_CUDA(launch_init_state(d.g, mu, (float)mu_scale, r_init, r, w, at<float>(ws, al.maxp), nullptr, st),
+           "init launch");
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_init(const clamp_params* p, const float* y, const float* pupil, const float* window,
+                                   const float* r_init, float* mu, float* r, float* w, void* ws, size_t ws_bytes,
+                                   void* stream) {
+  API_TRY(clamp_check_params(p));
+  API_TRY(need_ptrs({y, pupil, window, mu, r, w}, "clamp_init"));
+  const AgentLayout al = agent_layout(p);
+  API_TRY(check_ws(ws, ws_bytes, al.bytes, "clamp_init"));
+  API_TRY(ensure_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  Derived d;
+  API_TRY(derive(p, pupil, window, st, &d));
+  return do_init(p, d, y, pupil, window, r_init, reinterpret_cast<float2*>(mu), r, w, al, ws, st);
+}
+
+static float beta_of(int k) { return (float)(1.0 + 2.0 / log((double)k + 1.0)); }
+
+static clamp_status agent_ffts(const Derived& d, const float* y, const float* pupil, const float* window,
+                               const float2* mu, const float* r, const AgentLayout& al, void* ws, cudaStream_t st) {
+  API_CUDA(launch_agent_fft(d.g, d.s, mu, r, reinterpret_cast<const float2*>(y), pupil, window,
+                            at<float4>(ws, al.T), at<float2>(ws, al.U), partials(al, ws), st),
+           "forward-agent FFT passes");
+  API_CUDA(launch_gamma(d.g, d.s.nv, partials(al, ws), at<float>(ws, al.gamma), at<double>(ws, al.mures), st),
+           "line search");
+  return CLAMP_OK;
+}
+
+static PassC passc_args(const clamp_params* p, const Derived& d, const AgentLayout& al, void* ws, float2* mu,
+                        float* r, float* w, float* wbar, int k) {
+  PassC c{};
+  c.d = at<float2>(ws, al.U);
+  c.mu = mu;
+  c.r = r;
+  c.w = w;
+  c.wbar = wbar;
+  c.gamma = at<float>(ws, al.gamma);
+  c.nv = p->noise_var;
+  c.alpha = d.s.alpha;
+  c.prox_var = p->prox_var;
+  c.beta = k > 0 ? beta_of(k) : 1.0f;
+  c.ups_look = (float)((1.0 - (double)p->prior_weight) / p->looks);
+  c.ups_prior = p->prior_weight;
+  c.rho = p->rho;
+  c.part_num = at<double>(ws, al.num);
+  c.part_den = at<double>(ws, al.den);
+  c.err = at<int>(ws, al.err);
+  return c;
+}
+
+extern "C" clamp_status clamp_forward_prox(const clamp_params* p, int32_t k, const float* y, const float* pupil,
+                                           const float* window, float* mu, float* r, const float* w,
+                                           double* mu_residual, void* ws, size_t ws_bytes, void* stream) {
+  API_TRY(clamp_check_params(p));
+  if (k < 1) return fail(CLAMP_EINVAL, "iteration index k=%d must be >= 1", k);
+  API_TRY(need_ptrs({y, pupil, window, mu, r, w}, "clamp_forward_prox"));
+  const AgentLayout al = agent_layout(p);
+  API_TRY(check_ws(ws, ws_bytes, al.bytes, "clamp_forward_prox"));
+  API_TRY(ensure_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  Derived d;
+  API_TRY(derive(p, pupil, window, st, &d));
+  API_TRY(agent_ffts(d, y, pupil, window, reinterpret_cast<float2*>(mu), r, al, ws, st));
+  if (mu_residual) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_residual, st), "mu residual");
+  PassC c = passc_args(p, d, al, ws, reinterpret_cast<float2*>(mu), r, const_cast<float*>(w), nullptr, k);
+  c.err = nullptr;
+  API_CUDA(launch_prox_only(d.g, c, st), "prox pass");
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_mace_step(const clamp_params* p, const float* r, float* w, float* wbar,
+                                        double* ce_residual, void* ws, size_t ws_bytes, void* stream) {
+  API_TRY(clamp_check_params(p));
+  API_TRY(need_ptrs({r, w, wbar}, "clamp_mace_step"));
+  const AgentLayout al = agent_layout(p);
+  API_TRY(check_ws(ws, ws_bytes, al.bytes, "clamp_mace_step"));
+  API_TRY(ensure_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  Derived d{};
+  d.g = Geom{p->nx, p->ny, p->nz, p->looks, (long long)p->nx * p->ny * p->nz};
+  PassC c = passc_args(p, d, al, ws, nullptr, const_cast<float*>(r), w, wbar, 0);
+  c.err = nullptr;
+  API_CUDA(launch_mace_only(d.g, c, st), "MACE pass");
+  if (ce_residual) API_CUDA(launch_ce_final(c.part_num, c.part_den, al.nbc, ce_residual, st), "CE residual");
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_denoise(const clamp_denoiser* den, const float* w_prior, float* r_prior, int32_t nx,
+                                      int32_t ny, int32_t nz, void* ws, size_t ws_bytes, void* stream) {
+  if (!den) return fail(CLAMP_EINVAL, "denoiser is NULL");
+  if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096)
+    return fail(CLAMP_EINVAL, "denoiser volume %dx%dx%d out of range", nx, ny, nz);
+  API_TRY(need_ptrs({w_prior, r_prior}, "clamp_denoise"));
+  const size_t need = denoise_ws_bytes(den, nx, ny, nz);
+  if (need) API_TRY(check_ws(ws, ws_bytes, need, "clamp_denoise"));
+  API_TRY(ensure_device());
+  API_CUDA(denoise_apply(den, w_prior, r_prior, nx, ny, nz, ws, (cudaStream_t)stream), "denoiser");
+  return CLAMP_OK;
+}
+
+extern "C" size_t clamp_denoise_workspace_size(const clamp_denoiser* den, int32_t nx, int32_t ny, int32_t nz) {
+  return den ? denoise_ws_bytes(den, nx, ny, nz) : 0;
+}
+
+// ---------------------------------------------------------------- driver (Alg. 2)
+
+static size_t iterate_ws_bytes(const clamp_params* p, const clamp_denoiser* den) {
+  return agent_layout(p).bytes + ((denoise_ws_bytes(den, p->nx, p->ny, p->nz) + 255) & ~(size_t)255);
+}
+
+extern "C" size_t clamp_iterate_workspace_size(const clamp_params* p, const clamp_denoiser* den) {
+  if (clamp_check_params(p) != CLAMP_OK) return 0;
+  return iterate_ws_bytes(p, den);
+}
+
+// One to many loop bodies of Alg. 2 on the state (mu, r, w); ws = agent scratch then denoiser scratch.
+static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_first, int iters, const float* y,
+                                 const float* pupil, const float* window, const clamp_denoiser* den, float2* mu,
+                                 float* r, float* w, float* wbar, double* ce_out, double* mu_out, void* ws,
+                                 void* const* events, cudaStream_t st) {
+  const AgentLayout al = agent_layout(p);
+  void* dws = static_cast<char*>(ws) + al.bytes;
+  const long long n = d.g.n;
+  for (int it = 0; it < iters; ++it) {
+    const int k = k_first + it;
+    if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 0], st), "event");
+    API_TRY(agent_ffts(d, y, pupil, window, mu, r, al, ws, st));
+    if (mu_out) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_out + it, st), "mu residual");
+    if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 1], st), "event");
+    API_CUDA(denoise_apply(den, w + (long long)p->looks * n, r + (long long)p->looks * n, p->nx, p->ny, p->nz, dws,
+                           st),
+             "denoiser");
+    if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 2], st), "event");
+    PassC c = passc_args(p, d, al, ws, mu, r, w, wbar, k);
+    API_CUDA(launch_pass_c_fused(d.g, c, st), "fused prox + MACE pass");
+    if (ce_out) API_CUDA(launch_ce_final(c.part_num, c.part_den, al.nbc, ce_out + it, st), "CE residual");
+    if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 3], st), "event");
+  }
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_iterate(const clamp_params* p, int32_t k_first, int32_t iters, const float* y,
+                                      const float* pupil, const float* window, const clamp_denoiser* den, float* mu,
+                                      float* r, float* w, float* wbar, double* ce_out, double* mu_out, void* ws,
+                                      size_t ws_bytes, void* const* events, void* stream) {
+  API_TRY(clamp_check_params(p));
+  if (!den) return fail(CLAMP_EINVAL, "clamp_iterate: denoiser is NULL");
+  if (k_first < 1 || iters < 0) return fail(CLAMP_EINVAL, "clamp_iterate: k_first=%d must be >= 1, iters >= 0",
+                                            k_first);
+  API_TRY(need_ptrs({y, pupil, window, mu, r, w, wbar}, "clamp_iterate"));
+  API_TRY(check_ws(ws, ws_bytes, iterate_ws_bytes(p, den), "clamp_iterate"));
+  API_TRY(ensure_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  Derived d;
+  API_TRY(derive(p, pupil, window, st, &d));
+  API_CUDA(cudaMemsetAsync(at<int>(ws, agent_layout(p).err), 0, sizeof(int), st), "memset");
+  return iterate_impl(p, d, k_first, iters, y, pupil, window, den, reinterpret_cast<float2*>(mu), r, w, wbar, ce_out,
+                      mu_out, ws, events, st);
+}
+
+static clamp_status reconstruct_impl(const clamp_params* p, const float* y, const float* pupil, const float* window,
+                                     const clamp_denoiser* den, const float* r_init, float* r_out,
+                                     clamp_report* report, void* ws, cudaStream_t st) {
+  const ReconLayout rl = recon_layout(p, den);
+  const AgentLayout al = agent_layout(p);
+  void* aws = static_cast<char*>(ws) + rl.agent;
+  float2* mu = at<float2>(ws, rl.mu);
+  float* r = at<float>(ws, rl.r);
+  float* w = at<float>(ws, rl.w);
+  double* ce_ring = at<double>(ws, rl.ce_ring);
+  double* mu_ring = at<double>(ws, rl.mu_ring);
+  const long long n = (long long)p->nx * p->ny * p->nz;
+  Derived d;
+  API_TRY(derive(p, pupil, window, st, &d));
+  API_CUDA(cudaMemsetAsync(at<int>(aws, al.err), 0, sizeof(int), st), "memset");
+  API_TRY(do_init(p, d, y, pupil, window, r_init, mu, r, w, al, aws, st));
+  if (p->max_iters == 0) {
+    // r* = wbar of the initial state = r0
+    API_CUDA(cudaMemcpyAsync(r_out, r + (long long)p->looks * n, n * sizeof(float), cudaMemcpyDeviceToDevice, st),
+             "copy");
+  }
+  const int check = p->check_every > 0 ? p->check_every : 10;
+  int done = 0;
+  bool converged = false;
+  std::vector<double> ce_h(p->max_iters > 0 ? p->max_iters : 1), mu_h(ce_h.size());
+  int synced_upto = 0;
+  for (int it = 0; it < p->max_iters; ++it) {
+    const int k = p->k0 + it + 1;
+    API_TRY(iterate_impl(p, d, k, 1, y, pupil, window, den, mu, r, w, r_out, ce_ring + it, mu_ring + it, aws,
+                         nullptr, st));
+    done = it + 1;
+    const bool last = (it + 1 == p->max_iters);
+    if ((p->tol > 0 && ((it + 1) % check == 0 || last)) || (last && report)) {
+      int herr = 0;
+      API_CUDA(cudaMemcpyAsync(ce_h.data() + synced_upto, ce_ring + synced_upto, (done - synced_upto) * sizeof(double),
+                               cudaMemcpyDeviceToHost, st),
+               "residual readback");
+      API_CUDA(cudaMemcpyAsync(&herr, at<int>(aws, al.err), sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+      API_CUDA(cudaStreamSynchronize(st), "residual readback");
+      if (herr) return fail(CLAMP_ENONFINITE, "non-finite value in the state at or before iteration %d", k);
+      for (int i = synced_upto; i < done; ++i) {
+        if (p->tol > 0 && ce_h[i] <= p->tol) {
+          converged = true;
+        }
+      }
+      synced_upto = done;
+      if (converged) break;
+    }
+  }
+  if (report) {
+    report->iters = done;
+    report->converged = converged ? 1 : 0;
+    if (done > 0) {
+      API_CUDA(cudaMemcpyAsync(ce_h.data(), ce_ring, done * sizeof(double), cudaMemcpyDeviceToHost, st), "report");
+      API_CUDA(cudaMemcpyAsync(mu_h.data(), mu_ring, done * sizeof(double), cudaMemcpyDeviceToHost, st), "report");
+      API_CUDA(cudaStreamSynchronize(st), "report");
+      report->ce_residual = ce_h[done - 1];
+      report->mu_residual = mu_h[done - 1];
+      if (report->ce_hist) memcpy(report->ce_hist, ce_h.data(), done * sizeof(double));
+      if (report->mu_hist) memcpy(report->mu_hist, mu_h.data(), done * sizeof(double));
+    } else {
+      report->ce_residual = report->mu_residual = 0.0;
+    }
+  }
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_reconstruct(const clamp_params* p, const float* y, const float* pupil,
+                                          const float* window, const clamp_denoiser* den, const float* r_init,
+                                          float* r_out, clamp_report* report, void* ws, size_t ws_bytes,
+                                          void* stream) {
+  API_TRY(clamp_check_params(p));
+  if (!den) return fail(CLAMP_EINVAL, "clamp_reconstruct: denoiser is NULL");
+  API_TRY(need_ptrs({y, pupil, window, r_out}, "clamp_reconstruct"));
+  API_TRY(ensure_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t need = recon_layout(p, den).bytes;
+  void* own = nullptr;
+  if (!ws) {
+    API_CUDA(cudaMalloc(&own, need), "workspace allocation");
+    ws = own;
+    ws_bytes = need;
+  }
+  clamp_status s = check_ws(ws, ws_bytes, need, "clamp_reconstruct");
+  if (s == CLAMP_OK) s = reconstruct_impl(p, y, pupil, window, den, r_init, r_out, report, ws, st);
+  if (own) {
+    cudaStreamSynchronize(st);
+    cudaFree(own);
+  }
+  return s;
+}
+
+// ---------------------------------------------------------------- host-buffer variant with a device cache
+
+namespace {
+struct HostCache {
+  int dev = -1;
+  void* buf = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_cache_mu;
+std::vector<HostCache> g_cache;
+}  // namespace
+
+extern "C" void clamp_release_cache(void) {
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  int cur = -1;
+  cudaGetDevice(&cur);
+  for (auto& c : g_cache) {
+    if (c.buf) {
+      cudaSetDevice(c.dev);
+      cudaFree(c.buf);
+    }
+  }
+  g_cache.clear();
+  if (cur >= 0) cudaSetDevice(cur);
+}
+
+extern "C" clamp_status clamp_reconstruct_host(const clamp_params* p, const float* y_host, const float* pupil_host,
+                                               const float* window_host, const clamp_denoiser* den,
+                                               const float* r_init_host, float* r_out_host, clamp_report* report,
+                                               void* stream) {
+  API_TRY(clamp_check_params(p));
+  if (!den) return fail(CLAMP_EINVAL, "clamp_reconstruct_host: denoiser is NULL");
+  API_TRY(need_ptrs({y_host, pupil_host, window_host, r_out_host}, "clamp_reconstruct_host"));
+  API_TRY(ensure_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  const long long n = (long long)p->nx * p->ny * p->nz, L = p->looks;
+  Arena ar;
+  const size_t o_y = ar.take<float2>(L * n), o_p = ar.take<float>((long long)p->nx * p->ny),
+               o_w = ar.take<float>(p->nz), o_ri = ar.take<float>(n), o_ro = ar.take<float>(n);
+  const size_t o_ws = ar.off;
+  const size_t need = o_ws + recon_layout(p, den).bytes;
+  int dev = 0;
+  API_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  HostCache* hc = nullptr;
+  for (auto& c : g_cache)
+    if (c.dev == dev) hc = &c;
+  if (!hc) {
+    g_cache.push_back(HostCache{dev, nullptr, 0});
+    hc = &g_cache.back();
+  }
+  if (hc->bytes < need) {
+    if (hc->buf) {
+      API_CUDA(cudaDeviceSynchronize(), "sync");
+      cudaFree(hc->buf);
+      hc->buf = nullptr;
+      hc->bytes = 0;
+    }
+    API_CUDA(cudaMalloc(&hc->buf, need), "device cache allocation");
+    hc->bytes = need;
+  }
+  char* b = static_cast<char*>(hc->buf);
+  API_CUDA(cudaMemcpyAsync(b + o_y, y_host, L * n * sizeof(float2), cudaMemcpyHostToDevice, st), "y upload");
+  API_CUDA(cudaMemcpyAsync(b + o_p, pupil_host, (size_t)p->nx * p->ny * sizeof(float), cudaMemcpyHostToDevice, st),
+           "pupil upload");
+  API_CUDA(cudaMemcpyAsync(b + o_w, window_host, p->nz * sizeof(float), cudaMemcpyHostToDevice, st), "window upload");
+  if (r_init_host)
+    API_CUDA(cudaMemcpyAsync(b + o_ri, r_init_host, n * sizeof(float), cudaMemcpyHostToDevice, st), "r_init upload");
+  clamp_status s = reconstruct_impl(p, reinterpret_cast<float*>(b + o_y), reinterpret_cast<float*>(b + o_p),
+                                    reinterpret_cast<float*>(b + o_w), den,
+                                    r_init_host ? reinterpret_cast<float*>(b + o_ri) : nullptr,
+                                    reinterpret_cast<float*>(b + o_ro), report, b + o_ws, st);
+  if (s != CLAMP_OK) return s;
+  API_CUDA(cudaMemcpyAsync(r_out_host, b + o_ro, n * sizeof(float), cudaMemcpyDeviceToHost, st), "r_out download");
+  API_CUDA(cudaStreamSynchronize(st), "sync");
+  return CLAMP_OK;
+}

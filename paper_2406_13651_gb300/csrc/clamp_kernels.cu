@@ -1,0 +1,746 @@
+// clamp_kernels.cu -- CLAMP forward-agent, MACE and set-up passes for sm_103a.
+//
+// Per look and iteration the forward agent needs F(mu), F(D mu) and F^H of the
+// frequency-domain gradient (Eq. h-gradient).  The 3D transforms are split in
+// axis passes over HBM, with the agent arithmetic fused into them:
+//   A_x : read mu, r'  -> x-FFT of mu and D mu             -> T (float4 per voxel)
+//   A_y : T            -> y-FFT of both                    -> T (in place)
+//   ABz : T, y, a      -> z-FFT of both; Fd = a(y - aM)/sigma_w^2 - P;
+//                         S1 = ||Fd||^2, S2 = ||a Fd||^2, S4 = ||a y||^2;
+//                         inverse z-FFT of Fd              -> U
+//   B_y : U            -> inverse y-FFT                    -> U (in place)
+//   B_x : U, r'        -> inverse x-FFT = d; S3 = sum |d|^2 D -> U holds d
+// then gamma = S1 / (S2/sigma_w^2 + S3) (Parseval: ||d|| = ||Fd||, ||Ad|| = ||a Fd||)
+// and one elementwise pass C over all looks of a voxel does the mu update,
+// the App. A prox and the Mann step.
+#include "clamp_kernels.cuh"
+#include "fft_core.cuh"
+
+#include <math.h>
+
+#include <type_traits>
+#include <vector>
+
+namespace clamp {
+
+__device__ float2 g_tw[kTwTotal];
+
+cudaError_t upload_twiddles() {
+  std::vector<float2> h(kTwTotal);
+  for (int N = 8; N <= 256; N *= 2) {
+    const int off = tw_offset(N);
+    for (int m = 0; m < N; ++m) {
+      const double ang = -2.0 * M_PI * (double)m / (double)N;
+      h[off + m] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+  }
+  return cudaMemcpyToSymbol(g_tw, h.data(), sizeof(float2) * kTwTotal);
+}
+
+static const float2* tw_ptr(int N) {
+  void* p = nullptr;
+  cudaGetSymbolAddress(&p, g_tw);
+  return reinterpret_cast<const float2*>(p) + tw_offset(N);
+}
+
+extern __shared__ float4 dyn_smem[];
+
+// ---------------------------------------------------------------- reductions
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-reduces NV float partials (per-thread FP32, warp FP32, across warps FP64
+// in fixed order) and writes them to out[k][idx].  All threads must call.
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(const float (&v)[NV], double* const (&out)[NV], long long idx) {
+  __shared__ double red[NT / 32][NV];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float s = warp_sum(v[k]);
+    if (lane == 0) red[warp][k] = (double)s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double acc = 0.0;
+    for (int wi = 0; wi < (int)(blockDim.x / 32); ++wi) acc += red[wi][threadIdx.x];
+    out[threadIdx.x][idx] = acc;
+  }
+}
+
+// ---------------------------------------------------------------- pass A_x
+
+template <int N>
+__global__ void __launch_bounds__(NT) k_a_x(Geom g, AgentScalars s, const float2* __restrict__ mu,
+                                            const float* __restrict__ rprev, float4* __restrict__ T,
+                                            const float2* __restrict__ tw) {
+  constexpr int LX = rows_per_cta(N), LT = 2 * LX, LD = N + 1;
+  float2* sm = reinterpret_cast<float2*>(dyn_smem);
+  const long long e0 = (long long)blockIdx.x * LX * N;  // first element of the tile
+  for (int e = threadIdx.x; e < LX * N; e += NT) {
+    const int line = e / N, i = e - line * N;
+    const float2 m = mu[e0 + e];
+    const float D = 1.0f / (rprev[e0 + e] + s.floor);
+    sm[line * LD + i] = m;
+    sm[(LX + line) * LD + i] = cscale(m, D);
+  }
+  __syncthreads();
+  fft_tile<N, LT, NT, false>(sm, tw);
+  for (int e = threadIdx.x; e < LX * N; e += NT) {
+    const int line = e / N, i = e - line * N;
+    const float2 a = cscale(sm[line * LD + i], s.sc_x);
+    const float2 b = cscale(sm[(LX + line) * LD + i], s.sc_x);
+    T[e0 + e] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+// ---------------------------------------------------------------- pass A_y (in place on T)
+
+template <int N>
+__global__ void __launch_bounds__(NT) k_a_y(Geom g, AgentScalars s, float4* __restrict__ T,
+                                            const float2* __restrict__ tw) {
+  constexpr int LT = 2 * LC, LD = N + 1;
+  float2* sm = reinterpret_cast<float2*>(dyn_smem);
+  const long long S = g.nx;
+  const long long base = (long long)blockIdx.z * g.n + (long long)blockIdx.y * g.ny * g.nx + blockIdx.x * LC;
+  for (int e = threadIdx.x; e < LC * N; e += NT) {
+    const int line = e % LC, i = e / LC;
+    const float4 v = T[base + i * S + line];
+    sm[line * LD + i] = make_float2(v.x, v.y);
+    sm[(LC + line) * LD + i] = make_float2(v.z, v.w);
+  }
+  __syncthreads();
+  fft_tile<N, LT, NT, false>(sm, tw);
+  for (int e = threadIdx.x; e < LC * N; e += NT) {
+    const int line = e % LC, i = e / LC;
+    const float2 a = cscale(sm[line * LD + i], s.sc_y);
+    const float2 b = cscale(sm[(LC + line) * LD + i], s.sc_y);
+    T[base + i * S + line] = make_float4(a.x, a.y, b.x, b.y);
+  }
+}
+
+// ---------------------------------------------------------------- fused z pass (A_z + gradient + B_z)
+
+template <int N>
+__global__ void __launch_bounds__(NT) k_ab_z(Geom g, AgentScalars s, const float4* __restrict__ T,
+                                             const float2* __restrict__ y, const float* __restrict__ pupil,
+                                             const float* __restrict__ window, float2* __restrict__ U,
+                                             Partials p, const float2* __restrict__ tw) {
+  constexpr int LT = 2 * LC, LD = N + 1;
+  float2* sm = reinterpret_cast<float2*>(dyn_smem);
+  const long long S = (long long)g.nx * g.ny;
+  const int x0 = blockIdx.x * LC, ky = blockIdx.y, l = blockIdx.z;
+  const long long base = (long long)l * g.n + (long long)ky * g.nx + x0;
+  for (int e = threadIdx.x; e < LC * N; e += NT) {
+    const int line = e % LC, i = e / LC;
+    const float4 v = T[base + i * S + line];
+    sm[line * LD + i] = make_float2(v.x, v.y);
+    sm[(LC + line) * LD + i] = make_float2(v.z, v.w);
+  }
+  __syncthreads();
+  fft_tile<N, LT, NT, false>(sm, tw);
+  // frequency-domain gradient: Fd = a (y - a M) / sigma_w^2 - P
+  float acc[3] = {0.f, 0.f, 0.f};
+  const float inv_nv = 1.0f / s.nv;
+  for (int e = threadIdx.x; e < LC * N; e += NT) {
+    const int line = e % LC, kz = e / LC;
+    const float2 M = cscale(sm[line * LD + kz], s.sc_z);
+    const float2 P = cscale(sm[(LC + line) * LD + kz], s.sc_z);
+    const float av = __ldg(&pupil[ky * g.nx + x0 + line]) * __ldg(&window[kz]);
+    const float2 yv = y[base + kz * S + line];
+    const float2 res = make_float2(fmaf(-av, M.x, yv.x), fmaf(-av, M.y, yv.y));
+    const float f = av * inv_nv;
+    const float2 fd = make_float2(fmaf(f, res.x, -P.x), fmaf(f, res.y, -P.y));
+    const float fd2 = cabs2(fd), a2 = av * av;
+    acc[0] += fd2;
+    acc[1] += a2 * fd2;
+    acc[2] += a2 * cabs2(yv);
+    sm[line * LD + kz] = fd;
+  }
+  __syncthreads();
+  fft_tile<N, LC, NT, true>(sm, tw);
+  for (int e = threadIdx.x; e < LC * N; e += NT) {
+    const int line = e % LC, i = e / LC;
+    U[base + i * S + line] = cscale(sm[line * LD + i], s.sc_z);
+  }
+  double* const outs[3] = {p.s1, p.s2, p.s4};
+  block_reduce_store<3>(acc, outs, (long long)l * p.pz + (long long)blockIdx.y * gridDim.x + blockIdx.x);
+}
+
+// ---------------------------------------------------------------- generic single-transform passes
+
+enum RowMode { ROW_PLAIN = 0, ROW_SIM = 1, ROW_ADJ = 2, ROW_BX = 3 };
+enum ColMode { COL_PLAIN = 0, COL_SIM = 1, COL_ADJ = 2 };
+
+struct RowArgs {
+  const float2* in;
+  float2* out;
+  const float* rvol;   // ROW_SIM: reflectance [n]
+  const float* rprev;  // ROW_BX: r' [L][n]
+  float scale;         // 1/sqrt(N) (times mu_scale for ROW_ADJ)
+  float floor;         // ROW_BX: sigma_w^2 / alpha
+  double* s3;          // ROW_BX partials
+  int px;              // ROW_BX partials per look
+  long long n;
+  int nx;
+};
+
+template <int N, bool INV, int MODE>
+__global__ void __launch_bounds__(NT) k_row(RowArgs a, const float2* __restrict__ tw) {
+  constexpr int LX = rows_per_cta(N), LD = N + 1;
+  float2* sm = reinterpret_cast<float2*>(dyn_smem);
+  const long long e0 = (long long)blockIdx.x * LX * N;
+  for (int e = threadIdx.x; e < LX * N; e += NT) {
+    const int line = e / N, i = e - line * N;
+    float2 v = a.in[e0 + e];
+    if constexpr (MODE == ROW_SIM) {
+      const long long vox = (e0 + e) % a.n;
+      v = cscale(v, sqrtf(a.rvol[vox]));
+    }
+    sm[line * LD + i] = v;
+  }
+  __syncthreads();
+  fft_tile<N, LX, NT, INV>(sm, tw);
+  float acc[1] = {0.f};
+  for (int e = threadIdx.x; e < LX * N; e += NT) {
+    const int line = e / N, i = e - line * N;
+    const float2 v = cscale(sm[line * LD + i], a.scale);
+    if constexpr (MODE == ROW_BX) acc[0] += cabs2(v) / (a.rprev[e0 + e] + a.floor);
+    a.out[e0 + e] = v;
+  }
+  if constexpr (MODE == ROW_BX) {
+    double* const outs[1] = {a.s3};
+    const long long look = e0 / a.n;
+    const long long bpl = a.n / ((long long)LX * N);
+    block_reduce_store<1>(acc, outs, look * a.px + (blockIdx.x - look * bpl));
+  }
+}
+
+struct ColArgs {
+  const float2* in;
+  float2* out;
+  const float* pupil;
+  const float* window;
+  const float2* eta;   // COL_SIM noise draws
+  float sig_w;         // COL_SIM sqrt(sigma_w^2)
+  float scale;
+  long long n;
+  long long stride;    // element stride of the FFT axis
+  long long slab;      // element stride of grid.y (fixed index of the other axis)
+  int nx;
+  int zaxis;           // 1 when the FFT axis is z (aperture epilogue / prologue)
+};
+
+template <int N, bool INV, int MODE>
+__global__ void __launch_bounds__(NT) k_col(ColArgs a, const float2* __restrict__ tw) {
+  constexpr int LD = N + 1;
+  float2* sm = reinterpret_cast<float2*>(dyn_smem);
+  const int x0 = blockIdx.x * LC, fixed = blockIdx.y, l = blockIdx.z;
+  const long long base = (long long)l * a.n + (long long)fixed * a.slab + x0;
+  for (int e = threadIdx.x; e < LC * N; e += NT) {
+    const int line = e % LC, i = e / LC;
+    float2 v = a.in[base + i * a.stride + line];
+    if constexpr (MODE == COL_ADJ) {  // z axis, fixed = ky
+      v = cscale(v, __ldg(&a.pupil[fixed * a.nx + x0 + line]) * __ldg(&a.window[i]));
+    }
+    sm[line * LD + i] = v;
+  }
+  __syncthreads();
+  fft_tile<N, LC, NT, INV>(sm, tw);
+  for (int e = threadIdx.x; e < LC * N; e += NT) {
+    const int line = e % LC, i = e / LC;
+    float2 v = cscale(sm[line * LD + i], a.scale);
+    const long long gi = base + i * a.stride + line;
+    if constexpr (MODE == COL_SIM) {  // z axis, fixed = ky: y = a v + sigma_w eta
+      const float av = __ldg(&a.pupil[fixed * a.nx + x0 + line]) * __ldg(&a.window[i]);
+      const float2 et = a.eta[gi];
+      v = make_float2(fmaf(av, v.x, a.sig_w * et.x), fmaf(av, v.y, a.sig_w * et.y));
+    }
+    a.out[gi] = v;
+  }
+}
+
+// ---------------------------------------------------------------- dispatch helpers
+
+template <class F>
+static cudaError_t dispatch_len(int N, F&& f) {
+  switch (N) {
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 16: return f(std::integral_constant<int, 16>{});
+    case 32: return f(std::integral_constant<int, 32>{});
+    case 64: return f(std::integral_constant<int, 64>{});
+    case 128: return f(std::integral_constant<int, 128>{});
+    case 256: return f(std::integral_constant<int, 256>{});
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int N, bool INV, int MODE>
+static cudaError_t run_row(const Geom& g, const RowArgs& a, cudaStream_t st) {
+  constexpr int LX = rows_per_cta(N);
+  const size_t smem = (size_t)LX * (N + 1) * sizeof(float2);
+  auto kern = k_row<N, INV, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long rows = (long long)g.L * g.nz * g.ny;
+  kern<<<(unsigned)(rows / LX), NT, smem, st>>>(a, tw_ptr(N));
+  return cudaGetLastError();
+}
+
+template <int N, bool INV, int MODE>
+static cudaError_t run_col(const Geom& g, const ColArgs& a, int fixed_count, cudaStream_t st) {
+  const size_t smem = (size_t)LC * (N + 1) * sizeof(float2);
+  auto kern = k_col<N, INV, MODE>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(g.nx / LC, fixed_count, g.L);
+  kern<<<grid, NT, smem, st>>>(a, tw_ptr(N));
+  return cudaGetLastError();
+}
+
+static ColArgs col_args(const Geom& g, bool zaxis) {
+  ColArgs a{};
+  a.n = g.n;
+  a.nx = g.nx;
+  a.zaxis = zaxis;
+  if (zaxis) {
+    a.stride = (long long)g.nx * g.ny;
+    a.slab = g.nx;
+  } else {
+    a.stride = g.nx;
+    a.slab = (long long)g.nx * g.ny;
+  }
+  return a;
+}
+
+#define CLAMP_TRY(x)                       \
+  do {                                     \
+    cudaError_t _e = (x);                  \
+    if (_e != cudaSuccess) return _e;      \
+  } while (0)
+
+// ---------------------------------------------------------------- forward agent FFT passes
+
+cudaError_t launch_agent_fft(const Geom& g, const AgentScalars& s, const float2* mu, const float* rprev,
+                             const float2* y, const float* pupil, const float* window, float4* T, float2* U,
+                             const Partials& p, cudaStream_t st) {
+  // A_x
+  CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    constexpr int LX = rows_per_cta(N);
+    const size_t smem = (size_t)2 * LX * (N + 1) * sizeof(float2);
+    CLAMP_TRY(cudaFuncSetAttribute(k_a_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const long long rows = (long long)g.L * g.nz * g.ny;
+    k_a_x<N><<<(unsigned)(rows / LX), NT, smem, st>>>(g, s, mu, rprev, T, tw_ptr(N));
+    return cudaGetLastError();
+  }));
+  // A_y
+  CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    const size_t smem = (size_t)2 * LC * (N + 1) * sizeof(float2);
+    CLAMP_TRY(cudaFuncSetAttribute(k_a_y<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_a_y<N><<<dim3(g.nx / LC, g.nz, g.L), NT, smem, st>>>(g, s, T, tw_ptr(N));
+    return cudaGetLastError();
+  }));
+  // fused z pass
+  CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) -> cudaError_t {
+    constexpr int N = decltype(NC)::value;
+    const size_t smem = (size_t)2 * LC * (N + 1) * sizeof(float2);
+    CLAMP_TRY(cudaFuncSetAttribute(k_ab_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_ab_z<N><<<dim3(g.nx / LC, g.ny, g.L), NT, smem, st>>>(g, s, T, y, pupil, window, U, p, tw_ptr(N));
+    return cudaGetLastError();
+  }));
+  // B_y (in place on U)
+  ColArgs cy = col_args(g, false);
+  cy.in = U;
+  cy.out = U;
+  cy.scale = s.sc_y;
+  CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_PLAIN>(g, cy, g.nz, st); }));
+  // B_x (in place on U, d out, S3 partials)
+  RowArgs rx{};
+  rx.in = U;
+  rx.out = U;
+  rx.rprev = rprev;
+  rx.scale = s.sc_x;
+  rx.floor = s.floor;
+  rx.s3 = p.s3;
+  rx.px = p.px;
+  rx.n = g.n;
+  rx.nx = g.nx;
+  CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) { return run_row<decltype(NC)::value, true, ROW_BX>(g, rx, st); }));
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- gamma (exact line search)
+
+__global__ void __launch_bounds__(NT) k_gamma(int L, float nv, Partials p, float* gamma, double* mures) {
+  const int l = blockIdx.x;
+  __shared__ double red[NT][4];
+  double a1 = 0, a2 = 0, a4 = 0, a3 = 0;
+  for (int i = threadIdx.x; i < p.pz; i += NT) {
+    a1 += p.s1[(long long)l * p.pz + i];
+    a2 += p.s2[(long long)l * p.pz + i];
+    a4 += p.s4[(long long)l * p.pz + i];
+  }
+  for (int i = threadIdx.x; i < p.px; i += NT) a3 += p.s3[(long long)l * p.px + i];
+  red[threadIdx.x][0] = a1;
+  red[threadIdx.x][1] = a2;
+  red[threadIdx.x][2] = a3;
+  red[threadIdx.x][3] = a4;
+  __syncthreads();
+  for (int o = NT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 4; ++k) red[threadIdx.x][k] += red[threadIdx.x + o][k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double S1 = red[0][0], S2 = red[0][1], S3 = red[0][2], S4 = red[0][3];
+    const double den = S2 / (double)nv + S3;
+    gamma[l] = den > 0 ? (float)(S1 / den) : 0.0f;
+    mures[l] = S4 > 0 ? sqrt(S1) / (sqrt(S4) / (double)nv) : 0.0;
+  }
+}
+
+cudaError_t launch_gamma(const Geom& g, float nv, const Partials& p, float* gamma, double* mures, cudaStream_t st) {
+  k_gamma<<<g.L, NT, 0, st>>>(g.L, nv, p, gamma, mures);
+  return cudaGetLastError();
+}
+
+__global__ void k_mean(const double* v, int L, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a = 0;
+    for (int i = 0; i < L; ++i) a += v[i];
+    *out = a / L;
+  }
+}
+
+cudaError_t launch_mean(const double* v, int L, double* out, cudaStream_t st) {
+  k_mean<<<1, 32, 0, st>>>(v, L, out);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pass C
+
+// App. A reflectance update for one voxel of one look: quadratic fit of the
+// derivative of Q (Eq. convex-surrogate) between r' and xi, closed-form prox,
+// clip to the validity interval.
+__device__ __forceinline__ float prox_quad(float v, float rp, float K, float s2, float beta) {
+  const float inv = 1.0f / rp;
+  const float qr = fmaf(-K * inv, inv, inv);           // 1/r' - K/r'^2
+  const float drho = qr + (rp - v) / s2;
+  const float xi = drho > 0.0f ? rp / beta : beta * rp;
+  const float ixi = 1.0f / xi;
+  const float aq = K * (xi + rp) * (inv * inv) * (ixi * ixi);
+  const float bq = fmaf(-aq, rp, qr);
+  const float rn = (v - s2 * bq) / fmaf(s2, aq, 1.0f);
+  const float lo = fminf(rp, xi), hi = fmaxf(rp, xi);
+  return fminf(fmaxf(rn, lo), hi);
+}
+
+// Error-free sum accumulation (Knuth two-sum) for the per-voxel look averages.
+struct CSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ float get() const { return s + c; }
+};
+
+int passc_blocks(long long n) {
+  long long b = (n + NT - 1) / NT;
+  return (int)(b < 152 * 8 ? b : 152 * 8);
+}
+
+template <bool PROX, bool MACE>
+__global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
+  const long long n = g.n;
+  const int L = g.L;
+  float acc[2] = {0.f, 0.f};
+  for (long long v = (long long)blockIdx.x * NT + threadIdx.x; v < n; v += (long long)gridDim.x * NT) {
+    CSum wbar_old, xbar;
+    bool bad = false;
+    for (int l = 0; l < L; ++l) {
+      const long long i = (long long)l * n + v;
+      const float wl = c.w[i];
+      float rn;
+      if constexpr (PROX) {
+        const float rp = c.r[i];
+        float2 m = c.mu[i];
+        const float2 dd = c.d[i];
+        const float gm = __ldg(&c.gamma[l]);
+        m.x = fmaf(gm, dd.x, m.x);
+        m.y = fmaf(gm, dd.y, m.y);
+        c.mu[i] = m;
+        const float cc = c.nv * rp / fmaf(c.alpha, rp, c.nv);
+        const float K = cc + cabs2(m);
+        rn = prox_quad(wl, rp, K, c.prox_var, c.beta);
+        c.r[i] = rn;
+        bad |= !isfinite(rn);
+      } else {
+        rn = c.r[i];
+      }
+      if constexpr (MACE) {
+        wbar_old.add(c.ups_look * wl);
+        xbar.add(c.ups_look * (2.0f * rn - wl));
+      }
+    }
+    if constexpr (MACE) {
+      const long long ip = (long long)L * n + v;
+      const float rpr = c.r[ip], wpr = c.w[ip];
+      wbar_old.add(c.ups_prior * wpr);
+      xbar.add(c.ups_prior * (2.0f * rpr - wpr));
+      const float wb = wbar_old.get(), xb = xbar.get();
+      float num = 0.f;
+      CSum wbar_new;
+      for (int j = 0; j <= L; ++j) {
+        const long long i = (long long)j * n + v;
+        const float rj = c.r[i], wj = c.w[i];
+        const float dv = rj - wb;
+        num = fmaf(dv, dv, num);
+        const float wn = fmaf(2.0f * c.rho, xb - rj, wj);
+        c.w[i] = wn;
+        wbar_new.add((j < L ? c.ups_look : c.ups_prior) * wn);
+        bad |= !isfinite(wn);
+      }
+      c.wbar[v] = wbar_new.get();
+      acc[0] += num;
+      acc[1] += (float)(L + 1) * wb * wb;
+    }
+    if (bad && c.err) atomicOr(c.err, 1);
+  }
+  if constexpr (MACE) {
+    double* const outs[2] = {c.part_num, c.part_den};
+    block_reduce_store<2>(acc, outs, blockIdx.x);
+  }
+}
+
+cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st) {
+  k_pass_c<true, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  return cudaGetLastError();
+}
+cudaError_t launch_prox_only(const Geom& g, const PassC& c, cudaStream_t st) {
+  k_pass_c<true, false><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  return cudaGetLastError();
+}
+cudaError_t launch_mace_only(const Geom& g, const PassC& c, cudaStream_t st) {
+  k_pass_c<false, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(NT) k_ce_final(const double* num, const double* den, int nblk, double* ce) {
+  __shared__ double rn[NT], rd[NT];
+  double a = 0, b = 0;
+  for (int i = threadIdx.x; i < nblk; i += NT) {
+    a += num[i];
+    b += den[i];
+  }
+  rn[threadIdx.x] = a;
+  rd[threadIdx.x] = b;
+  __syncthreads();
+  for (int o = NT / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      rn[threadIdx.x] += rn[threadIdx.x + o];
+      rd[threadIdx.x] += rd[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ce = rd[0] > 0 ? sqrt(rn[0] / rd[0]) : 0.0;
+}
+
+cudaError_t launch_ce_final(const double* num, const double* den, int nblk, double* ce, cudaStream_t st) {
+  k_ce_final<<<1, NT, 0, st>>>(num, den, nblk, ce);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- plain transforms, simulation, adjoint
+
+cudaError_t launch_fft3(const Geom& g, const float2* in, float2* out, bool inverse, float sc_x, float sc_y,
+                        float sc_z, cudaStream_t st) {
+  RowArgs rx{};
+  rx.n = g.n;
+  rx.nx = g.nx;
+  ColArgs cy = col_args(g, false), cz = col_args(g, true);
+  cy.in = cy.out = out;
+  cy.scale = sc_y;
+  cz.scale = sc_z;
+  rx.scale = sc_x;
+  if (!inverse) {
+    rx.in = in;
+    rx.out = out;
+    cz.in = cz.out = out;
+    CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) { return run_row<decltype(NC)::value, false, ROW_PLAIN>(g, rx, st); }));
+    CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) { return run_col<decltype(NC)::value, false, COL_PLAIN>(g, cy, g.nz, st); }));
+    CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) { return run_col<decltype(NC)::value, false, COL_PLAIN>(g, cz, g.ny, st); }));
+  } else {
+    cz.in = in;
+    cz.out = out;
+    rx.in = rx.out = out;
+    CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_PLAIN>(g, cz, g.ny, st); }));
+    CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_PLAIN>(g, cy, g.nz, st); }));
+    CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) { return run_row<decltype(NC)::value, true, ROW_PLAIN>(g, rx, st); }));
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_simulate(const Geom& g, const float* r, const float2* z, const float2* eta, const float* pupil,
+                            const float* window, float sig_w, float2* y, float sc_x, float sc_y, float sc_z,
+                            cudaStream_t st) {
+  RowArgs rx{};
+  rx.in = z;
+  rx.out = y;
+  rx.rvol = r;
+  rx.scale = sc_x;
+  rx.n = g.n;
+  rx.nx = g.nx;
+  ColArgs cy = col_args(g, false), cz = col_args(g, true);
+  cy.in = cy.out = y;
+  cy.scale = sc_y;
+  cz.in = cz.out = y;
+  cz.scale = sc_z;
+  cz.pupil = pupil;
+  cz.window = window;
+  cz.eta = eta;
+  cz.sig_w = sig_w;
+  CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) { return run_row<decltype(NC)::value, false, ROW_SIM>(g, rx, st); }));
+  CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) { return run_col<decltype(NC)::value, false, COL_PLAIN>(g, cy, g.nz, st); }));
+  CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) { return run_col<decltype(NC)::value, false, COL_SIM>(g, cz, g.ny, st); }));
+  return cudaSuccess;
+}
+
+cudaError_t launch_adjoint(const Geom& g, const float2* y, const float* pupil, const float* window, float mu_scale,
+                           float2* mu, float sc_x, float sc_y, float sc_z, cudaStream_t st) {
+  ColArgs cz = col_args(g, true), cy = col_args(g, false);
+  cz.in = y;
+  cz.out = mu;
+  cz.pupil = pupil;
+  cz.window = window;
+  cz.scale = sc_z;
+  cy.in = cy.out = mu;
+  cy.scale = sc_y;
+  RowArgs rx{};
+  rx.in = rx.out = mu;
+  rx.scale = sc_x * mu_scale;
+  rx.n = g.n;
+  rx.nx = g.nx;
+  CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_ADJ>(g, cz, g.ny, st); }));
+  CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_PLAIN>(g, cy, g.nz, st); }));
+  CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) { return run_row<decltype(NC)::value, true, ROW_PLAIN>(g, rx, st); }));
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- initial state
+
+__global__ void __launch_bounds__(NT) k_speckle_avg(Geom g, const float2* __restrict__ mu, float inv_scale2,
+                                                    const float* __restrict__ r_init, float* __restrict__ r0,
+                                                    float* __restrict__ max_part) {
+  float mx = 0.f;
+  for (long long v = (long long)blockIdx.x * NT + threadIdx.x; v < g.n; v += (long long)gridDim.x * NT) {
+    float val;
+    if (r_init) {
+      val = r_init[v];
+    } else {
+      float a = 0.f;
+      for (int l = 0; l < g.L; ++l) a += cabs2(mu[(long long)l * g.n + v]);
+      val = a * inv_scale2 / (float)g.L;
+    }
+    r0[v] = val;
+    mx = fmaxf(mx, val);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ float red[NT / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int i = 0; i < NT / 32; ++i) m = fmaxf(m, red[i]);
+    max_part[blockIdx.x] = m;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_broadcast_init(Geom g, const float* __restrict__ max_part, int nblk,
+                                                       float* __restrict__ r, float* __restrict__ w) {
+  __shared__ float s_floor;
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int i = 0; i < nblk; ++i) m = fmaxf(m, max_part[i]);
+    s_floor = 1e-12f * m;
+  }
+  __syncthreads();
+  const float fl = s_floor;
+  const float* r0 = r + (long long)g.L * g.n;  // staged in the prior row
+  for (long long v = (long long)blockIdx.x * NT + threadIdx.x; v < g.n; v += (long long)gridDim.x * NT) {
+    const float val = fmaxf(r0[v], fl);
+    for (int j = 0; j <= g.L; ++j) {
+      r[(long long)j * g.n + v] = val;
+      w[(long long)j * g.n + v] = val;
+    }
+  }
+}
+
+cudaError_t launch_init_state(const Geom& g, const float2* mu, float mu_scale, const float* r_init, float* r, float* w,
+                              float* max_part, int* nblk_out, cudaStream_t st) {
+  const int nb = passc_blocks(g.n);
+  float* r0 = r + (long long)g.L * g.n;
+  k_speckle_avg<<<nb, NT, 0, st>>>(g, mu, 1.0f / (mu_scale * mu_scale), r_init, r0, max_part);
+  CLAMP_TRY(cudaGetLastError());
+  k_broadcast_init<<<nb, NT, 0, st>>>(g, max_part, nb, r, w);
+  if (nblk_out) *nblk_out = nb;
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- Gaussian prior agent
+
+__global__ void __launch_bounds__(NT) k_gauss3(int nx, int ny, int nz, const float* __restrict__ in,
+                                               float* __restrict__ out, float g0, float g1) {
+  const long long n = (long long)nx * ny * nz;
+  for (long long v = (long long)blockIdx.x * NT + threadIdx.x; v < n; v += (long long)gridDim.x * NT) {
+    const int x = (int)(v % nx);
+    const int y = (int)((v / nx) % ny);
+    const int z = (int)(v / ((long long)nx * ny));
+    float acc = 0.f;
+    for (int dz = -1; dz <= 1; ++dz) {
+      const int zz = z + dz;
+      if (zz < 0 || zz >= nz) continue;
+      const float wz = dz == 0 ? g1 : g0;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int yy = y + dy;
+        if (yy < 0 || yy >= ny) continue;
+        const float wzy = wz * (dy == 0 ? g1 : g0);
+        const float* row = in + ((long long)zz * ny + yy) * nx;
+        float s = g1 * __ldg(&row[x]);
+        if (x > 0) s = fmaf(g0, __ldg(&row[x - 1]), s);
+        if (x + 1 < nx) s = fmaf(g0, __ldg(&row[x + 1]), s);
+        acc = fmaf(wzy, s, acc);
+      }
+    }
+    out[v] = acc;
+  }
+}
+
+cudaError_t launch_gauss3(int nx, int ny, int nz, const float* in, float* out, float g0, float g1, cudaStream_t st) {
+  const long long n = (long long)nx * ny * nz;
+  long long b = (n + NT - 1) / NT;
+  if (b > 152 * 16) b = 152 * 16;
+  k_gauss3<<<(unsigned)b, NT, 0, st>>>(nx, ny, nz, in, out, g0, g1);
+  return cudaGetLastError();
+}
+
+__global__ void k_nonfinite(const float* x, long long count, int* err) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) atomicOr(err, 1);
+}
+
+cudaError_t launch_nonfinite_check(const float* x, long long count, int* err, cudaStream_t st) {
+  k_nonfinite<<<152 * 4, NT, 0, st>>>(x, count, err);
+  return cudaGetLastError();
+}
+
+}  // namespace clamp

@@ -1,0 +1,89 @@
+// clamp_kernels.cuh -- launch interface of the CLAMP device passes (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace clamp {
+
+constexpr int NT = 256;   // threads per CTA in every FFT pass
+constexpr int LC = 16;    // adjacent x-columns per CTA in the y / z passes
+
+// Rows (x-lines) per CTA in the x passes.
+__host__ __device__ constexpr int rows_per_cta(int N) { return N <= 32 ? 64 : (N <= 128 ? 32 : 16); }
+
+struct Geom {
+  int nx, ny, nz, L;
+  long long n;  // nx * ny * nz
+};
+
+// Scalars shared by the passes of one forward-agent evaluation.
+struct AgentScalars {
+  float nv;        // sigma_w^2
+  float alpha;     // mean(a^2)
+  float floor;     // sigma_w^2 / alpha (noise floor of h)
+  float sc_x, sc_y, sc_z;  // 1/sqrt(nx), 1/sqrt(ny), 1/sqrt(nz) (exact, from double)
+};
+
+// Reduction partial layout in the workspace (doubles).
+struct Partials {
+  double* s1;   // [L][pz]  ||Fd||^2        (z pass)
+  double* s2;   // [L][pz]  ||a Fd||^2      (z pass)
+  double* s4;   // [L][pz]  ||a y||^2       (z pass)
+  double* s3;   // [L][px]  sum |d|^2 D     (x pass)
+  int pz, px;
+};
+
+// Twiddle tables (host-computed, uploaded once per device).
+cudaError_t upload_twiddles();
+
+// ---- forward agent (Alg. 2 steps 6-8): pass A (x, y), fused z pass, pass B (y, x)
+cudaError_t launch_agent_fft(const Geom& g, const AgentScalars& s, const float2* mu, const float* rprev,
+                             const float2* y, const float* pupil, const float* window, float4* T,
+                             float2* U, const Partials& p, cudaStream_t st);
+// gamma_l = S1 / (S2 / sigma_w^2 + S3) and the floored mu-residual per look.
+cudaError_t launch_gamma(const Geom& g, float nv, const Partials& p, float* gamma, double* mures,
+                         cudaStream_t st);
+// mean of mures[0..L) -> *out (device double)
+cudaError_t launch_mean(const double* v, int L, double* out, cudaStream_t st);
+
+// ---- pass C variants
+struct PassC {
+  const float2* d;
+  float2* mu;
+  float* r;          // [L+1][n]
+  float* w;          // [L+1][n]
+  float* wbar;       // [n] (MACE variants)
+  const float* gamma;
+  float nv, alpha, prox_var, beta;
+  float ups_look, ups_prior, rho;
+  double* part_num;  // CE partials (MACE variants)
+  double* part_den;
+  int* err;          // device error word (non-finite)
+};
+int passc_blocks(long long n);
+cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st);
+cudaError_t launch_prox_only(const Geom& g, const PassC& c, cudaStream_t st);
+cudaError_t launch_mace_only(const Geom& g, const PassC& c, cudaStream_t st);
+// CE = sqrt(sum num / sum den) over nblk partials -> *ce (and ring[idx] if ring)
+cudaError_t launch_ce_final(const double* num, const double* den, int nblk, double* ce, cudaStream_t st);
+
+// ---- plain transforms and data set-up
+cudaError_t launch_fft3(const Geom& g, const float2* in, float2* out, bool inverse, float sc_x, float sc_y,
+                        float sc_z, cudaStream_t st);
+cudaError_t launch_simulate(const Geom& g, const float* r, const float2* z, const float2* eta,
+                            const float* pupil, const float* window, float sig_w, float2* y, float sc_x,
+                            float sc_y, float sc_z, cudaStream_t st);
+// mu = A^H y * mu_scale (inverse transform of a .* y)
+cudaError_t launch_adjoint(const Geom& g, const float2* y, const float* pupil, const float* window,
+                           float mu_scale, float2* mu, float sc_x, float sc_y, float sc_z, cudaStream_t st);
+// r0 = (1/L) sum |mu|^2 / mu_scale^2 (or r_init), floored at 1e-12 max, broadcast to r, w rows 0..L
+cudaError_t launch_init_state(const Geom& g, const float2* mu, float mu_scale, const float* r_init, float* r,
+                              float* w, float* max_part, int* nblk_out, cudaStream_t st);
+
+// ---- prior agents
+cudaError_t launch_gauss3(int nx, int ny, int nz, const float* in, float* out, float g0, float g1, cudaStream_t st);
+
+// device error word helpers
+cudaError_t launch_nonfinite_check(const float* x, long long count, int* err, cudaStream_t st);
+
+}  // namespace clamp

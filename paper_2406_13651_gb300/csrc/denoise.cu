@@ -1,0 +1,232 @@
+// denoise.cu -- prior agents: 3x3x3 Gaussian smoother and the residual 3D CNN
+// H(x) = x + CNN(x) (3x3x3 convs, zero padding, ReLU on hidden layers).
+//
+// FP32 convolution: direct 3x3x3 conv as a shared-memory tiled kernel.  A CTA
+// computes a 32(x) x TY(y) x 1(z) voxel tile for CO*CG output channels; each
+// thread keeps 4 consecutive x voxels x CO channels in registers.  Input
+// channels are staged CINC at a time: the (TY+2) x 34 x 3 halo of each and the
+// matching 27 x CO*CG weights.
+#include "../../include/clamp.h"
+#include "clamp_kernels.cuh"
+#include "denoise.cuh"
+
+#include <math.h>
+#include <stdio.h>
+
+#include <string>
+
+namespace clamp {
+
+constexpr int CV_TX = 32;  // output x per CTA
+constexpr int CV_VX = 4;   // output x per thread
+
+template <int CO, int CG, int CINC>
+struct ConvCfg {
+  static constexpr int TY = NT / ((CV_TX / CV_VX) * CG);  // output rows per CTA
+  static constexpr int IX = CV_TX + 2, IY = TY + 2;
+  static constexpr int IN_FLOATS = CINC * 3 * IY * IX;
+  static constexpr int W_FLOATS = CINC * 27 * CO * CG;
+  static constexpr size_t SMEM = sizeof(float) * (IN_FLOATS + W_FLOATS);
+};
+
+// out[co][v] = bias[co] + sum_ci sum_taps W[co][ci][tap] in[ci][v + tap]  (+ resid[v]) (ReLU)
+template <int CO, int CG, int CINC, bool RELU>
+__global__ void __launch_bounds__(NT) k_conv3_f32(const float* __restrict__ in, int cin, float* __restrict__ out,
+                                                  int cout, const float* __restrict__ W,
+                                                  const float* __restrict__ bias, const float* __restrict__ resid,
+                                                  int nx, int ny, int nz) {
+  using C = ConvCfg<CO, CG, CINC>;
+  constexpr int TY = C::TY, IX = C::IX, IY = C::IY, COT = CO * CG;
+  extern __shared__ float4 smem4[];
+  float* s_in = reinterpret_cast<float*>(smem4);
+  float* s_w = s_in + C::IN_FLOATS;
+  const int tx = threadIdx.x % (CV_TX / CV_VX);
+  const int ty = (threadIdx.x / (CV_TX / CV_VX)) % TY;
+  const int cg = threadIdx.x / ((CV_TX / CV_VX) * TY);
+  const int x0 = blockIdx.x * CV_TX, y0 = blockIdx.y * TY;
+  const int ncb = (cout + COT - 1) / COT;
+  const int z = blockIdx.z / ncb, cb = blockIdx.z % ncb;
+  const long long plane = (long long)nx * ny, n = plane * nz;
+  float acc[CV_VX][CO];
+#pragma unroll
+  for (int o = 0; o < CO; ++o) {
+    const int co = cb * COT + cg * CO + o;
+    const float bv = co < cout ? __ldg(&bias[co]) : 0.f;
+#pragma unroll
+    for (int v = 0; v < CV_VX; ++v) acc[v][o] = bv;
+  }
+  for (int c0 = 0; c0 < cin; c0 += CINC) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < C::IN_FLOATS; e += NT) {
+      const int xi = e % IX;
+      const int yi = (e / IX) % IY;
+      const int zi = (e / (IX * IY)) % 3;
+      const int ci = e / (IX * IY * 3);
+      const int gx = x0 + xi - 1, gy = y0 + yi - 1, gz = z + zi - 1;
+      float v = 0.f;
+      if (c0 + ci < cin && gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+        v = __ldg(&in[(long long)(c0 + ci) * n + (long long)gz * plane + (long long)gy * nx + gx]);
+      s_in[e] = v;
+    }
+    for (int e = threadIdx.x; e < C::W_FLOATS; e += NT) {
+      const int o = e % COT;
+      const int tap = (e / COT) % 27;
+      const int ci = e / (COT * 27);
+      const int co = cb * COT + o;
+      s_w[e] = (co < cout && c0 + ci < cin) ? __ldg(&W[((long long)co * cin + c0 + ci) * 27 + tap]) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int ci = 0; ci < CINC; ++ci) {
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz) {
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy) {
+          const float* row = s_in + ((ci * 3 + dz) * IY + ty + dy) * IX + tx * CV_VX;
+          float xin[CV_VX + 2];
+#pragma unroll
+          for (int q = 0; q < CV_VX + 2; ++q) xin[q] = row[q];
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            const float* wp = s_w + (ci * 27 + dz * 9 + dy * 3 + dx) * COT + cg * CO;
+            float wv[CO];
+#pragma unroll
+            for (int o = 0; o < CO; ++o) wv[o] = wp[o];
+#pragma unroll
+            for (int v = 0; v < CV_VX; ++v)
+#pragma unroll
+              for (int o = 0; o < CO; ++o) acc[v][o] = fmaf(xin[v + dx], wv[o], acc[v][o]);
+          }
+        }
+      }
+    }
+  }
+  const int gy = y0 + ty;
+  if (gy >= ny) return;
+#pragma unroll
+  for (int o = 0; o < CO; ++o) {
+    const int co = cb * COT + cg * CO + o;
+    if (co >= cout) continue;
+#pragma unroll
+    for (int v = 0; v < CV_VX; ++v) {
+      const int gx = x0 + tx * CV_VX + v;
+      if (gx >= nx) continue;
+      const long long vox = (long long)z * plane + (long long)gy * nx + gx;
+      float r = acc[v][o];
+      if (RELU) r = fmaxf(r, 0.f);
+      if (resid) r += resid[vox];
+      out[(long long)co * n + vox] = r;
+    }
+  }
+}
+
+template <int CO, int CG, int CINC, bool RELU>
+static cudaError_t run_conv(const float* in, int cin, float* out, int cout, const float* W, const float* b,
+                            const float* resid, int nx, int ny, int nz, cudaStream_t st) {
+  using C = ConvCfg<CO, CG, CINC>;
+  auto kern = k_conv3_f32<CO, CG, CINC, RELU>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+  if (e != cudaSuccess) return e;
+  const int ncb = (cout + CO * CG - 1) / (CO * CG);
+  dim3 grid((nx + CV_TX - 1) / CV_TX, (ny + C::TY - 1) / C::TY, nz * ncb);
+  kern<<<grid, NT, C::SMEM, st>>>(in, cin, out, cout, W, b, resid, nx, ny, nz);
+  return cudaGetLastError();
+}
+
+}  // namespace clamp
+
+using namespace clamp;
+
+size_t denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz) {
+  if (!d || d->kind != 1) return 0;
+  const size_t n = (size_t)nx * ny * nz;
+  return 2 * (((size_t)d->channels * n * sizeof(float) + 255) & ~(size_t)255);
+}
+
+cudaError_t denoise_apply(const clamp_denoiser* d, const float* in, float* out, int nx, int ny, int nz, void* ws,
+                          cudaStream_t st) {
+  if (d->kind == 0) {
+    return launch_gauss3(nx, ny, nz, in, out, d->g0, d->g1, st);
+  }
+  const size_t n = (size_t)nx * ny * nz;
+  float* A = static_cast<float*>(ws);
+  float* B = A + ((((size_t)d->channels * n * sizeof(float) + 255) & ~(size_t)255) / sizeof(float));
+  const float* cur = in;
+  for (int i = 0; i < d->layers; ++i) {
+    const bool last = i == d->layers - 1;
+    float* dst = last ? out : (cur == A ? B : A);
+    cudaError_t e;
+    if (last) {
+      e = run_conv<1, 1, 8, false>(cur, d->cin[i], dst, d->cout[i], d->w[i], d->b[i], in, nx, ny, nz, st);
+    } else {
+      e = run_conv<8, 4, 8, true>(cur, d->cin[i], dst, d->cout[i], d->w[i], d->b[i], nullptr, nx, ny, nz, st);
+    }
+    if (e != cudaSuccess) return e;
+    cur = dst;
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- C ABI
+
+static thread_local std::string g_den_err;
+
+extern "C" clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser** out) {
+  if (!out) return CLAMP_EINVAL;
+  if (!(sigma > 0.f) || !isfinite(sigma)) return CLAMP_EINVAL;
+  clamp_denoiser* d = new clamp_denoiser();
+  d->kind = 0;
+  const double e = exp(-1.0 / (2.0 * (double)sigma * sigma));
+  d->g0 = (float)(e / (1.0 + 2.0 * e));
+  d->g1 = (float)(1.0 / (1.0 + 2.0 * e));
+  cudaGetDevice(&d->dev);
+  *out = d;
+  return CLAMP_OK;
+}
+
+extern "C" void clamp_denoiser_destroy(clamp_denoiser* d) {
+  if (!d) return;
+  for (float* p : d->w) cudaFree(p);
+  for (float* p : d->b) cudaFree(p);
+  for (void* p : d->w16) cudaFree(p);
+  delete d;
+}
+
+extern "C" clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channels, int32_t dtype,
+                                                  const float* weights_host, const float* biases_host,
+                                                  clamp_denoiser** out) {
+  if (!out || !weights_host || !biases_host) return CLAMP_EINVAL;
+  if (layers < 2 || layers > 64 || channels < 1 || channels > 256) return CLAMP_EINVAL;
+  if (dtype != CLAMP_DENOISER_FP32 && dtype != CLAMP_DENOISER_BF16) return CLAMP_EINVAL;
+  if (dtype == CLAMP_DENOISER_BF16) return CLAMP_EUNSUPPORTED;
+  clamp_denoiser* d = new clamp_denoiser();
+  d->kind = 1;
+  d->layers = layers;
+  d->channels = channels;
+  d->dtype = dtype;
+  cudaGetDevice(&d->dev);
+  const float* wp = weights_host;
+  const float* bp = biases_host;
+  for (int i = 0; i < layers; ++i) {
+    const int ci = i == 0 ? 1 : channels;
+    const int co = i == layers - 1 ? 1 : channels;
+    d->cin.push_back(ci);
+    d->cout.push_back(co);
+    float *wd = nullptr, *bd = nullptr;
+    const size_t wn = (size_t)co * ci * 27;
+    if (cudaMalloc(&wd, wn * sizeof(float)) != cudaSuccess || cudaMalloc(&bd, co * sizeof(float)) != cudaSuccess ||
+        cudaMemcpy(wd, wp, wn * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(bd, bp, co * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+      if (wd) cudaFree(wd);
+      if (bd) cudaFree(bd);
+      clamp_denoiser_destroy(d);
+      return CLAMP_ECUDA;
+    }
+    d->w.push_back(wd);
+    d->b.push_back(bd);
+    wp += wn;
+    bp += co;
+  }
+  *out = d;
+  return CLAMP_OK;
+}
