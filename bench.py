@@ -306,20 +306,22 @@ def main():
                                             ctypes.byref(rep), stream.cuda_stream), "clamp_reconstruct_host")
         return rep
 
-    e2e_call()  # warm-up (allocates the device cache)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_calls):
-        e2e_call()
-    torch.cuda.synchronize()
-    e2e_t = (time.perf_counter() - t0) / args.e2e_calls
-    if world > 1:
-        t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e_value = n * L * e2e_iters * world / e2e_t
+    e2e_value = None
+    if args.e2e_calls > 0:
+        e2e_call()  # warm-up (allocates the device cache)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_calls):
+            e2e_call()
+        torch.cuda.synchronize()
+        e2e_t = (time.perf_counter() - t0) / args.e2e_calls
+        if world > 1:
+            t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_t = float(t.item())
+        e2e_value = n * L * e2e_iters * world / e2e_t
     h2d = L * n * 8 + wl.nx * wl.ny * 4 + wl.nz * 4
     d2h = n * 4 + 2 * 8 * e2e_iters
 
