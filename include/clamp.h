@@ -142,6 +142,20 @@ clamp_status clamp_denoise(const clamp_denoiser* den, const float* w_prior, floa
 clamp_status clamp_mace_step(const clamp_params* p, const float* r, float* w, float* wbar,
                              double* ce_residual, void* ws, size_t ws_bytes, void* stream);
 
+/* The MACE step of clamp_mace_step without any device allocation, for callers that
+ * cannot allocate device memory themselves (an application allocator that owns the
+ * GPU's memory, or a loop that must not allocate once running).  No counterpart in
+ * the paper: same arguments and results as clamp_mace_step, minus the workspace.
+ * Its only scratch (the convergence-error partial sums) lives in a 32 KiB static
+ * device array that every GPU loading this library keeps until exit; the first call
+ * on a device looks up that array's address (so make it before any stream capture).
+ * Calls no cudaMalloc/cudaFree.  All calls share the array: calls that overlap on
+ * the GPU (other streams, other threads) race and must be serialised by the caller.
+ * Returns CLAMP_ENOMEM if the partial sums would not fit the array (never for the
+ * volumes clamp_check_params accepts: at most 1216 reduction blocks x 16 bytes). */
+clamp_status clamp_mace_step_noalloc(const clamp_params* p, const float* r, float* w, float* wbar,
+                                     double* ce_residual, void* stream);
+
 /* Prior agents. */
 clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser** out);
 /* Residual CNN H(x) = x + CNN(x), 3x3x3 convs, zero padding; layer i maps

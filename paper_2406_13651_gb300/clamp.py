@@ -31,7 +31,7 @@ EXPORTS = [
     "clamp_init", "clamp_forward_prox", "clamp_denoise", "clamp_mace_step",
     "clamp_denoiser_create_gauss", "clamp_denoiser_create_cnn", "clamp_denoiser_destroy",
     "clamp_denoise_workspace_size", "clamp_reconstruct", "clamp_reconstruct_host", "clamp_release_cache",
-    "clamp_iterate", "clamp_iterate_workspace_size",
+    "clamp_iterate", "clamp_iterate_workspace_size", "clamp_mace_step_noalloc",
 ]
 
 
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_release_cache": (V, []),
         "clamp_iterate_workspace_size": (S, [PP, P]),
         "clamp_iterate": (I, [PP, I, I, P, P, P, P, P, P, P, P, P, P, P, S, P, P]),
+        "clamp_mace_step_noalloc": (I, [PP, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
