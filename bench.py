@@ -40,56 +40,73 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="clamp", choices=["clamp", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3"])
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
 
 def workload_desc(wl):
+    den = wl.denoiser
+    if den["kind"] == "cnn":
+        prior = (f"residual CNN prior {len(den['weights'])} layers x 3x3x3 x {den['channels']} ch "
+                 f"{den.get('dtype', 'fp32').upper()}")
+    else:
+        prior = f"Gaussian prior sigma {den['sigma']}"
+    scene = "facet scene with occlusion" if wl.name == "cfg3" else "column-surface speckle scene"
+    radius = {"cfg1": 0.5, "cfg2": 0.4, "cfg3": 0.35}.get(wl.name)
+    snr = {"cfg1": 10, "cfg2": 15, "cfg3": 10}.get(wl.name)
     return {
-        "workload": f"{wl.nx}x{wl.ny}x{wl.nz} complex64, L={wl.looks} looks, column-surface speckle scene, "
-                    f"pupil R=0.4 Nyquist, Hann range window, 15 dB SNR, residual CNN prior "
-                    f"{len(wl.denoiser.get('weights', []))} layers x 3x3x3 x {wl.denoiser.get('channels')} ch FP32"
-        if wl.denoiser["kind"] == "cnn" else f"{wl.nx}x{wl.ny}x{wl.nz} complex64, L={wl.looks}, Gaussian prior",
+        "workload": f"{wl.nx}x{wl.ny}x{wl.nz} complex64, L={wl.looks} looks, {scene}, pupil R={radius} Nyquist, "
+                    f"Hann range window, {snr} dB SNR, {prior}",
         "nx": wl.nx, "ny": wl.ny, "nz": wl.nz, "looks": wl.looks,
         "voxel_looks_per_step": wl.nx * wl.ny * wl.nz * wl.looks,
         "prox_var": wl.prox_var, "noise_var": round(wl.noise_var, 8),
-        "l2": "inputs larger than L2: per-iteration working set ~0.85 GB (y, mu, r, w, scratch) vs 129 MB L2",
+        "l2": "inputs larger than L2: per-iteration working set "
+              f"{wl.nx * wl.ny * wl.nz * wl.looks * 48 / 1e9:.2f} GB (y, mu, r, w, scratch) vs 129 MB L2",
     }
 
 
 # ---------------------------------------------------------------------- oracle (CPU) sample
 
-def oracle_sample(wl, y64, looks_sample: int, slab: int, seed: int = 0):
-    """Times the FP64 oracle on a bounded sample of one CLAMP iteration: the forward
-    agents of ``looks_sample`` looks on the full volume, the prior agent on a
-    ``slab``-deep z-slab (with its receptive-field halo) and the MACE step on the full
-    volume, and scales each part to the whole iteration.  Returns (seconds per
-    iteration estimate, description)."""
+def oracle_sample(wl, looks_sample: int, slab: int, seed: int = 1):
+    """Times the FP64 oracle on a bounded sample of one CLAMP iteration: the forward agents
+    of ``looks_sample`` looks on the full volume (their data simulated by the oracle from
+    the same seeded draws), the prior agent and the MACE step on a ``slab``-deep z-slab
+    (the prior with its receptive-field halo), each part scaled to the whole iteration.
+    Returns (seconds per iteration estimate, description)."""
     import numpy as np
     from oracle import clamp_oracle as O
+    from paper_2406_13651_gb300 import inputs as I
     a = O.aperture(wl.pupil, wl.window)
-    st = O.init_state(y64, a)
     alpha = O.alpha_of(a)
-    t0 = time.perf_counter()
+    t_look = 0.0
     for l in range(looks_sample):
-        O.forward_agent(st.mu[l], st.r[l], st.w[l], y64[l], a, wl.noise_var, wl.prox_var, alpha, O.beta_k(1))
-    t_look = (time.perf_counter() - t0) / looks_sample
+        spk, eta = I.look_draws(wl, seed, l)
+        y = O.simulate_data(wl.r_true, spk[None], eta[None], a, wl.noise_var)
+        st = O.init_state(y, a)
+        t0 = time.perf_counter()
+        O.forward_agent(st.mu[0], st.r[0], st.w[0], y[0], a, wl.noise_var, wl.prox_var, alpha, O.beta_k(1))
+        t_look += time.perf_counter() - t0
+    t_look /= looks_sample
     halo = len(wl.denoiser["weights"]) if wl.denoiser["kind"] == "cnn" else 1
     z0 = wl.nz // 2 - slab // 2
-    crop = st.w[wl.looks, max(0, z0 - halo):z0 + slab + halo]
+    rng = np.random.default_rng(0)
+    crop = rng.uniform(0.01, 1.0, (min(wl.nz, slab + 2 * halo), wl.ny, wl.nx))
     t0 = time.perf_counter()
     O.apply_prior(crop, wl.denoiser)
     t_prior = (time.perf_counter() - t0) * wl.nz / slab
     ups = O.consensus_weights(wl.looks)
+    r = rng.uniform(0.01, 1.0, (wl.looks + 1, slab, wl.ny, wl.nx))
+    w = rng.uniform(0.01, 1.0, r.shape)
     t0 = time.perf_counter()
-    O.mace_update(st.r, st.w, ups, 0.5)
-    O.convergence_error(st.r, st.w, ups)
-    t_mace = time.perf_counter() - t0
+    O.mace_update(r, w, ups, 0.5)
+    O.convergence_error(r, w, ups)
+    t_mace = (time.perf_counter() - t0) * wl.nz / slab
     t_iter = wl.looks * t_look + t_prior + t_mace
-    desc = (f"{looks_sample} of {wl.looks} looks' forward agents on the full volume, prior agent on a "
-            f"{slab}-of-{wl.nz} z-slab (+{halo} halo), MACE step on the full volume; scaled to one iteration")
+    desc = (f"{looks_sample} of {wl.looks} looks' forward agents on the full volume; prior agent on a "
+            f"{slab}-of-{wl.nz} z-slab (+{halo} halo) and MACE step on a {slab}-plane slab; "
+            f"each scaled to one iteration")
     return t_iter, desc
 
 
@@ -159,32 +176,44 @@ def run_reference(args, rank, world):
     import numpy as np
     from oracle import clamp_oracle as O
     from paper_2406_13651_gb300 import inputs as I
-    wl = I.make_workload(args.workload, seed=1)
+    wl = I.make_workload(args.workload, seed=1, with_draws=False)
     a = O.aperture(wl.pupil, wl.window)
-    y64 = O.simulate_data(wl.r_true, wl.speckle, wl.noise, a, wl.noise_var).astype(np.complex64)
-    y64 = y64.astype(np.complex128)
-    del wl.speckle, wl.noise
-    st = O.init_state(y64, a)
     alpha = O.alpha_of(a)
     ups = O.consensus_weights(wl.looks)
     halo = len(wl.denoiser["weights"]) if wl.denoiser["kind"] == "cnn" else 1
     slab = 2
+    rng = np.random.default_rng(0)
+    w_prior = rng.uniform(0.01, 1.0, (wl.nz, wl.ny, wl.nx))
+    r_s = rng.uniform(0.01, 1.0, (wl.looks + 1, slab, wl.ny, wl.nx))
+    w_s = rng.uniform(0.01, 1.0, r_s.shape)
+    look_cache = {}
+
+    def look_state(l):
+        if l not in look_cache:
+            look_cache.clear()
+            spk, eta = I.look_draws(wl, 1, l)
+            y = O.simulate_data(wl.r_true, spk[None], eta[None], a, wl.noise_var)
+            look_cache[l] = (y, O.init_state(y, a))
+        return look_cache[l]
+
     kinds = ["agent", "prior", "mace"]
     times = {k: [] for k in kinds}
 
     def unit(i):
         kind = kinds[i % 3]
-        t0 = time.perf_counter()
         if kind == "agent":
-            l = (i // 3) % wl.looks
-            O.forward_agent(st.mu[l], st.r[l], st.w[l], y64[l], a, wl.noise_var, wl.prox_var, alpha, O.beta_k(1))
+            y, st = look_state((i // 3) % wl.looks)   # data set-up is not timed
+            t0 = time.perf_counter()
+            O.forward_agent(st.mu[0], st.r[0], st.w[0], y[0], a, wl.noise_var, wl.prox_var, alpha, O.beta_k(1))
         elif kind == "prior":
             z0 = ((i // 3) * slab) % wl.nz
             lo, hi = max(0, z0 - halo), min(wl.nz, z0 + slab + halo)
-            O.apply_prior(st.w[wl.looks, lo:hi], wl.denoiser)
+            t0 = time.perf_counter()
+            O.apply_prior(w_prior[lo:hi], wl.denoiser)
         else:
-            O.mace_update(st.r, st.w, ups, 0.5)
-            O.convergence_error(st.r, st.w, ups)
+            t0 = time.perf_counter()
+            O.mace_update(r_s, w_s, ups, 0.5)
+            O.convergence_error(r_s, w_s, ups)
         return kind, time.perf_counter() - t0
 
     for i in range(max(args.warmup, 0) and 3):
@@ -195,12 +224,13 @@ def run_reference(args, rank, world):
         times[kind].append(t)
         t_all += t
     mean = {k: (sum(v) / len(v) if v else 0.0) for k, v in times.items()}
-    t_iter = wl.looks * mean["agent"] + (wl.nz / slab) * mean["prior"] + mean["mace"]
+    t_iter = wl.looks * mean["agent"] + (wl.nz / slab) * (mean["prior"] + mean["mace"])
     value = wl.nx * wl.ny * wl.nz * wl.looks / t_iter
     cores = oracle_threads()
     desc = (f"each step one unit of an iteration, round robin: one look's forward agent on the full "
             f"{wl.nx}x{wl.ny}x{wl.nz} volume, the prior agent on a {slab}-plane z-slab (+{halo} halo), or the "
-            f"MACE step; iteration time = {wl.looks} x agent + {wl.nz // slab} x prior slab + MACE")
+            f"MACE step on a {slab}-plane slab; iteration time = {wl.looks} x agent + "
+            f"{wl.nz // slab} x (prior slab + MACE slab)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_all / max(args.steps, 1) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -238,15 +268,20 @@ def main():
     stream = torch.cuda.current_stream()
 
     # ---- inputs: seeded scene and draws on the host, data simulated on the device
-    wl = I.make_workload(args.workload, seed=1 + rank)
+    seed = 1 + rank
+    wl = I.make_workload(args.workload, seed=seed, with_draws=False)
     L, n = wl.looks, wl.nx * wl.ny * wl.nz
     p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var)
+    p1 = C.make_params(wl.nx, wl.ny, wl.nz, 1, wl.noise_var, wl.prox_var)
     pupil = torch.from_numpy(wl.pupil).to(dev)
     window = torch.from_numpy(wl.window).to(dev)
     r_true = torch.from_numpy(wl.r_true.astype(np.float32)).to(dev)
-    spk = torch.from_numpy(wl.speckle.astype(np.complex64)).to(dev)
-    eta = torch.from_numpy(wl.noise.astype(np.complex64)).to(dev)
-    y = C.simulate(p, r_true, spk, eta, pupil, window)
+    y = torch.empty((L, wl.nz, wl.ny, wl.nx), dtype=torch.complex64, device=dev)
+    for l in range(L):   # seeded draws per look on the host, data simulated on the device
+        spk_h, eta_h = I.look_draws(wl, seed, l)
+        spk = torch.from_numpy(spk_h.astype(np.complex64)).to(dev)
+        eta = torch.from_numpy(eta_h.astype(np.complex64)).to(dev)
+        C.simulate(p1, r_true, spk[None], eta[None], pupil, window, out=y[l:l + 1])
     del spk, eta
     y_host = None
     den = C.Denoiser.from_desc(wl.denoiser)
@@ -347,11 +382,28 @@ def main():
         macs = 27 * (ch + (nl - 2) * ch * ch + ch)
         flops = 2.0 * macs * n
         cnn_tflops = flops / prior / 1e12
-        roofline = {"bound": "alu", "kernel": "k_conv3_f32 (all layers of the prior agent)",
-                    "achieved": cnn_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": cnn_tflops / fp32_peak, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
-                    "algorithmic": f"{macs} MAC/voxel x {n} voxels per launch set"}
+        bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+        tensor_path = wl.nx % 128 == 0 and ch in (16, 32, 48) and wl.ny % 2 == 0 and wl.nz % 2 == 0
+        if wl.denoiser.get("dtype", "fp32") == "bf16":
+            roofline = {"bound": "tensor", "kernel": "k_conv3_tc<BF16> (+ SIMT first layer): the prior agent",
+                        "achieved": cnn_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
+                        "frac": cnn_tflops / bf16_peak, "traffic": None,
+                        "peak_source": "measured bf16_tflops_sustained",
+                        "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
+        elif tensor_path:
+            tf32x3_peak = bf16_peak * (1.1 / 2.25) / 3.0
+            roofline = {"bound": "tensor", "kernel": "k_conv3_tc<TF32x3> (+ SIMT first layer): the prior agent",
+                        "achieved": cnn_tflops, "peak": tf32x3_peak, "unit": "TFLOP/s",
+                        "frac": cnn_tflops / tf32x3_peak, "traffic": None,
+                        "peak_source": "measured bf16_tflops_sustained x nominal TF32/BF16 ratio (1.1/2.25), "
+                                       "/3 for the three TF32 MMAs per FP32 product",
+                        "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
+        else:
+            roofline = {"bound": "alu", "kernel": "k_conv3_f32 (all layers of the prior agent)",
+                        "achieved": cnn_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                        "frac": cnn_tflops / fp32_peak, "traffic": None,
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                        "algorithmic": f"{macs} MAC/voxel x {n} voxels per launch set"}
     else:
         roofline = None
     # forward-agent FFT + prox + Mann path: 136 B per voxel-look (two HBM passes per 3D FFT)
@@ -366,10 +418,7 @@ def main():
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        from oracle import clamp_oracle as O
-        a = O.aperture(wl.pupil, wl.window)
-        y64 = y.cpu().numpy().astype(np.complex128)
-        t_it, desc = oracle_sample(wl, y64, 2, max(4, wl.nz // 8))
+        t_it, desc = oracle_sample(wl, 2, max(4, wl.nz // 16), seed=seed)
         cpu = {"value": n * L / t_it, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": desc}
 
     launches_per_iter = 5 + 1 + (len(wl.denoiser.get("weights", [])) if wl.denoiser["kind"] == "cnn" else 1) + 1 + 1

@@ -161,11 +161,27 @@ clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser** out);
 /* Residual CNN H(x) = x + CNN(x), 3x3x3 convs, zero padding; layer i maps
  * c_in -> c_out (1 -> C -> ... -> C -> 1), ReLU after every layer but the last.
  * weights_host: all layers' [c_out][c_in][3][3][3] float32 concatenated;
- * biases_host: all layers' [c_out] concatenated.  dtype: CLAMP_DENOISER_FP32 or _BF16. */
+ * biases_host: all layers' [c_out] concatenated.  dtype: CLAMP_DENOISER_FP32 or _BF16.
+ * BF16: weights and every layer's input are rounded to bfloat16, products accumulate in
+ * FP32 on the tensor cores; needs channels in {16, 32, 48, 64} and volumes with
+ * nx % 128 == 0, ny % 4 == 0, nz % 2 == 0 (else CLAMP_EUNSUPPORTED at use).
+ * FP32: on the tensor cores through a TF32x3 split when channels are in {16, 32, 48} and
+ * nx % 128 == 0, ny % 2 == 0, nz % 2 == 0; otherwise on FP32 CUDA cores. */
 clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channels, int32_t dtype,
                                        const float* weights_host, const float* biases_host,
                                        clamp_denoiser** out);
 void clamp_denoiser_destroy(clamp_denoiser* den);
+
+/* Tensor-core building block check: D[128][n] = A[128][k] B[n][k]^T with A, B BF16
+ * (row-major, k contiguous) and D FP32, on one CTA through tcgen05 MMAs with TMEM
+ * accumulators -- the same descriptor conventions the BF16 CNN prior uses.
+ * 16 <= n, k <= 256, multiples of 16.  Device pointers. */
+clamp_status clamp_tc_gemm_bf16(int32_t n, int32_t k, const void* a, const void* b, float* d, void* stream);
+
+/* Same with FP32 A, B through the TF32x3 split the FP32 CNN prior uses
+ * (hi*hi + hi*lo + lo*hi on kind::tf32).  16 <= n <= 256 (multiple of 16), 8 <= k <= 192
+ * (multiple of 8); CLAMP_EINVAL if the operands exceed shared memory. */
+clamp_status clamp_tc_gemm_tf32x3(int32_t n, int32_t k, const float* a, const float* b, float* d, void* stream);
 size_t clamp_denoise_workspace_size(const clamp_denoiser* den, int32_t nx, int32_t ny, int32_t nz);
 
 /* Scratch bytes clamp_iterate needs (forward-agent scratch plus the denoiser's). */

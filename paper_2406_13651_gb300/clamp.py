@@ -32,6 +32,7 @@ EXPORTS = [
     "clamp_denoiser_create_gauss", "clamp_denoiser_create_cnn", "clamp_denoiser_destroy",
     "clamp_denoise_workspace_size", "clamp_reconstruct", "clamp_reconstruct_host", "clamp_release_cache",
     "clamp_iterate", "clamp_iterate_workspace_size", "clamp_mace_step_noalloc",
+    "clamp_tc_gemm_bf16", "clamp_tc_gemm_tf32x3",
 ]
 
 
@@ -94,6 +95,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_iterate_workspace_size": (S, [PP, P]),
         "clamp_iterate": (I, [PP, I, I, P, P, P, P, P, P, P, P, P, P, P, S, P, P]),
         "clamp_mace_step_noalloc": (I, [PP, P, P, P, P, P]),
+        "clamp_tc_gemm_bf16": (I, [I, I, P, P, P, P]),
+        "clamp_tc_gemm_tf32x3": (I, [I, I, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -201,9 +204,9 @@ def fft3(x, inverse: bool = False, out=None, stream=None):
     return out
 
 
-def simulate(p: Params, r, speckle, noise, pupil, window, stream=None):
+def simulate(p: Params, r, speckle, noise, pupil, window, stream=None, out=None):
     import torch
-    y = torch.empty_like(speckle)
+    y = torch.empty_like(speckle) if out is None else out
     _check(load().clamp_simulate(ctypes.byref(p), _ptr(r), _ptr(speckle), _ptr(noise), _ptr(pupil), _ptr(window),
                                  _ptr(y), _stream(stream)), "clamp_simulate")
     return y

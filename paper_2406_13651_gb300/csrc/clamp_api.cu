@@ -370,10 +370,13 @@ extern "C" clamp_status clamp_denoise(const clamp_denoiser* den, const float* w_
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096)
     return fail(CLAMP_EINVAL, "denoiser volume %dx%dx%d out of range", nx, ny, nz);
   API_TRY(need_ptrs({w_prior, r_prior}, "clamp_denoise"));
+  if (!denoise_supports(den, nx, ny, nz))
+    return fail(CLAMP_EUNSUPPORTED, "BF16 CNN prior needs nx %% 128 == 0, ny %% 4 == 0, nz %% 2 == 0 (got %dx%dx%d)",
+                nx, ny, nz);
   const size_t need = denoise_ws_bytes(den, nx, ny, nz);
   if (need) API_TRY(check_ws(ws, ws_bytes, need, "clamp_denoise"));
   API_TRY(ensure_device());
-  API_CUDA(denoise_apply(den, w_prior, r_prior, nx, ny, nz, ws, (cudaStream_t)stream), "denoiser");
+  API_CUDA(denoise_apply(den, w_prior, r_prior, nx, ny, nz, ws, nullptr, (cudaStream_t)stream), "denoiser");
   return CLAMP_OK;
 }
 
@@ -407,7 +410,7 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
     if (mu_out) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_out + it, st), "mu residual");
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 1], st), "event");
     API_CUDA(denoise_apply(den, w + (long long)p->looks * n, r + (long long)p->looks * n, p->nx, p->ny, p->nz, dws,
-                           st),
+                           at<int>(ws, al.err), st),
              "denoiser");
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 2], st), "event");
     PassC c = passc_args(p, d, al, ws, mu, r, w, wbar, k);
@@ -424,6 +427,8 @@ extern "C" clamp_status clamp_iterate(const clamp_params* p, int32_t k_first, in
                                       size_t ws_bytes, void* const* events, void* stream) {
   API_TRY(clamp_check_params(p));
   if (!den) return fail(CLAMP_EINVAL, "clamp_iterate: denoiser is NULL");
+  if (!denoise_supports(den, p->nx, p->ny, p->nz))
+    return fail(CLAMP_EUNSUPPORTED, "clamp_iterate: the prior agent does not support this volume");
   if (k_first < 1 || iters < 0) return fail(CLAMP_EINVAL, "clamp_iterate: k_first=%d must be >= 1, iters >= 0",
                                             k_first);
   API_TRY(need_ptrs({y, pupil, window, mu, r, w, wbar}, "clamp_iterate"));
@@ -476,6 +481,7 @@ static clamp_status reconstruct_impl(const clamp_params* p, const float* y, cons
                "residual readback");
       API_CUDA(cudaMemcpyAsync(&herr, at<int>(aws, al.err), sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
       API_CUDA(cudaStreamSynchronize(st), "residual readback");
+      if (herr & 2) return fail(CLAMP_ETIMEOUT, "a bounded tensor-core wait gave up at or before iteration %d", k);
       if (herr) return fail(CLAMP_ENONFINITE, "non-finite value in the state at or before iteration %d", k);
       for (int i = synced_upto; i < done; ++i) {
         if (p->tol > 0 && ce_h[i] <= p->tol) {
@@ -510,6 +516,8 @@ extern "C" clamp_status clamp_reconstruct(const clamp_params* p, const float* y,
                                           void* stream) {
   API_TRY(clamp_check_params(p));
   if (!den) return fail(CLAMP_EINVAL, "clamp_reconstruct: denoiser is NULL");
+  if (!denoise_supports(den, p->nx, p->ny, p->nz))
+    return fail(CLAMP_EUNSUPPORTED, "clamp_reconstruct: the prior agent does not support this volume");
   API_TRY(need_ptrs({y, pupil, window, r_out}, "clamp_reconstruct"));
   API_TRY(ensure_device());
   cudaStream_t st = (cudaStream_t)stream;
@@ -561,6 +569,8 @@ extern "C" clamp_status clamp_reconstruct_host(const clamp_params* p, const floa
                                                void* stream) {
   API_TRY(clamp_check_params(p));
   if (!den) return fail(CLAMP_EINVAL, "clamp_reconstruct_host: denoiser is NULL");
+  if (!denoise_supports(den, p->nx, p->ny, p->nz))
+    return fail(CLAMP_EUNSUPPORTED, "clamp_reconstruct_host: the prior agent does not support this volume");
   API_TRY(need_ptrs({y_host, pupil_host, window_host, r_out_host}, "clamp_reconstruct_host"));
   API_TRY(ensure_device());
   cudaStream_t st = (cudaStream_t)stream;

@@ -133,21 +133,114 @@ static cudaError_t run_conv(const float* in, int cin, float* out, int cout, cons
   return cudaGetLastError();
 }
 
+// Single-output-channel layer (the CNN's last layer, SIMT fallback): out[v] = b + sum_ci sum_taps
+// W[ci][tap] in[ci][v+tap] (+ resid[v]).  A thread computes a 2(x) x 2(y) block at one z, so each
+// input value it loads from shared memory feeds up to 4 accumulators per tap plane.
+constexpr int C1_TX = 32, C1_TY = 32, C1_CINC = 4;
+constexpr int C1_IX = C1_TX + 2, C1_IY = C1_TY + 2;
+constexpr size_t C1_SMEM = sizeof(float) * (C1_CINC * 3 * C1_IY * C1_IX + C1_CINC * 27);
+
+__global__ void __launch_bounds__(NT) k_conv3_c1(const float* __restrict__ in, int cin, float* __restrict__ out,
+                                                 const float* __restrict__ W, const float* __restrict__ bias,
+                                                 const float* __restrict__ resid, int nx, int ny, int nz) {
+  extern __shared__ float4 smem4[];
+  float* s_in = reinterpret_cast<float*>(smem4);
+  float* s_w = s_in + C1_CINC * 3 * C1_IY * C1_IX;
+  const int tx = threadIdx.x % (C1_TX / 2), ty = threadIdx.x / (C1_TX / 2);  // 16 x 16 threads
+  const int x0 = blockIdx.x * C1_TX, y0 = blockIdx.y * C1_TY, z = blockIdx.z;
+  const long long plane = (long long)nx * ny, n = plane * nz;
+  float acc[2][2];
+  const float b0 = __ldg(&bias[0]);
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) acc[a][c] = b0;
+  for (int c0 = 0; c0 < cin; c0 += C1_CINC) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < C1_CINC * 3 * C1_IY * C1_IX; e += NT) {
+      const int xi = e % C1_IX;
+      const int yi = (e / C1_IX) % C1_IY;
+      const int zi = (e / (C1_IX * C1_IY)) % 3;
+      const int ci = e / (C1_IX * C1_IY * 3);
+      const int gx = x0 + xi - 1, gy = y0 + yi - 1, gz = z + zi - 1;
+      float v = 0.f;
+      if (c0 + ci < cin && gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+        v = __ldg(&in[(long long)(c0 + ci) * n + (long long)gz * plane + (long long)gy * nx + gx]);
+      s_in[e] = v;
+    }
+    for (int e = threadIdx.x; e < C1_CINC * 27; e += NT)
+      s_w[e] = (c0 + e / 27 < cin) ? __ldg(&W[(long long)c0 * 27 + e]) : 0.f;
+    __syncthreads();
+#pragma unroll 1
+    for (int ci = 0; ci < C1_CINC; ++ci) {
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz) {
+        float xin[4][4];
+        const float* base = s_in + ((ci * 3 + dz) * C1_IY + ty * 2) * C1_IX + tx * 2;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) xin[a][c] = base[a * C1_IX + c];
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            const float wv = s_w[ci * 27 + dz * 9 + dy * 3 + dx];
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+              for (int c = 0; c < 2; ++c) acc[a][c] = fmaf(xin[a + dy][c + dx], wv, acc[a][c]);
+          }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 2; ++a) {
+    const int gy = y0 + ty * 2 + a;
+    if (gy >= ny) continue;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int gx = x0 + tx * 2 + c;
+      if (gx >= nx) continue;
+      const long long vox = (long long)z * plane + (long long)gy * nx + gx;
+      out[vox] = acc[a][c] + (resid ? resid[vox] : 0.f);
+    }
+  }
+}
+
+static cudaError_t run_conv_c1(const float* in, int cin, float* out, const float* W, const float* b,
+                               const float* resid, int nx, int ny, int nz, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_c1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C1_SMEM);
+  if (e != cudaSuccess) return e;
+  dim3 grid((nx + C1_TX - 1) / C1_TX, (ny + C1_TY - 1) / C1_TY, nz);
+  k_conv3_c1<<<grid, NT, C1_SMEM, st>>>(in, cin, out, W, b, resid, nx, ny, nz);
+  return cudaGetLastError();
+}
+
 }  // namespace clamp
 
 using namespace clamp;
 
 size_t denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz) {
   if (!d || d->kind != 1) return 0;
+  if (d->dtype == CLAMP_DENOISER_BF16) return tc_denoise_ws_bytes(d, nx, ny, nz);
   const size_t n = (size_t)nx * ny * nz;
   return 2 * (((size_t)d->channels * n * sizeof(float) + 255) & ~(size_t)255);
 }
 
+bool denoise_supports(const clamp_denoiser* d, int nx, int ny, int nz) {
+  if (d->kind == 1 && d->dtype == CLAMP_DENOISER_BF16) return tc_denoiser_supports(d, nx, ny, nz);
+  return true;
+}
+
 cudaError_t denoise_apply(const clamp_denoiser* d, const float* in, float* out, int nx, int ny, int nz, void* ws,
-                          cudaStream_t st) {
+                          int* err, cudaStream_t st) {
   if (d->kind == 0) {
     return launch_gauss3(nx, ny, nz, in, out, d->g0, d->g1, st);
   }
+  // tensor-core path (BF16, or FP32 through TF32x3) when the volume fits its tiling
+  if (tc_denoiser_supports(d, nx, ny, nz)) return tc_denoise_apply(d, in, out, nx, ny, nz, ws, err, st);
+  if (d->dtype == CLAMP_DENOISER_BF16) return cudaErrorInvalidValue;
   const size_t n = (size_t)nx * ny * nz;
   float* A = static_cast<float*>(ws);
   float* B = A + ((((size_t)d->channels * n * sizeof(float) + 255) & ~(size_t)255) / sizeof(float));
@@ -157,7 +250,9 @@ cudaError_t denoise_apply(const clamp_denoiser* d, const float* in, float* out, 
     float* dst = last ? out : (cur == A ? B : A);
     cudaError_t e;
     if (last) {
-      e = run_conv<1, 1, 8, false>(cur, d->cin[i], dst, d->cout[i], d->w[i], d->b[i], in, nx, ny, nz, st);
+      e = run_conv_c1(cur, d->cin[i], dst, d->w[i], d->b[i], in, nx, ny, nz, st);
+    } else if (d->cin[i] == 1) {
+      e = run_conv<8, 4, 1, true>(cur, 1, dst, d->cout[i], d->w[i], d->b[i], nullptr, nx, ny, nz, st);
     } else {
       e = run_conv<8, 4, 8, true>(cur, d->cin[i], dst, d->cout[i], d->w[i], d->b[i], nullptr, nx, ny, nz, st);
     }
@@ -186,9 +281,12 @@ extern "C" clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser*
 
 extern "C" void clamp_denoiser_destroy(clamp_denoiser* d) {
   if (!d) return;
-  for (float* p : d->w) cudaFree(p);
-  for (float* p : d->b) cudaFree(p);
-  for (void* p : d->w16) cudaFree(p);
+  for (float* p : d->w)
+    if (p) cudaFree(p);
+  for (float* p : d->b)
+    if (p) cudaFree(p);
+  for (void* p : d->w16)
+    if (p) cudaFree(p);
   delete d;
 }
 
@@ -198,7 +296,7 @@ extern "C" clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channe
   if (!out || !weights_host || !biases_host) return CLAMP_EINVAL;
   if (layers < 2 || layers > 64 || channels < 1 || channels > 256) return CLAMP_EINVAL;
   if (dtype != CLAMP_DENOISER_FP32 && dtype != CLAMP_DENOISER_BF16) return CLAMP_EINVAL;
-  if (dtype == CLAMP_DENOISER_BF16) return CLAMP_EUNSUPPORTED;
+  if (dtype == CLAMP_DENOISER_BF16 && (channels % 16 || channels > 64)) return CLAMP_EUNSUPPORTED;
   clamp_denoiser* d = new clamp_denoiser();
   d->kind = 1;
   d->layers = layers;
@@ -207,23 +305,37 @@ extern "C" clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channe
   cudaGetDevice(&d->dev);
   const float* wp = weights_host;
   const float* bp = biases_host;
+  auto upload = [](void** dst, const void* src, size_t bytes) {
+    return cudaMalloc(dst, bytes) == cudaSuccess && cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+  };
   for (int i = 0; i < layers; ++i) {
     const int ci = i == 0 ? 1 : channels;
     const int co = i == layers - 1 ? 1 : channels;
     d->cin.push_back(ci);
     d->cout.push_back(co);
-    float *wd = nullptr, *bd = nullptr;
     const size_t wn = (size_t)co * ci * 27;
-    if (cudaMalloc(&wd, wn * sizeof(float)) != cudaSuccess || cudaMalloc(&bd, co * sizeof(float)) != cudaSuccess ||
-        cudaMemcpy(wd, wp, wn * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(bd, bp, co * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
-      if (wd) cudaFree(wd);
-      if (bd) cudaFree(bd);
+    void *wd = nullptr, *bd = nullptr, *w16 = nullptr;
+    bool ok = upload(&bd, bp, co * sizeof(float));
+    const bool bf = dtype == CLAMP_DENOISER_BF16;
+    if (!bf || i == 0) {
+      // float weights: every FP32 layer (SIMT fallback), and the first layer (SIMT) of both kinds
+      std::vector<float> wf(wp, wp + wn);
+      if (bf)
+        for (auto& v : wf) v = clamp::bf16_round_value(v);
+      ok = ok && upload(&wd, wf.data(), wn * sizeof(float));
+    }
+    const int chunk = bf ? 16 : 8;
+    if (i > 0 && ci % chunk == 0) {
+      const std::vector<uint8_t> pk = clamp::pack_tc_weights(wp, ci, co, co == 1 ? 16 : co, bf);
+      ok = ok && upload(&w16, pk.data(), pk.size());
+    }
+    d->w.push_back(static_cast<float*>(wd));
+    d->b.push_back(static_cast<float*>(bd));
+    d->w16.push_back(w16);
+    if (!ok) {
       clamp_denoiser_destroy(d);
       return CLAMP_ECUDA;
     }
-    d->w.push_back(wd);
-    d->b.push_back(bd);
     wp += wn;
     bp += co;
   }

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <stdint.h>
+
 #include <vector>
 
 struct clamp_denoiser {
@@ -13,9 +15,23 @@ struct clamp_denoiser {
   std::vector<int> cin, cout;
   std::vector<float*> w;      // per layer, device, [cout][cin][27]
   std::vector<float*> b;      // per layer, device, [cout]
-  std::vector<void*> w16;     // per layer, device, bf16 packed weights (dtype BF16)
+  std::vector<void*> w16;     // per layer, device, tensor-core packed weights (layers >= 1)
 };
 
 size_t denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz);
+// True if the denoiser can run on an nx x ny x nz volume (the BF16 CNN runs only on the
+// tensor cores: nx % 128 == 0, ny % 4 == 0, nz % 2 == 0, 16..64 channels in steps of 16).
+bool denoise_supports(const clamp_denoiser* d, int nx, int ny, int nz);
+// err: optional device error word (bit 2: a bounded tensor-core wait gave up).
 cudaError_t denoise_apply(const clamp_denoiser* d, const float* in, float* out, int nx, int ny, int nz, void* ws,
-                          cudaStream_t st);
+                          int* err, cudaStream_t st);
+
+namespace clamp {
+// Tensor-core CNN prior (BF16, or FP32 through the TF32x3 split), implemented in tc_conv.cu.
+bool tc_denoiser_supports(const clamp_denoiser* d, int nx, int ny, int nz);
+size_t tc_denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz);
+cudaError_t tc_denoise_apply(const clamp_denoiser* d, const float* in, float* out, int nx, int ny, int nz, void* ws,
+                             int* err, cudaStream_t st);
+std::vector<uint8_t> pack_tc_weights(const float* W, int cin, int cout, int npad, bool bf16);
+float bf16_round_value(float f);
+}  // namespace clamp

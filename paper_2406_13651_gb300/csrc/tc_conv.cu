@@ -1,0 +1,564 @@
+// tc_conv.cu -- 3x3x3 convolutions of the CNN prior on the 5th-generation tensor cores (tcgen05).
+//
+// Implicit GEMM: for one output tile of 128 consecutive x voxels (M = 128) and all
+// output channels (N), K runs over 27 taps x input channels.  A CTA computes TY x TZ
+// such tiles.  For each chunk of input channels it stages the zero-padded input halo
+// (130 x (TY+2) x (TZ+2) voxels, channels-last in 16-byte channel groups) and the
+// chunk's weights in shared memory in the no-swizzle K-major core-matrix layout; a tap
+// is then only an offset of the A descriptor's start address.  One thread issues the
+// chunk's MMAs into FP32 accumulators in TMEM and commits them to an mbarrier (a
+// warp-wide elected issue measured slower here); the
+// epilogue reads TMEM (tcgen05.ld), adds the bias, applies ReLU and writes the next
+// layer's activations, or (last layer) FP32 plus the residual input.
+//
+// Two operand kinds:
+//  * BF16: kind::f16 with BF16 operands, 16 channels per chunk (the BF16 prior).
+//  * TF32x3: kind::tf32 with every FP32 operand split as hi + lo, both rounded to nearest
+//    TF32 (hi = RN(x), lo = RN(x - hi)); hi*hi + hi*lo + lo*hi keeps each product to
+//    about 2^-21 relative with zero-mean residuals, so the FP32 prior keeps FP32 accuracy.
+//    (Truncating hi instead biases lo to the sign of x, and the dropped lo*lo terms then
+//    add up across the 27 x Cin products of an output.)
+//
+// Activation layouts: BF16 [C/8][nz][ny][nx][8], FP32 [C/4][nz][ny][nx][4]: 16 bytes per
+// voxel per channel group.
+#include "../../include/clamp.h"
+#include "clamp_kernels.cuh"
+#include "denoise.cuh"
+#include "tc_core.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cstring>
+#include <vector>
+
+namespace clamp {
+
+constexpr int TCX = 128, TC_HX = TCX + 2, TC_NT = 256;
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__host__ __device__ constexpr int pow2_cols(int c) {
+  return c <= 32 ? 32 : c <= 64 ? 64 : c <= 128 ? 128 : c <= 256 ? 256 : 512;
+}
+
+enum TcKindId { TC_BF16 = 0, TC_TF32X3 = 1 };
+
+template <int KIND>
+struct TcKind;
+template <>
+struct TcKind<TC_BF16> {
+  static constexpr int EPV = 8;      // channels per 16-byte group
+  static constexpr int SPLIT = 1;    // operand copies (hi only)
+  static constexpr int TY = 4, TZ = 2;
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  }
+};
+template <>
+struct TcKind<TC_TF32X3> {
+  static constexpr int EPV = 4;
+  static constexpr int SPLIT = 2;    // hi and lo copies
+  static constexpr int TY = 2, TZ = 2;
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+  }
+};
+
+__device__ __forceinline__ void mma_kind(int kind, uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (kind == TC_BF16) {
+    tc::mma_bf16(d, a, b, idesc, acc);
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+template <int KIND, int CIN, int NPAD>
+struct TcCfg {
+  using K = TcKind<KIND>;
+  static constexpr int TY = K::TY, TZ = K::TZ, MT = TY * TZ, HY = TY + 2, HZ = TZ + 2;
+  static constexpr int CH = 2 * K::EPV;               // input channels per chunk (one MMA K step)
+  static constexpr int CHUNKS = CIN / CH;
+  static constexpr int HALO_VEC = 2 * HZ * HY * TC_HX;  // 16-byte vectors per chunk, per split
+  static constexpr int W_VEC = 27 * 2 * NPAD;
+  static constexpr int TMEM_COLS = pow2_cols(MT * NPAD);
+  static constexpr size_t SMEM = 1024 + 16 * (size_t)K::SPLIT * (HALO_VEC + W_VEC) + 64;
+  static_assert(CIN % CH == 0 && NPAD % 16 == 0 && MT * NPAD <= 512, "tile");
+  static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  const __nv_bfloat16 lo = __float2bfloat16_rn(a), hi = __float2bfloat16_rn(b);
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+// Round to the nearest TF32 value (10 explicit mantissa bits), ties to even.
+__device__ __forceinline__ float tf32_rn(float x) {
+  uint32_t u = __float_as_uint(x);
+  u += 0xFFFu + ((u >> 13) & 1u);
+  return __uint_as_float(u & 0xFFFFE000u);
+}
+
+// 16-byte asynchronous global -> shared copy; with valid == false nothing is read and the
+// destination is zero-filled.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_addr(smem_dst)), "l"(gsrc),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
+template <int KIND, int CIN, int NPAD, bool LAST>
+__global__ void __launch_bounds__(TC_NT, 1)
+    k_conv3_tc(const uint4* __restrict__ in, const uint4* __restrict__ wpk, const float* __restrict__ bias,
+               uint4* __restrict__ out_act, float* __restrict__ out_f32, const float* __restrict__ resid, int nx,
+               int ny, int nz, int* err) {
+  using Cfg = TcCfg<KIND, CIN, NPAD>;
+  using Kd = TcKind<KIND>;
+  constexpr int TY = Cfg::TY, HY = Cfg::HY, HZ = Cfg::HZ, MT = Cfg::MT;
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint4* s_halo = reinterpret_cast<uint4*>(base);              // [SPLIT][2][HZ][HY][HX]
+  uint4* s_w = s_halo + Kd::SPLIT * Cfg::HALO_VEC;             // [SPLIT][27][2][NPAD]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_w + Kd::SPLIT * Cfg::W_VEC);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * TCX, y0 = blockIdx.y * TY, z0 = blockIdx.z * Cfg::TZ;
+  const long long plane = (long long)nx * ny, n = plane * nz;
+
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    *abort_flag = 0;
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, Cfg::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const uint32_t idesc = Kd::idesc(128, NPAD);
+  const uint32_t halo_s = tc::smem_addr(s_halo), w_s = tc::smem_addr(s_w);
+  constexpr uint32_t LBO_A = HZ * HY * TC_HX * 16;  // channel group 0 -> 1
+  constexpr uint32_t LBO_B = NPAD * 16;
+  constexpr uint32_t SPLIT_A = 16u * Cfg::HALO_VEC, SPLIT_B = 16u * Cfg::W_VEC;  // hi -> lo copies
+  bool aborted = false;
+  uint32_t fail_parity = 0;
+
+  // Chunk staging: cp.async 16-byte copies (zero-fill outside the volume), all in flight
+  // at once.  TF32x3 lands the raw FP32 halo in the lo copy and splits it in place.
+  uint4* s_raw = s_halo + (Kd::SPLIT - 1) * Cfg::HALO_VEC;
+  for (int c = 0; c < Cfg::CHUNKS; ++c) {
+    for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
+      const int xr = e % TC_HX;
+      int t = e / TC_HX;
+      const int yr = t % HY;
+      t /= HY;
+      const int zr = t % HZ, cg = t / HZ;
+      const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z0 + zr - 1;
+      const bool inb = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+      const uint4* src = inb ? &in[(long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx + gx] : in;
+      cp_async16(&s_raw[e], src, inb);
+    }
+    for (int s = 0; s < Kd::SPLIT; ++s) {
+      const uint4* wsrc = wpk + ((long long)s * Cfg::CHUNKS + c) * Cfg::W_VEC;
+      for (int e = tid; e < Cfg::W_VEC; e += TC_NT) cp_async16(&s_w[s * Cfg::W_VEC + e], &wsrc[e], true);
+    }
+    cp_async_wait_all();
+    if constexpr (KIND == TC_TF32X3) {
+      __syncthreads();
+      float4* hi = reinterpret_cast<float4*>(s_halo);
+      float4* lo = reinterpret_cast<float4*>(s_raw);
+      for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
+        const float4 f = lo[e];
+        const float4 h = make_float4(tf32_rn(f.x), tf32_rn(f.y), tf32_rn(f.z), tf32_rn(f.w));
+        hi[e] = h;
+        lo[e] = make_float4(tf32_rn(f.x - h.x), tf32_rn(f.y - h.y), tf32_rn(f.z - h.z), tf32_rn(f.w - h.w));
+      }
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      // Descriptors differ only in the start-address field (bits 0-13, 16-byte units), so
+      // each MMA adds a compile-time tap / tile offset to a base descriptor.  Consecutive
+      // MMAs write different accumulators.
+      const uint64_t a0 = tc::make_desc(halo_s, LBO_A, 128);
+      const uint64_t b0 = tc::make_desc(w_s, LBO_B, 128);
+      const uint32_t first = c > 0 ? 1u : 0u;
+#pragma unroll
+      for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        const uint64_t boff = (uint64_t)(tap * 2 * NPAD);
+#pragma unroll
+        for (int sp = 0; sp < (KIND == TC_BF16 ? 1 : 3); ++sp) {
+          // TF32x3 terms: (a_lo, b_hi), (a_hi, b_lo), (a_hi, b_hi)
+          const uint64_t a_sp = (KIND == TC_BF16 || sp > 0) ? 0 : (uint64_t)(SPLIT_A >> 4);
+          const uint64_t b_sp = (KIND != TC_BF16 && sp == 1) ? (uint64_t)(SPLIT_B >> 4) : 0;
+#pragma unroll
+          for (int mt = 0; mt < MT; ++mt) {
+            const int ty = mt % TY, tz = mt / TY;
+            const uint64_t aoff = (uint64_t)(((tz + dz) * HY + (ty + dy)) * TC_HX + dx);
+            const uint32_t acc = (tap == 0 && sp == 0) ? first : 1u;
+            mma_kind(KIND, tbase + (uint32_t)(mt * NPAD), a0 + a_sp + aoff, b0 + b_sp + boff, idesc, acc);
+          }
+        }
+      }
+      tc::mma_commit(mbar);
+    }
+    // every thread waits for the chunk's MMAs: they read the buffers the next chunk overwrites
+    if (!tc::mbar_wait_bounded(mbar, (uint32_t)(c & 1), kWaitLimit)) atomicOr(abort_flag, 1);
+    __syncthreads();
+    if (*abort_flag) {
+      aborted = true;
+      fail_parity = (uint32_t)(c & 1);
+      break;
+    }
+  }
+  tc::fence_after_sync();
+  if (!aborted) {
+    const int q = warp & 3, h = warp >> 2;
+#pragma unroll 1
+    for (int mt = 0; mt < MT; ++mt) {
+      const int gy = y0 + mt % TY, gz = z0 + mt / TY, gx = x0 + 32 * q + lane;
+      const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
+      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * NPAD);
+      if constexpr (LAST) {
+        if (h == 0) {
+          float v[8];
+          tc::tmem_ld_x8(trow, v);
+          out_f32[vox] = v[0] + __ldg(&bias[0]) + resid[vox];
+        }
+      } else {
+        constexpr int HALF = NPAD / 2;
+#pragma unroll
+        for (int j = 0; j < HALF / 8; ++j) {
+          const int col = h * HALF + 8 * j;
+          float v[8];
+          tc::tmem_ld_x8(trow + (uint32_t)col, v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
+          if constexpr (KIND == TC_BF16) {
+            uint4 o;
+            o.x = pack_bf16x2(v[0], v[1]);
+            o.y = pack_bf16x2(v[2], v[3]);
+            o.z = pack_bf16x2(v[4], v[5]);
+            o.w = pack_bf16x2(v[6], v[7]);
+            out_act[(long long)(col / 8) * n + vox] = o;
+          } else {
+            float4* o4 = reinterpret_cast<float4*>(out_act);
+            o4[(long long)(col / 4) * n + vox] = make_float4(v[0], v[1], v[2], v[3]);
+            o4[(long long)(col / 4 + 1) * n + vox] = make_float4(v[4], v[5], v[6], v[7]);
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    if (err) atomicOr(err, 2);
+    // the chunk's MMAs may still be in flight: give them a bounded wait before TMEM is freed
+    tc::mbar_wait_bounded(mbar, fail_parity, kWaitLimit);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, Cfg::TMEM_COLS);
+}
+
+// First layer (one input channel): out[co] = ReLU(b[co] + sum_taps W[co][tap] x(v + tap)), written
+// in 16-byte channel groups.  BF16: x and W are BF16-rounded and the output is BF16.
+// SIMT: K = 27 is too small for the tensor path.
+template <int C, bool BF16>
+__global__ void __launch_bounds__(NT) k_conv_first(const float* __restrict__ in, const float* __restrict__ w,
+                                                   const float* __restrict__ bias, uint4* __restrict__ out, int nx,
+                                                   int ny, int nz) {
+  __shared__ float4 s_w[27 * C / 4];  // [tap][co]
+  __shared__ float s_b[C];
+  for (int e = threadIdx.x; e < 27 * C; e += NT) {
+    const int co = e % C, tap = e / C;
+    reinterpret_cast<float*>(s_w)[e] = w[co * 27 + tap];
+  }
+  for (int e = threadIdx.x; e < C; e += NT) s_b[e] = bias[e];
+  __syncthreads();
+  const long long plane = (long long)nx * ny, n = plane * nz;
+  for (long long v = (long long)blockIdx.x * NT + threadIdx.x; v < n; v += (long long)gridDim.x * NT) {
+    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / plane);
+    float acc[C];
+#pragma unroll
+    for (int co = 0; co < C; ++co) acc[co] = s_b[co];
+#pragma unroll 1
+    for (int tap = 0; tap < 27; ++tap) {
+      const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+      if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) continue;
+      float xv = __ldg(&in[(long long)zz * plane + (long long)yy * nx + xx]);
+      if (BF16) xv = __bfloat162float(__float2bfloat16_rn(xv));
+#pragma unroll
+      for (int q = 0; q < C / 4; ++q) {
+        const float4 wv = s_w[tap * (C / 4) + q];
+        acc[4 * q + 0] = fmaf(xv, wv.x, acc[4 * q + 0]);
+        acc[4 * q + 1] = fmaf(xv, wv.y, acc[4 * q + 1]);
+        acc[4 * q + 2] = fmaf(xv, wv.z, acc[4 * q + 2]);
+        acc[4 * q + 3] = fmaf(xv, wv.w, acc[4 * q + 3]);
+      }
+    }
+#pragma unroll
+    for (int co = 0; co < C; ++co) acc[co] = fmaxf(acc[co], 0.f);
+    if constexpr (BF16) {
+#pragma unroll
+      for (int g = 0; g < C / 8; ++g) {
+        uint4 o;
+        o.x = pack_bf16x2(acc[8 * g + 0], acc[8 * g + 1]);
+        o.y = pack_bf16x2(acc[8 * g + 2], acc[8 * g + 3]);
+        o.z = pack_bf16x2(acc[8 * g + 4], acc[8 * g + 5]);
+        o.w = pack_bf16x2(acc[8 * g + 6], acc[8 * g + 7]);
+        out[(long long)g * n + v] = o;
+      }
+    } else {
+      float4* o4 = reinterpret_cast<float4*>(out);
+#pragma unroll
+      for (int g = 0; g < C / 4; ++g)
+        o4[(long long)g * n + v] = make_float4(acc[4 * g], acc[4 * g + 1], acc[4 * g + 2], acc[4 * g + 3]);
+    }
+  }
+}
+
+// One-tile GEMM on the tensor core: D[128][N] = A[128][K] B[N][K]^T, FP32 out.  BF16 operands
+// (KIND = BF16) or FP32 operands through the TF32x3 split.  Checks the descriptor,
+// instruction-descriptor and TMEM conventions the conv kernels rely on.
+template <int KIND>
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const void* __restrict__ Av, const void* __restrict__ Bv,
+                                                    float* __restrict__ D, int N, int K) {
+  using Kd = TcKind<KIND>;
+  constexpr int EPV = Kd::EPV, ES = 16 / EPV;  // elements per vector, bytes per element
+  extern __shared__ unsigned char g_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)g_smem_raw + 1023) & ~(uintptr_t)1023);
+  const size_t a_bytes = (size_t)K * 128 * ES, b_bytes = (size_t)K * N * ES;
+  unsigned char* sA = base;                        // [SPLIT][K/EPV][128][EPV]
+  unsigned char* sB = base + Kd::SPLIT * a_bytes;  // [SPLIT][K/EPV][N][EPV]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(sB + Kd::SPLIT * b_bytes);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int e = tid; e < 128 * K; e += 128) {
+    const int m = e / K, k = e % K;
+    const size_t off = ((size_t)(k / EPV) * 128 + m) * EPV + k % EPV;
+    if constexpr (KIND == TC_BF16) {
+      reinterpret_cast<unsigned short*>(sA)[off] = static_cast<const unsigned short*>(Av)[e];
+    } else {
+      const float x = static_cast<const float*>(Av)[e], h = tf32_rn(x);
+      reinterpret_cast<float*>(sA)[off] = h;
+      reinterpret_cast<float*>(sA + a_bytes)[off] = tf32_rn(x - h);
+    }
+  }
+  for (int e = tid; e < N * K; e += 128) {
+    const int nn = e / K, k = e % K;
+    const size_t off = ((size_t)(k / EPV) * N + nn) * EPV + k % EPV;
+    if constexpr (KIND == TC_BF16) {
+      reinterpret_cast<unsigned short*>(sB)[off] = static_cast<const unsigned short*>(Bv)[e];
+    } else {
+      const float x = static_cast<const float*>(Bv)[e], h = tf32_rn(x);
+      reinterpret_cast<float*>(sB)[off] = h;
+      reinterpret_cast<float*>(sB + b_bytes)[off] = tf32_rn(x - h);
+    }
+  }
+  const uint32_t ncols = (uint32_t)pow2_cols(N);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, ncols);
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  if (tid == 0) {
+    const uint32_t a_s = tc::smem_addr(sA), b_s = tc::smem_addr(sB);
+    const uint32_t idesc = Kd::idesc(128, N);
+    for (int kk = 0; kk < K / (2 * EPV); ++kk) {
+      const uint64_t ah = tc::make_desc(a_s + kk * 2 * 128 * 16, 128 * 16, 128);
+      const uint64_t bh = tc::make_desc(b_s + kk * 2 * N * 16, N * 16, 128);
+      if constexpr (KIND == TC_BF16) {
+        mma_kind(KIND, tbase, ah, bh, idesc, kk > 0 ? 1u : 0u);
+      } else {
+        const uint64_t al = tc::make_desc(a_s + (uint32_t)a_bytes + kk * 2 * 128 * 16, 128 * 16, 128);
+        const uint64_t bl = tc::make_desc(b_s + (uint32_t)b_bytes + kk * 2 * N * 16, N * 16, 128);
+        mma_kind(KIND, tbase, al, bh, idesc, kk > 0 ? 1u : 0u);
+        mma_kind(KIND, tbase, ah, bl, idesc, 1u);
+        mma_kind(KIND, tbase, ah, bh, idesc, 1u);
+      }
+    }
+    tc::mma_commit(mbar);
+  }
+  const bool ok = __all_sync(0xffffffffu, tc::mbar_wait_bounded(mbar, 0u, kWaitLimit));
+  tc::fence_after_sync();
+  if (ok) {
+    const int m = 32 * warp + lane;
+    for (int c = 0; c < N; c += 8) {
+      float v[8];
+      tc::tmem_ld_x8(tbase + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) D[m * N + c + i] = v[i];
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, ncols);
+}
+
+// ---------------------------------------------------------------- host side
+
+static uint16_t bf16_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u = (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;  // round to nearest even (finite inputs)
+  return (uint16_t)u;
+}
+static float bits_to_float(uint32_t u) {
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+float bf16_round_value(float f) { return bits_to_float((uint32_t)bf16_bits(f) << 16); }
+static float tf32_rn_host(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  u += 0xFFFu + ((u >> 13) & 1u);
+  return bits_to_float(u & 0xFFFFE000u);
+}
+
+template <int KIND, int CIN, int NPAD, bool LAST>
+static cudaError_t run_tc(const uint4* in, const uint4* wpk, const float* bias, uint4* out_act, float* out_f32,
+                          const float* resid, int nx, int ny, int nz, int* err, cudaStream_t st) {
+  using Cfg = TcCfg<KIND, CIN, NPAD>;
+  auto kern = k_conv3_tc<KIND, CIN, NPAD, LAST>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+  if (e != cudaSuccess) return e;
+  dim3 grid(nx / TCX, ny / Cfg::TY, nz / Cfg::TZ);
+  kern<<<grid, TC_NT, Cfg::SMEM, st>>>(in, wpk, bias, out_act, out_f32, resid, nx, ny, nz, err);
+  return cudaGetLastError();
+}
+
+template <int C, bool BF16>
+static cudaError_t run_first(const float* in, const float* w, const float* b, uint4* out, int nx, int ny, int nz,
+                             cudaStream_t st) {
+  const long long n = (long long)nx * ny * nz;
+  long long blocks = (n + NT - 1) / NT;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_conv_first<C, BF16><<<(unsigned)blocks, NT, 0, st>>>(in, w, b, out, nx, ny, nz);
+  return cudaGetLastError();
+}
+
+template <int KIND, int C>
+static cudaError_t apply_tc_c(const clamp_denoiser* d, const float* in, float* out, int nx, int ny, int nz, void* ws,
+                              int* err, cudaStream_t st) {
+  const size_t n = (size_t)nx * ny * nz;
+  const size_t esz = KIND == TC_BF16 ? 2 : 4;
+  const size_t act = ((size_t)C * n * esz + 255) & ~(size_t)255;
+  uint4* A = static_cast<uint4*>(ws);
+  uint4* B = reinterpret_cast<uint4*>(static_cast<char*>(ws) + act);
+  cudaError_t e = run_first<C, KIND == TC_BF16>(in, d->w[0], d->b[0], A, nx, ny, nz, st);
+  if (e != cudaSuccess) return e;
+  uint4* cur = A;
+  for (int i = 1; i < d->layers; ++i) {
+    const uint4* wp = static_cast<const uint4*>(d->w16[i]);
+    if (i == d->layers - 1) {
+      e = run_tc<KIND, C, 16, true>(cur, wp, d->b[i], nullptr, out, in, nx, ny, nz, err, st);
+    } else {
+      uint4* dst = cur == A ? B : A;
+      e = run_tc<KIND, C, C, false>(cur, wp, d->b[i], dst, nullptr, nullptr, nx, ny, nz, err, st);
+      cur = dst;
+    }
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+bool tc_denoiser_supports(const clamp_denoiser* d, int nx, int ny, int nz) {
+  const bool bf = d->dtype == CLAMP_DENOISER_BF16;
+  const int C = d->channels;
+  const bool ch = bf ? (C == 16 || C == 32 || C == 48 || C == 64) : (C == 16 || C == 32 || C == 48);
+  const int ty = bf ? TcKind<TC_BF16>::TY : TcKind<TC_TF32X3>::TY;
+  const int tz = bf ? TcKind<TC_BF16>::TZ : TcKind<TC_TF32X3>::TZ;
+  return ch && nx % TCX == 0 && ny % ty == 0 && nz % tz == 0;
+}
+
+size_t tc_denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz) {
+  const size_t n = (size_t)nx * ny * nz;
+  const size_t esz = d->dtype == CLAMP_DENOISER_BF16 ? 2 : 4;
+  return 2 * ((((size_t)d->channels * n * esz) + 255) & ~(size_t)255);
+}
+
+cudaError_t tc_denoise_apply(const clamp_denoiser* d, const float* in, float* out, int nx, int ny, int nz, void* ws,
+                             int* err, cudaStream_t st) {
+  if (d->dtype == CLAMP_DENOISER_BF16) {
+    switch (d->channels) {
+      case 16: return apply_tc_c<TC_BF16, 16>(d, in, out, nx, ny, nz, ws, err, st);
+      case 32: return apply_tc_c<TC_BF16, 32>(d, in, out, nx, ny, nz, ws, err, st);
+      case 48: return apply_tc_c<TC_BF16, 48>(d, in, out, nx, ny, nz, ws, err, st);
+      case 64: return apply_tc_c<TC_BF16, 64>(d, in, out, nx, ny, nz, ws, err, st);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (d->channels) {
+    case 16: return apply_tc_c<TC_TF32X3, 16>(d, in, out, nx, ny, nz, ws, err, st);
+    case 32: return apply_tc_c<TC_TF32X3, 32>(d, in, out, nx, ny, nz, ws, err, st);
+    case 48: return apply_tc_c<TC_TF32X3, 48>(d, in, out, nx, ny, nz, ws, err, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Packs layer weights W[cout][cin][27] (float) for the tensor-core kernels.
+// BF16: [cin/16][27][2][npad][8] BF16 (RNE).  TF32x3: hi copy then lo copy, each
+// [cin/8][27][2][npad][4] FP32.  Output channels >= cout are zero.
+std::vector<uint8_t> pack_tc_weights(const float* W, int cin, int cout, int npad, bool bf16) {
+  const int epv = bf16 ? 8 : 4, ch = 2 * epv, chunks = cin / ch;
+  const size_t per = (size_t)chunks * 27 * 2 * npad * epv;  // elements per copy
+  std::vector<uint8_t> p(bf16 ? per * 2 : per * 8, 0);
+  for (int c = 0; c < chunks; ++c)
+    for (int tap = 0; tap < 27; ++tap)
+      for (int cg = 0; cg < 2; ++cg)
+        for (int co = 0; co < cout; ++co)
+          for (int e = 0; e < epv; ++e) {
+            const int ci = ch * c + epv * cg + e;
+            const size_t dst = ((((size_t)c * 27 + tap) * 2 + cg) * npad + co) * epv + e;
+            const float w = W[((size_t)co * cin + ci) * 27 + tap];
+            if (bf16) {
+              reinterpret_cast<uint16_t*>(p.data())[dst] = bf16_bits(w);
+            } else {
+              const float h = tf32_rn_host(w);
+              reinterpret_cast<float*>(p.data())[dst] = h;
+              reinterpret_cast<float*>(p.data())[per + dst] = tf32_rn_host(w - h);
+            }
+          }
+  return p;
+}
+
+}  // namespace clamp
+
+extern "C" clamp_status clamp_tc_gemm_bf16(int32_t n, int32_t k, const void* a, const void* b, float* d,
+                                           void* stream) {
+  if (n < 16 || n > 256 || n % 16 || k < 16 || k > 256 || k % 16 || !a || !b || !d) return CLAMP_EINVAL;
+  const size_t smem = 1024 + (size_t)k * 128 * 2 + (size_t)k * n * 2 + 64;
+  auto kern = clamp::k_tc_gemm<clamp::TC_BF16>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return CLAMP_ECUDA;
+  kern<<<1, 128, smem, (cudaStream_t)stream>>>(a, b, d, n, k);
+  return cudaGetLastError() == cudaSuccess ? CLAMP_OK : CLAMP_ECUDA;
+}
+
+extern "C" clamp_status clamp_tc_gemm_tf32x3(int32_t n, int32_t k, const float* a, const float* b, float* d,
+                                             void* stream) {
+  if (n < 16 || n > 256 || n % 16 || k < 8 || k > 192 || k % 8 || !a || !b || !d) return CLAMP_EINVAL;
+  const size_t smem = 1024 + 2 * ((size_t)k * 128 * 4 + (size_t)k * n * 4) + 64;
+  if (smem > 227 * 1024) return CLAMP_EINVAL;
+  auto kern = clamp::k_tc_gemm<clamp::TC_TF32X3>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return CLAMP_ECUDA;
+  kern<<<1, 128, smem, (cudaStream_t)stream>>>(a, b, d, n, k);
+  return cudaGetLastError() == cudaSuccess ? CLAMP_OK : CLAMP_ECUDA;
+}

@@ -42,18 +42,20 @@ def _stream_key(seed: int, stream: int) -> np.uint64:
     return _mix64(k)[0]
 
 
-def uniform(seed: int, stream: int, count: int) -> np.ndarray:
-    """``count`` doubles in [0, 1) from counter ``i`` of stream (seed, stream)."""
+def uniform(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """``count`` doubles in [0, 1) from counters offset+1 .. offset+count of stream (seed, stream)."""
     with np.errstate(over="ignore"):
-        i = np.arange(1, count + 1, dtype=np.uint64)
+        i = np.arange(offset + 1, offset + count + 1, dtype=np.uint64)
         z = _mix64(_stream_key(seed, stream) + i * _GOLDEN)
     return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
 
 
-def normal(seed: int, stream: int, count: int) -> np.ndarray:
-    """``count`` standard normal doubles (Box-Muller on pairs of uniforms)."""
+def normal(seed: int, stream: int, count: int, offset: int = 0) -> np.ndarray:
+    """``count`` standard normal doubles (Box-Muller on pairs of uniforms); ``offset`` (even)
+    is the index of the first normal within the stream, so chunks concatenate to one draw."""
+    assert offset % 2 == 0
     m = (count + 1) // 2
-    u = uniform(seed, stream, 2 * m)
+    u = uniform(seed, stream, 2 * m, offset)
     u1 = 1.0 - u[0::2]  # in (0, 1], keeps log finite
     u2 = u[1::2]
     rad = np.sqrt(-2.0 * np.log(u1))
@@ -63,11 +65,20 @@ def normal(seed: int, stream: int, count: int) -> np.ndarray:
     return out[:count]
 
 
-def complex_normal(seed: int, stream: int, shape) -> np.ndarray:
-    """Circular complex Gaussian CN(0, 1): E|z|^2 = 1, real and imaginary parts N(0, 1/2)."""
+def complex_normal(seed: int, stream: int, shape, offset: int = 0) -> np.ndarray:
+    """Circular complex Gaussian CN(0, 1): E|z|^2 = 1, real and imaginary parts N(0, 1/2).
+    ``offset`` is the index of the first complex value within the stream."""
     cnt = int(np.prod(shape))
-    v = normal(seed, stream, 2 * cnt)
+    v = normal(seed, stream, 2 * cnt, 2 * offset)
     return ((v[0::2] + 1j * v[1::2]) * math.sqrt(0.5)).reshape(shape)
+
+
+def look_draws(wl: "Workload", seed: int, look: int):
+    """Speckle and noise draws of one look, equal to look ``look`` of the full draws
+    make_workload(..., with_draws=True) returns."""
+    n = wl.nx * wl.ny * wl.nz
+    shape = (wl.nz, wl.ny, wl.nx)
+    return complex_normal(seed, 20, shape, look * n), complex_normal(seed, 21, shape, look * n)
 
 
 # ----------------------------------------------------------------------------- apertures

@@ -72,3 +72,14 @@ def test_workload_presets():
     w2 = I.make_workload("cfg2", seed=1, with_draws=False)
     assert w2.denoiser["kind"] == "cnn" and len(w2.denoiser["weights"]) == 5
     assert w2.denoiser["weights"][1].shape == (32, 32, 3, 3, 3)
+
+
+def test_chunked_draws_equal_full_draw():
+    full = I.complex_normal(5, 20, (3, 4, 8, 16))
+    n = 4 * 8 * 16
+    parts = [I.complex_normal(5, 20, (4, 8, 16), l * n) for l in range(3)]
+    np.testing.assert_array_equal(np.stack(parts), full)
+    wl = I.make_workload("tiny", seed=2)
+    spk, eta = I.look_draws(wl, 2, 1)
+    np.testing.assert_array_equal(spk, wl.speckle[1])
+    np.testing.assert_array_equal(eta, wl.noise[1])
