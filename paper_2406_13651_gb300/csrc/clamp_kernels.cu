@@ -80,21 +80,39 @@ __global__ void __launch_bounds__(NT) k_a_x(Geom g, AgentScalars s, const float2
                                             const float2* __restrict__ tw) {
   constexpr int LX = rows_per_cta(N), LT = 2 * LX, LD = N + 1;
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
+  constexpr int CNT = LX * N, PER = (CNT + NT - 1) / NT;
   const long long e0 = (long long)blockIdx.x * LX * N;  // first element of the tile
-  for (int e = threadIdx.x; e < LX * N; e += NT) {
-    const int line = e / N, i = e - line * N;
-    const float2 m = mu[e0 + e];
-    const float D = 1.0f / (rprev[e0 + e] + s.floor);
-    sm[line * LD + i] = m;
-    sm[(LX + line) * LD + i] = cscale(m, D);
+  // all of a thread's loads are issued before any shared-memory store
+  float2 mv[PER];
+  float rv[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      mv[p] = mu[e0 + e];
+      rv[p] = rprev[e0 + e];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e / N, i = e - line * N;
+      sm[line * LD + i] = mv[p];
+      sm[(LX + line) * LD + i] = cscale(mv[p], 1.0f / (rv[p] + s.floor));
+    }
   }
   __syncthreads();
   fft_tile<N, LT, NT, false>(sm, tw);
-  for (int e = threadIdx.x; e < LX * N; e += NT) {
-    const int line = e / N, i = e - line * N;
-    const float2 a = cscale(sm[line * LD + i], s.sc_x);
-    const float2 b = cscale(sm[(LX + line) * LD + i], s.sc_x);
-    T[e0 + e] = make_float4(a.x, a.y, b.x, b.y);
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e / N, i = e - line * N;
+      const float2 a = cscale(sm[line * LD + i], s.sc_x);
+      const float2 b = cscale(sm[(LX + line) * LD + i], s.sc_x);
+      T[e0 + e] = make_float4(a.x, a.y, b.x, b.y);
+    }
   }
 }
 
@@ -106,20 +124,34 @@ __global__ void __launch_bounds__(NT) k_a_y(Geom g, AgentScalars s, float4* __re
   constexpr int LT = 2 * LC, LD = N + 1;
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
   const long long S = g.nx;
+  constexpr int CNT = LC * N, PER = (CNT + NT - 1) / NT;
   const long long base = (long long)blockIdx.z * g.n + (long long)blockIdx.y * g.ny * g.nx + blockIdx.x * LC;
-  for (int e = threadIdx.x; e < LC * N; e += NT) {
-    const int line = e % LC, i = e / LC;
-    const float4 v = T[base + i * S + line];
-    sm[line * LD + i] = make_float2(v.x, v.y);
-    sm[(LC + line) * LD + i] = make_float2(v.z, v.w);
+  float4 tv[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) tv[p] = T[base + (e / LC) * S + e % LC];
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e % LC, i = e / LC;
+      sm[line * LD + i] = make_float2(tv[p].x, tv[p].y);
+      sm[(LC + line) * LD + i] = make_float2(tv[p].z, tv[p].w);
+    }
   }
   __syncthreads();
   fft_tile<N, LT, NT, false>(sm, tw);
-  for (int e = threadIdx.x; e < LC * N; e += NT) {
-    const int line = e % LC, i = e / LC;
-    const float2 a = cscale(sm[line * LD + i], s.sc_y);
-    const float2 b = cscale(sm[(LC + line) * LD + i], s.sc_y);
-    T[base + i * S + line] = make_float4(a.x, a.y, b.x, b.y);
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e % LC, i = e / LC;
+      const float2 a = cscale(sm[line * LD + i], s.sc_y);
+      const float2 b = cscale(sm[(LC + line) * LD + i], s.sc_y);
+      T[base + i * S + line] = make_float4(a.x, a.y, b.x, b.y);
+    }
   }
 }
 
@@ -135,23 +167,40 @@ __global__ void __launch_bounds__(NT) k_ab_z(Geom g, AgentScalars s, const float
   const long long S = (long long)g.nx * g.ny;
   const int x0 = blockIdx.x * LC, ky = blockIdx.y, l = blockIdx.z;
   const long long base = (long long)l * g.n + (long long)ky * g.nx + x0;
-  for (int e = threadIdx.x; e < LC * N; e += NT) {
-    const int line = e % LC, i = e / LC;
-    const float4 v = T[base + i * S + line];
-    sm[line * LD + i] = make_float2(v.x, v.y);
-    sm[(LC + line) * LD + i] = make_float2(v.z, v.w);
+  constexpr int CNT = LC * N, PER = (CNT + NT - 1) / NT;
+  float4 tv[PER];
+  float2 yvs[PER];   // the data for the epilogue is fetched together with T
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      tv[p] = T[base + (e / LC) * S + e % LC];
+      yvs[p] = y[base + (e / LC) * S + e % LC];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e % LC, i = e / LC;
+      sm[line * LD + i] = make_float2(tv[p].x, tv[p].y);
+      sm[(LC + line) * LD + i] = make_float2(tv[p].z, tv[p].w);
+    }
   }
   __syncthreads();
   fft_tile<N, LT, NT, false>(sm, tw);
   // frequency-domain gradient: Fd = a (y - a M) / sigma_w^2 - P
   float acc[3] = {0.f, 0.f, 0.f};
   const float inv_nv = 1.0f / s.nv;
-  for (int e = threadIdx.x; e < LC * N; e += NT) {
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (!(CNT % NT == 0 || e < CNT)) continue;
     const int line = e % LC, kz = e / LC;
     const float2 M = cscale(sm[line * LD + kz], s.sc_z);
     const float2 P = cscale(sm[(LC + line) * LD + kz], s.sc_z);
     const float av = __ldg(&pupil[ky * g.nx + x0 + line]) * __ldg(&window[kz]);
-    const float2 yv = y[base + kz * S + line];
+    const float2 yv = yvs[p];
     const float2 res = make_float2(fmaf(-av, M.x, yv.x), fmaf(-av, M.y, yv.y));
     const float f = av * inv_nv;
     const float2 fd = make_float2(fmaf(f, res.x, -P.x), fmaf(f, res.y, -P.y));
@@ -163,9 +212,13 @@ __global__ void __launch_bounds__(NT) k_ab_z(Geom g, AgentScalars s, const float
   }
   __syncthreads();
   fft_tile<N, LC, NT, true>(sm, tw);
-  for (int e = threadIdx.x; e < LC * N; e += NT) {
-    const int line = e % LC, i = e / LC;
-    U[base + i * S + line] = cscale(sm[line * LD + i], s.sc_z);
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e % LC, i = e / LC;
+      U[base + i * S + line] = cscale(sm[line * LD + i], s.sc_z);
+    }
   }
   double* const outs[3] = {p.s1, p.s2, p.s4};
   block_reduce_store<3>(acc, outs, (long long)l * p.pz + (long long)blockIdx.y * gridDim.x + blockIdx.x);
@@ -193,24 +246,47 @@ template <int N, bool INV, int MODE>
 __global__ void __launch_bounds__(NT) k_row(RowArgs a, const float2* __restrict__ tw) {
   constexpr int LX = rows_per_cta(N), LD = N + 1;
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
+  constexpr int CNT = LX * N, PER = (CNT + NT - 1) / NT;
   const long long e0 = (long long)blockIdx.x * LX * N;
-  for (int e = threadIdx.x; e < LX * N; e += NT) {
-    const int line = e / N, i = e - line * N;
-    float2 v = a.in[e0 + e];
-    if constexpr (MODE == ROW_SIM) {
-      const long long vox = (e0 + e) % a.n;
-      v = cscale(v, sqrtf(a.rvol[vox]));
+  float2 iv[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) iv[p] = a.in[e0 + e];
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e / N, i = e - line * N;
+      float2 v = iv[p];
+      if constexpr (MODE == ROW_SIM) {
+        const long long vox = (e0 + e) % a.n;
+        v = cscale(v, sqrtf(a.rvol[vox]));
+      }
+      sm[line * LD + i] = v;
     }
-    sm[line * LD + i] = v;
   }
   __syncthreads();
   fft_tile<N, LX, NT, INV>(sm, tw);
   float acc[1] = {0.f};
-  for (int e = threadIdx.x; e < LX * N; e += NT) {
-    const int line = e / N, i = e - line * N;
-    const float2 v = cscale(sm[line * LD + i], a.scale);
-    if constexpr (MODE == ROW_BX) acc[0] += cabs2(v) / (a.rprev[e0 + e] + a.floor);
-    a.out[e0 + e] = v;
+  float rpv[PER];
+  if constexpr (MODE == ROW_BX) {
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+      const int e = threadIdx.x + p * NT;
+      if (CNT % NT == 0 || e < CNT) rpv[p] = a.rprev[e0 + e];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e / N, i = e - line * N;
+      const float2 v = cscale(sm[line * LD + i], a.scale);
+      if constexpr (MODE == ROW_BX) acc[0] += cabs2(v) / (rpv[p] + a.floor);
+      a.out[e0 + e] = v;
+    }
   }
   if constexpr (MODE == ROW_BX) {
     double* const outs[1] = {a.s3};
@@ -241,17 +317,31 @@ __global__ void __launch_bounds__(NT) k_col(ColArgs a, const float2* __restrict_
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
   const int x0 = blockIdx.x * LC, fixed = blockIdx.y, l = blockIdx.z;
   const long long base = (long long)l * a.n + (long long)fixed * a.slab + x0;
-  for (int e = threadIdx.x; e < LC * N; e += NT) {
-    const int line = e % LC, i = e / LC;
-    float2 v = a.in[base + i * a.stride + line];
-    if constexpr (MODE == COL_ADJ) {  // z axis, fixed = ky
-      v = cscale(v, __ldg(&a.pupil[fixed * a.nx + x0 + line]) * __ldg(&a.window[i]));
+  constexpr int CNT = LC * N, PER = (CNT + NT - 1) / NT;
+  float2 iv[PER];
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) iv[p] = a.in[base + (e / LC) * a.stride + e % LC];
+  }
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (CNT % NT == 0 || e < CNT) {
+      const int line = e % LC, i = e / LC;
+      float2 v = iv[p];
+      if constexpr (MODE == COL_ADJ) {  // z axis, fixed = ky
+        v = cscale(v, __ldg(&a.pupil[fixed * a.nx + x0 + line]) * __ldg(&a.window[i]));
+      }
+      sm[line * LD + i] = v;
     }
-    sm[line * LD + i] = v;
   }
   __syncthreads();
   fft_tile<N, LC, NT, INV>(sm, tw);
-  for (int e = threadIdx.x; e < LC * N; e += NT) {
+#pragma unroll
+  for (int p = 0; p < PER; ++p) {
+    const int e = threadIdx.x + p * NT;
+    if (!(CNT % NT == 0 || e < CNT)) continue;
     const int line = e % LC, i = e / LC;
     float2 v = cscale(sm[line * LD + i], a.scale);
     const long long gi = base + i * a.stride + line;

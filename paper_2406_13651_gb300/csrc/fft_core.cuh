@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace clamp {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -59,6 +61,13 @@ __device__ __forceinline__ constexpr int bitrev(int i) {
   return r;
 }
 
+// v[i] <- v[bitrev(i)], with every index a compile-time constant so the array stays in registers.
+template <int R, int... I>
+__device__ __forceinline__ void bitrev_permute(float2 (&v)[R], std::integer_sequence<int, I...>) {
+  const float2 t[R] = {v[std::integral_constant<int, bitrev<R>(I)>::value]...};
+  ((v[I] = t[I]), ...);
+}
+
 // In-place R-point DFT in registers, natural order in and out.
 // Forward: V[s] = sum_r v[r] exp(-2 pi i r s / R); inverse uses +.
 template <int R, bool INV>
@@ -77,15 +86,7 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
     v[2] = csub(m, t);
   } else {
     static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      const int j = bitrev<R>(i);
-      if (j > i) {
-        float2 t = v[i];
-        v[i] = v[j];
-        v[j] = t;
-      }
-    }
+    bitrev_permute(v, std::make_integer_sequence<int, R>{});
 #pragma unroll
     for (int len = 2; len <= R; len <<= 1) {
 #pragma unroll
