@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="clamp", choices=["clamp", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "batch"])
+    ap.add_argument("--batch-iters", type=int, default=10)
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -243,6 +244,83 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------------- GPU arm
 
+def run_batch(args, rank, world, local):
+    """24 seeded scenes of uneven size and look count in one captured CUDA graph; a step
+    is one graph launch (every scene runs --batch-iters iterations)."""
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2406_13651_gb300 import build as B
+    from paper_2406_13651_gb300 import clamp as C
+    from paper_2406_13651_gb300 import inputs as I
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    specs = I.batch_specs(24, seed=7 + rank, iters=args.batch_iters)
+    den = C.Denoiser.gauss(0.8)
+    scenes = []
+    gen = torch.Generator(device=dev)
+    for sp in specs:   # scene and aperture from the seeded generator; speckle and noise drawn on the device
+        wl = I.batch_scene(sp, with_draws=False)
+        gen.manual_seed(sp["seed"])
+        shape = (wl.looks, wl.nz, wl.ny, wl.nx)
+        spk = torch.complex(torch.randn(shape, generator=gen, device=dev),
+                            torch.randn(shape, generator=gen, device=dev)) * (0.5 ** 0.5)
+        eta = torch.complex(torch.randn(shape, generator=gen, device=dev),
+                            torch.randn(shape, generator=gen, device=dev)) * (0.5 ** 0.5)
+        p = C.make_params(wl.nx, wl.ny, wl.nz, wl.looks, wl.noise_var, wl.prox_var, max_iters=wl.iters)
+        pu, wi = torch.from_numpy(wl.pupil).to(dev), torch.from_numpy(wl.window).to(dev)
+        y = C.simulate(p, torch.from_numpy(wl.r_true.astype(np.float32)).to(dev), spk, eta, pu, wi)
+        del spk, eta
+        scenes.append((p, y, pu, wi, torch.empty((wl.nz, wl.ny, wl.nx), dtype=torch.float32, device=dev)))
+    t0 = time.perf_counter()
+    batch = C.Batch(scenes, den)
+    plan_s = time.perf_counter() - t0
+    units = sum(sp["nx"] * sp["ny"] * sp["nz"] * sp["looks"] * sp["iters"] for sp in specs)
+    K, W = max(3, min(args.steps, 10)), max(1, min(args.warmup, 3))
+    for _ in range(W):
+        batch.launch()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_start.record(stream)
+        for _ in range(K):
+            batch.launch()
+        t_end.record(stream)
+        torch.cuda.synchronize()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    lat = batch.latencies()   # of the last launch
+    t_max = elapsed
+    if world > 1:
+        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+    value = units * K * world / t_max
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"batch of 24 scenes in one CUDA graph launch: lateral {{64,96,128,192,256}}, "
+                                   f"range {{32,64,128}}, L in [4,32], R~U[0.3,0.5], SNR~U[5,20] dB, Gaussian prior, "
+                                   f"{args.batch_iters} iterations per scene per launch",
+                       "scenes": [[sp["nx"], sp["ny"], sp["nz"], sp["looks"]] for sp in specs],
+                       "voxel_look_iterations_per_step": units, "graph_build_s": plan_s},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max()), "per_scene": [round(float(x), 3) for x in lat]},
+            "gpu_launches": K, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -250,6 +328,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, rank, world, local)
 
     import numpy as np
     import torch

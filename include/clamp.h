@@ -11,7 +11,8 @@
  *    (re, im) float32 pairs.  Frequency-domain arrays (y, pupil, window) are in
  *    unshifted FFT order, DC at index 0.  Per-look arrays are [L][n] with
  *    n = nx*ny*nz, look-major.
- *  - Axis lengths must be powers of two in [8, 256]; nx must be a multiple of 16.
+ *  - Axis lengths must be 8, 16, 32, 64, 96, 128, 192 or 256 (radix 2/4/8/16 and 3 passes);
+ *    nx must be a multiple of 16.
  *  - Unless a function says "host", every array pointer is caller-owned DEVICE
  *    memory on the current CUDA device; the library never frees it.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
@@ -222,6 +223,39 @@ clamp_status clamp_reconstruct_host(const clamp_params* p, const float* y_host,
                                     const clamp_denoiser* den, const float* r_init_host,
                                     float* r_out_host, clamp_report* report, void* stream);
 void clamp_release_cache(void);
+
+/* ---- Batched reconstruction: many scenes of uneven size and look count in one launch. */
+
+/* One scene of a batch: its parameters (shape, looks, variances, iterations) and DEVICE
+ * buffers laid out as for clamp_reconstruct. */
+typedef struct clamp_scene {
+  clamp_params p;
+  const float* y;       /* complex [L][n] */
+  const float* pupil;   /* [ny][nx] */
+  const float* window;  /* [nz] */
+  float* r_out;         /* [n] <- r* */
+} clamp_scene;
+
+typedef struct clamp_batch clamp_batch;  /* opaque plan: captured CUDA graph + per-scene state */
+
+/* Scratch bytes for a batch (the sum of the scenes' reconstruction workspaces). */
+size_t clamp_batch_workspace_size(const clamp_scene* scenes, int32_t count, const clamp_denoiser* den);
+
+/* Builds a batch plan: checks every scene, partitions `ws` among them and captures
+ * into ONE CUDA graph, for every scene as an independent branch, the Alg. 2
+ * initialisation followed by p.max_iters iterations (forward agents, prior agent,
+ * MACE step), with a timing event at the start and at the end of each branch.
+ * Scenes, denoiser and ws must stay valid while the plan is used.  Synchronises. */
+clamp_status clamp_batch_create(const clamp_scene* scenes, int32_t count, const clamp_denoiser* den, void* ws,
+                                size_t ws_bytes, clamp_batch** out);
+/* Launches the whole batch with one cudaGraphLaunch on `stream` (asynchronous). */
+clamp_status clamp_batch_launch(clamp_batch* b, void* stream);
+/* After the launch completed (synchronises `stream`): per-scene latency from the launch
+ * start to the end of that scene's branch, milliseconds, host array [count]. */
+clamp_status clamp_batch_latencies(clamp_batch* b, void* stream, float* latency_ms);
+/* Per-scene final convergence error (host array [count]); synchronises. */
+clamp_status clamp_batch_residuals(clamp_batch* b, void* stream, double* ce);
+void clamp_batch_destroy(clamp_batch* b);
 
 #ifdef __cplusplus
 }

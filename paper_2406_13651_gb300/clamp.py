@@ -33,6 +33,8 @@ EXPORTS = [
     "clamp_denoise_workspace_size", "clamp_reconstruct", "clamp_reconstruct_host", "clamp_release_cache",
     "clamp_iterate", "clamp_iterate_workspace_size", "clamp_mace_step_noalloc",
     "clamp_tc_gemm_bf16", "clamp_tc_gemm_tf32x3",
+    "clamp_batch_workspace_size", "clamp_batch_create", "clamp_batch_launch", "clamp_batch_latencies",
+    "clamp_batch_residuals", "clamp_batch_destroy",
 ]
 
 
@@ -49,6 +51,12 @@ class Params(ctypes.Structure):
                 ("rho", ctypes.c_float), ("prior_weight", ctypes.c_float), ("max_iters", ctypes.c_int32),
                 ("k0", ctypes.c_int32), ("flags", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("tol", ctypes.c_double)]
+
+
+class Scene(ctypes.Structure):
+    """Mirror of ``clamp_scene``."""
+    _fields_ = [("p", Params), ("y", ctypes.c_void_p), ("pupil", ctypes.c_void_p), ("window", ctypes.c_void_p),
+                ("r_out", ctypes.c_void_p)]
 
 
 class Report(ctypes.Structure):
@@ -97,6 +105,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_mace_step_noalloc": (I, [PP, P, P, P, P, P]),
         "clamp_tc_gemm_bf16": (I, [I, I, P, P, P, P]),
         "clamp_tc_gemm_tf32x3": (I, [I, I, P, P, P, P]),
+        "clamp_batch_workspace_size": (S, [ctypes.POINTER(Scene), I, P]),
+        "clamp_batch_create": (I, [ctypes.POINTER(Scene), I, P, P, S, ctypes.POINTER(P)]),
+        "clamp_batch_launch": (I, [P, P]),
+        "clamp_batch_latencies": (I, [P, P, ctypes.POINTER(ctypes.c_float)]),
+        "clamp_batch_residuals": (I, [P, P, ctypes.POINTER(ctypes.c_double)]),
+        "clamp_batch_destroy": (V, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -320,3 +334,54 @@ def reconstruct_host(p: Params, y: np.ndarray, pupil: np.ndarray, window: np.nda
                                          den.handle, None if ri is None else ri.ctypes.data, r_out.ctypes.data,
                                          ctypes.byref(rep), _stream(stream)), "clamp_reconstruct_host")
     return Result(r_out, rep.iters, bool(rep.converged), ce[:rep.iters], mh[:rep.iters])
+
+
+class Batch:
+    """Many reconstructions as one CUDA graph (``clamp_batch_*``).
+
+    ``scenes``: list of (Params, y, pupil, window, r_out) with device tensors; they must
+    stay alive while the batch is used."""
+
+    def __init__(self, scenes, den: Denoiser):
+        import torch
+        self._keep = scenes
+        self.den = den
+        self.count = len(scenes)
+        self._arr = (Scene * self.count)(*[Scene(p, _ptr(y), _ptr(pu), _ptr(wi), _ptr(ro))
+                                            for (p, y, pu, wi, ro) in scenes])
+        need = load().clamp_batch_workspace_size(self._arr, self.count, den.handle)
+        if need == 0:
+            raise ClampError(1, "clamp_batch_workspace_size", "invalid scene parameters")
+        self.ws = _ws(need)
+        h = ctypes.c_void_p()
+        _check(load().clamp_batch_create(self._arr, self.count, den.handle, _ptr(self.ws), self.ws.numel(),
+                                         ctypes.byref(h)), "clamp_batch_create")
+        self.handle = h.value
+
+    def launch(self, stream=None):
+        _check(load().clamp_batch_launch(self.handle, _stream(stream)), "clamp_batch_launch")
+
+    def latencies(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.count, np.float32)
+        _check(load().clamp_batch_latencies(self.handle, _stream(stream),
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))),
+               "clamp_batch_latencies")
+        return out
+
+    def residuals(self, stream=None) -> np.ndarray:
+        out = np.zeros(self.count, np.float64)
+        _check(load().clamp_batch_residuals(self.handle, _stream(stream),
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))),
+               "clamp_batch_residuals")
+        return out
+
+    def close(self):
+        if self.handle:
+            load().clamp_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,6 +1,7 @@
 // clamp_api.cu -- the C ABI (include/clamp.h): argument checks, workspace
 // layout, per-device set-up and the CLAMP iteration driver (Alg. 2).
 #include "../../include/clamp.h"
+#include "clamp_internal.cuh"
 #include "clamp_kernels.cuh"
 #include "denoise.cuh"
 
@@ -20,7 +21,7 @@ using namespace clamp;
 
 static thread_local std::string g_err;
 
-static clamp_status fail(clamp_status s, const char* fmt, ...) {
+clamp_status api_fail(clamp_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -31,7 +32,7 @@ static clamp_status fail(clamp_status s, const char* fmt, ...) {
 }
 
 static clamp_status cuda_fail(cudaError_t e, const char* where) {
-  return fail(CLAMP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+  return api_fail(CLAMP_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
 #define API_CUDA(x, where)                             \
@@ -48,7 +49,7 @@ extern "C" const char* clamp_version(void) { return "clamp-gb300 0.1 (sm_103a)";
 static std::mutex g_dev_mu;
 static std::set<int> g_dev_ready;
 
-static clamp_status ensure_device() {
+clamp_status api_ensure_device() {
   int dev = -1;
   API_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   std::lock_guard<std::mutex> lk(g_dev_mu);
@@ -61,30 +62,30 @@ static clamp_status ensure_device() {
 // ---------------------------------------------------------------- validation
 
 extern "C" int32_t clamp_supported_length(int32_t n) {
-  return (n == 8 || n == 16 || n == 32 || n == 64 || n == 128 || n == 256) ? 1 : 0;
+  return (n == 8 || n == 16 || n == 32 || n == 64 || n == 96 || n == 128 || n == 192 || n == 256) ? 1 : 0;
 }
 
 static clamp_status check_shape(int nx, int ny, int nz) {
   if (!clamp_supported_length(nx) || !clamp_supported_length(ny) || !clamp_supported_length(nz))
-    return fail(CLAMP_EUNSUPPORTED, "volume %dx%dx%d (nx,ny,nz): axis lengths must be powers of two in [8, 256]",
+    return api_fail(CLAMP_EUNSUPPORTED, "volume %dx%dx%d (nx,ny,nz): axis lengths must be 8, 16, 32, 64, 96, 128, 192 or 256",
                 nx, ny, nz);
-  if (nx % LC) return fail(CLAMP_EUNSUPPORTED, "nx=%d must be a multiple of %d", nx, LC);
+  if (nx % LC) return api_fail(CLAMP_EUNSUPPORTED, "nx=%d must be a multiple of %d", nx, LC);
   return CLAMP_OK;
 }
 
 extern "C" clamp_status clamp_check_params(const clamp_params* p) {
-  if (!p) return fail(CLAMP_EINVAL, "params is NULL");
+  if (!p) return api_fail(CLAMP_EINVAL, "params is NULL");
   clamp_status s = check_shape(p->nx, p->ny, p->nz);
   if (s != CLAMP_OK) return s;
-  if (p->looks < 1 || p->looks > 4096) return fail(CLAMP_EINVAL, "looks=%d must be in [1, 4096]", p->looks);
-  if (!(p->noise_var > 0.f) || !isfinite(p->noise_var)) return fail(CLAMP_EINVAL, "noise_var must be > 0");
-  if (!(p->prox_var > 0.f) || !isfinite(p->prox_var)) return fail(CLAMP_EINVAL, "prox_var must be > 0");
-  if (!(p->rho > 0.f && p->rho < 1.f)) return fail(CLAMP_EINVAL, "rho=%g must be in (0, 1)", p->rho);
+  if (p->looks < 1 || p->looks > 4096) return api_fail(CLAMP_EINVAL, "looks=%d must be in [1, 4096]", p->looks);
+  if (!(p->noise_var > 0.f) || !isfinite(p->noise_var)) return api_fail(CLAMP_EINVAL, "noise_var must be > 0");
+  if (!(p->prox_var > 0.f) || !isfinite(p->prox_var)) return api_fail(CLAMP_EINVAL, "prox_var must be > 0");
+  if (!(p->rho > 0.f && p->rho < 1.f)) return api_fail(CLAMP_EINVAL, "rho=%g must be in (0, 1)", p->rho);
   if (!(p->prior_weight > 0.f && p->prior_weight < 1.f))
-    return fail(CLAMP_EINVAL, "prior_weight=%g must be in (0, 1)", p->prior_weight);
-  if (p->max_iters < 0) return fail(CLAMP_EINVAL, "max_iters must be >= 0");
-  if (p->k0 < 0) return fail(CLAMP_EINVAL, "k0 must be >= 0");
-  if (!(p->tol >= 0.0)) return fail(CLAMP_EINVAL, "tol must be >= 0");
+    return api_fail(CLAMP_EINVAL, "prior_weight=%g must be in (0, 1)", p->prior_weight);
+  if (p->max_iters < 0) return api_fail(CLAMP_EINVAL, "max_iters must be >= 0");
+  if (p->k0 < 0) return api_fail(CLAMP_EINVAL, "k0 must be >= 0");
+  if (!(p->tol >= 0.0)) return api_fail(CLAMP_EINVAL, "tol must be >= 0");
   return CLAMP_OK;
 }
 
@@ -158,14 +159,13 @@ T* at(void* base, size_t off) {
   return reinterpret_cast<T*>(static_cast<char*>(base) + off);
 }
 
-struct Derived {
-  Geom g;
-  AgentScalars s;
-  double alpha;
-};
+}  // namespace
+
+using Derived = ReconPlan;
 
 // alpha = mean(a^2) for the separable aperture a = window[kz] * pupil[ky][kx] (host, double).
-clamp_status derive(const clamp_params* p, const float* pupil, const float* window, cudaStream_t st, Derived* d) {
+clamp_status recon_prepare(const clamp_params* p, const float* pupil, const float* window, cudaStream_t st,
+                           ReconPlan* d) {
   d->g.nx = p->nx;
   d->g.ny = p->ny;
   d->g.nz = p->nz;
@@ -177,15 +177,15 @@ clamp_status derive(const clamp_params* p, const float* pupil, const float* wind
   API_CUDA(cudaStreamSynchronize(st), "pupil read");
   double sp = 0, sw = 0;
   for (float v : hp) {
-    if (!isfinite(v)) return fail(CLAMP_EINVAL, "pupil has a non-finite value");
+    if (!isfinite(v)) return api_fail(CLAMP_EINVAL, "pupil has a non-finite value");
     sp += (double)v * v;
   }
   for (float v : hw) {
-    if (!isfinite(v)) return fail(CLAMP_EINVAL, "window has a non-finite value");
+    if (!isfinite(v)) return api_fail(CLAMP_EINVAL, "window has a non-finite value");
     sw += (double)v * v;
   }
   const double alpha = (sp / hp.size()) * (sw / hw.size());
-  if (!(alpha > 0)) return fail(CLAMP_EINVAL, "aperture is identically zero (alpha = 0)");
+  if (!(alpha > 0)) return api_fail(CLAMP_EINVAL, "aperture is identically zero (alpha = 0)");
   d->alpha = alpha;
   d->s.nv = p->noise_var;
   d->s.alpha = (float)alpha;
@@ -196,6 +196,7 @@ clamp_status derive(const clamp_params* p, const float* pupil, const float* wind
   return CLAMP_OK;
 }
 
+namespace {
 Partials partials(const AgentLayout& a, void* ws) {
   Partials p{};
   p.s1 = at<double>(ws, a.s1);
@@ -209,14 +210,14 @@ Partials partials(const AgentLayout& a, void* ws) {
 
 clamp_status need_ptrs(std::initializer_list<const void*> ptrs, const char* what) {
   for (const void* q : ptrs)
-    if (!q) return fail(CLAMP_EINVAL, "%s: NULL array argument", what);
+    if (!q) return api_fail(CLAMP_EINVAL, "%s: NULL array argument", what);
   return CLAMP_OK;
 }
 
 clamp_status check_ws(void* ws, size_t have, size_t need, const char* what) {
-  if (!ws) return fail(CLAMP_EINVAL, "%s: workspace is NULL", what);
-  if (((uintptr_t)ws) & 255) return fail(CLAMP_EINVAL, "%s: workspace must be 256-byte aligned", what);
-  if (have < need) return fail(CLAMP_ENOMEM, "%s: workspace %zu bytes < %zu needed", what, have, need);
+  if (!ws) return api_fail(CLAMP_EINVAL, "%s: workspace is NULL", what);
+  if (((uintptr_t)ws) & 255) return api_fail(CLAMP_EINVAL, "%s: workspace must be 256-byte aligned", what);
+  if (have < need) return api_fail(CLAMP_ENOMEM, "%s: workspace %zu bytes < %zu needed", what, have, need);
   return CLAMP_OK;
 }
 }  // namespace
@@ -242,9 +243,9 @@ extern "C" size_t clamp_reconstruct_workspace_size(const clamp_params* p, const 
 extern "C" clamp_status clamp_fft3(int32_t nx, int32_t ny, int32_t nz, int32_t batch, const float* in, float* out,
                                    int32_t inverse, void* stream) {
   API_TRY(check_shape(nx, ny, nz));
-  if (batch < 1) return fail(CLAMP_EINVAL, "batch=%d must be >= 1", batch);
+  if (batch < 1) return api_fail(CLAMP_EINVAL, "batch=%d must be >= 1", batch);
   API_TRY(need_ptrs({in, out}, "clamp_fft3"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   Geom g{nx, ny, nz, batch, (long long)nx * ny * nz};
   API_CUDA(launch_fft3(g, reinterpret_cast<const float2*>(in), reinterpret_cast<float2*>(out), inverse != 0,
                        (float)(1.0 / sqrt((double)nx)), (float)(1.0 / sqrt((double)ny)),
@@ -257,7 +258,7 @@ extern "C" clamp_status clamp_simulate(const clamp_params* p, const float* r, co
                                        const float* pupil, const float* window, float* y, void* stream) {
   API_TRY(clamp_check_params(p));
   API_TRY(need_ptrs({r, speckle, noise, pupil, window, y}, "clamp_simulate"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   Geom g{p->nx, p->ny, p->nz, p->looks, (long long)p->nx * p->ny * p->nz};
   API_CUDA(launch_simulate(g, r, reinterpret_cast<const float2*>(speckle), reinterpret_cast<const float2*>(noise),
                            pupil, window, (float)sqrt((double)p->noise_var), reinterpret_cast<float2*>(y),
@@ -286,10 +287,10 @@ extern "C" clamp_status clamp_init(const clamp_params* p, const float* y, const 
   API_TRY(need_ptrs({y, pupil, window, mu, r, w}, "clamp_init"));
   const AgentLayout al = agent_layout(p);
   API_TRY(check_ws(ws, ws_bytes, al.bytes, "clamp_init"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   cudaStream_t st = (cudaStream_t)stream;
   Derived d;
-  API_TRY(derive(p, pupil, window, st, &d));
+  API_TRY(recon_prepare(p, pupil, window, st, &d));
   return do_init(p, d, y, pupil, window, r_init, reinterpret_cast<float2*>(mu), r, w, al, ws, st);
 }
 
@@ -331,14 +332,14 @@ extern "C" clamp_status clamp_forward_prox(const clamp_params* p, int32_t k, con
                                            const float* window, float* mu, float* r, const float* w,
                                            double* mu_residual, void* ws, size_t ws_bytes, void* stream) {
   API_TRY(clamp_check_params(p));
-  if (k < 1) return fail(CLAMP_EINVAL, "iteration index k=%d must be >= 1", k);
+  if (k < 1) return api_fail(CLAMP_EINVAL, "iteration index k=%d must be >= 1", k);
   API_TRY(need_ptrs({y, pupil, window, mu, r, w}, "clamp_forward_prox"));
   const AgentLayout al = agent_layout(p);
   API_TRY(check_ws(ws, ws_bytes, al.bytes, "clamp_forward_prox"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   cudaStream_t st = (cudaStream_t)stream;
   Derived d;
-  API_TRY(derive(p, pupil, window, st, &d));
+  API_TRY(recon_prepare(p, pupil, window, st, &d));
   API_TRY(agent_ffts(d, y, pupil, window, reinterpret_cast<float2*>(mu), r, al, ws, st));
   if (mu_residual) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_residual, st), "mu residual");
   PassC c = passc_args(p, d, al, ws, reinterpret_cast<float2*>(mu), r, const_cast<float*>(w), nullptr, k);
@@ -353,7 +354,7 @@ extern "C" clamp_status clamp_mace_step(const clamp_params* p, const float* r, f
   API_TRY(need_ptrs({r, w, wbar}, "clamp_mace_step"));
   const AgentLayout al = agent_layout(p);
   API_TRY(check_ws(ws, ws_bytes, al.bytes, "clamp_mace_step"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   cudaStream_t st = (cudaStream_t)stream;
   Derived d{};
   d.g = Geom{p->nx, p->ny, p->nz, p->looks, (long long)p->nx * p->ny * p->nz};
@@ -366,16 +367,16 @@ extern "C" clamp_status clamp_mace_step(const clamp_params* p, const float* r, f
 
 extern "C" clamp_status clamp_denoise(const clamp_denoiser* den, const float* w_prior, float* r_prior, int32_t nx,
                                       int32_t ny, int32_t nz, void* ws, size_t ws_bytes, void* stream) {
-  if (!den) return fail(CLAMP_EINVAL, "denoiser is NULL");
+  if (!den) return api_fail(CLAMP_EINVAL, "denoiser is NULL");
   if (nx < 1 || ny < 1 || nz < 1 || nx > 4096 || ny > 4096 || nz > 4096)
-    return fail(CLAMP_EINVAL, "denoiser volume %dx%dx%d out of range", nx, ny, nz);
+    return api_fail(CLAMP_EINVAL, "denoiser volume %dx%dx%d out of range", nx, ny, nz);
   API_TRY(need_ptrs({w_prior, r_prior}, "clamp_denoise"));
   if (!denoise_supports(den, nx, ny, nz))
-    return fail(CLAMP_EUNSUPPORTED, "BF16 CNN prior needs nx %% 128 == 0, ny %% 4 == 0, nz %% 2 == 0 (got %dx%dx%d)",
+    return api_fail(CLAMP_EUNSUPPORTED, "BF16 CNN prior needs nx %% 128 == 0, ny %% 4 == 0, nz %% 2 == 0 (got %dx%dx%d)",
                 nx, ny, nz);
   const size_t need = denoise_ws_bytes(den, nx, ny, nz);
   if (need) API_TRY(check_ws(ws, ws_bytes, need, "clamp_denoise"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   API_CUDA(denoise_apply(den, w_prior, r_prior, nx, ny, nz, ws, nullptr, (cudaStream_t)stream), "denoiser");
   return CLAMP_OK;
 }
@@ -421,22 +422,48 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
   return CLAMP_OK;
 }
 
+// Initialisation and p->max_iters iterations with no host synchronisation (capturable).
+clamp_status recon_enqueue(const clamp_params* p, const ReconPlan& d, const float* y, const float* pupil,
+                           const float* window, const clamp_denoiser* den, const float* r_init, float* r_out, void* ws,
+                           cudaStream_t st) {
+  const ReconLayout rl = recon_layout(p, den);
+  const AgentLayout al = agent_layout(p);
+  void* aws = static_cast<char*>(ws) + rl.agent;
+  float2* mu = at<float2>(ws, rl.mu);
+  float* r = at<float>(ws, rl.r);
+  float* w = at<float>(ws, rl.w);
+  const long long n = (long long)p->nx * p->ny * p->nz;
+  API_CUDA(cudaMemsetAsync(at<int>(aws, al.err), 0, sizeof(int), st), "memset");
+  API_TRY(do_init(p, d, y, pupil, window, r_init, mu, r, w, al, aws, st));
+  if (p->max_iters == 0)
+    API_CUDA(cudaMemcpyAsync(r_out, r + (long long)p->looks * n, n * sizeof(float), cudaMemcpyDeviceToDevice, st),
+             "copy");
+  for (int it = 0; it < p->max_iters; ++it)
+    API_TRY(iterate_impl(p, d, p->k0 + it + 1, 1, y, pupil, window, den, mu, r, w, r_out,
+                         at<double>(ws, rl.ce_ring) + it, at<double>(ws, rl.mu_ring) + it, aws, nullptr, st));
+  return CLAMP_OK;
+}
+
+const double* recon_ce_ring(const clamp_params* p, const clamp_denoiser* den, const void* ws) {
+  return reinterpret_cast<const double*>(static_cast<const char*>(ws) + recon_layout(p, den).ce_ring);
+}
+
 extern "C" clamp_status clamp_iterate(const clamp_params* p, int32_t k_first, int32_t iters, const float* y,
                                       const float* pupil, const float* window, const clamp_denoiser* den, float* mu,
                                       float* r, float* w, float* wbar, double* ce_out, double* mu_out, void* ws,
                                       size_t ws_bytes, void* const* events, void* stream) {
   API_TRY(clamp_check_params(p));
-  if (!den) return fail(CLAMP_EINVAL, "clamp_iterate: denoiser is NULL");
+  if (!den) return api_fail(CLAMP_EINVAL, "clamp_iterate: denoiser is NULL");
   if (!denoise_supports(den, p->nx, p->ny, p->nz))
-    return fail(CLAMP_EUNSUPPORTED, "clamp_iterate: the prior agent does not support this volume");
-  if (k_first < 1 || iters < 0) return fail(CLAMP_EINVAL, "clamp_iterate: k_first=%d must be >= 1, iters >= 0",
+    return api_fail(CLAMP_EUNSUPPORTED, "clamp_iterate: the prior agent does not support this volume");
+  if (k_first < 1 || iters < 0) return api_fail(CLAMP_EINVAL, "clamp_iterate: k_first=%d must be >= 1, iters >= 0",
                                             k_first);
   API_TRY(need_ptrs({y, pupil, window, mu, r, w, wbar}, "clamp_iterate"));
   API_TRY(check_ws(ws, ws_bytes, iterate_ws_bytes(p, den), "clamp_iterate"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   cudaStream_t st = (cudaStream_t)stream;
   Derived d;
-  API_TRY(derive(p, pupil, window, st, &d));
+  API_TRY(recon_prepare(p, pupil, window, st, &d));
   API_CUDA(cudaMemsetAsync(at<int>(ws, agent_layout(p).err), 0, sizeof(int), st), "memset");
   return iterate_impl(p, d, k_first, iters, y, pupil, window, den, reinterpret_cast<float2*>(mu), r, w, wbar, ce_out,
                       mu_out, ws, events, st);
@@ -455,7 +482,7 @@ static clamp_status reconstruct_impl(const clamp_params* p, const float* y, cons
   double* mu_ring = at<double>(ws, rl.mu_ring);
   const long long n = (long long)p->nx * p->ny * p->nz;
   Derived d;
-  API_TRY(derive(p, pupil, window, st, &d));
+  API_TRY(recon_prepare(p, pupil, window, st, &d));
   API_CUDA(cudaMemsetAsync(at<int>(aws, al.err), 0, sizeof(int), st), "memset");
   API_TRY(do_init(p, d, y, pupil, window, r_init, mu, r, w, al, aws, st));
   if (p->max_iters == 0) {
@@ -481,8 +508,8 @@ static clamp_status reconstruct_impl(const clamp_params* p, const float* y, cons
                "residual readback");
       API_CUDA(cudaMemcpyAsync(&herr, at<int>(aws, al.err), sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
       API_CUDA(cudaStreamSynchronize(st), "residual readback");
-      if (herr & 2) return fail(CLAMP_ETIMEOUT, "a bounded tensor-core wait gave up at or before iteration %d", k);
-      if (herr) return fail(CLAMP_ENONFINITE, "non-finite value in the state at or before iteration %d", k);
+      if (herr & 2) return api_fail(CLAMP_ETIMEOUT, "a bounded tensor-core wait gave up at or before iteration %d", k);
+      if (herr) return api_fail(CLAMP_ENONFINITE, "non-finite value in the state at or before iteration %d", k);
       for (int i = synced_upto; i < done; ++i) {
         if (p->tol > 0 && ce_h[i] <= p->tol) {
           converged = true;
@@ -515,11 +542,11 @@ extern "C" clamp_status clamp_reconstruct(const clamp_params* p, const float* y,
                                           float* r_out, clamp_report* report, void* ws, size_t ws_bytes,
                                           void* stream) {
   API_TRY(clamp_check_params(p));
-  if (!den) return fail(CLAMP_EINVAL, "clamp_reconstruct: denoiser is NULL");
+  if (!den) return api_fail(CLAMP_EINVAL, "clamp_reconstruct: denoiser is NULL");
   if (!denoise_supports(den, p->nx, p->ny, p->nz))
-    return fail(CLAMP_EUNSUPPORTED, "clamp_reconstruct: the prior agent does not support this volume");
+    return api_fail(CLAMP_EUNSUPPORTED, "clamp_reconstruct: the prior agent does not support this volume");
   API_TRY(need_ptrs({y, pupil, window, r_out}, "clamp_reconstruct"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   cudaStream_t st = (cudaStream_t)stream;
   const size_t need = recon_layout(p, den).bytes;
   void* own = nullptr;
@@ -568,11 +595,11 @@ extern "C" clamp_status clamp_reconstruct_host(const clamp_params* p, const floa
                                                const float* r_init_host, float* r_out_host, clamp_report* report,
                                                void* stream) {
   API_TRY(clamp_check_params(p));
-  if (!den) return fail(CLAMP_EINVAL, "clamp_reconstruct_host: denoiser is NULL");
+  if (!den) return api_fail(CLAMP_EINVAL, "clamp_reconstruct_host: denoiser is NULL");
   if (!denoise_supports(den, p->nx, p->ny, p->nz))
-    return fail(CLAMP_EUNSUPPORTED, "clamp_reconstruct_host: the prior agent does not support this volume");
+    return api_fail(CLAMP_EUNSUPPORTED, "clamp_reconstruct_host: the prior agent does not support this volume");
   API_TRY(need_ptrs({y_host, pupil_host, window_host, r_out_host}, "clamp_reconstruct_host"));
-  API_TRY(ensure_device());
+  API_TRY(api_ensure_device());
   cudaStream_t st = (cudaStream_t)stream;
   const long long n = (long long)p->nx * p->ny * p->nz, L = p->looks;
   Arena ar;

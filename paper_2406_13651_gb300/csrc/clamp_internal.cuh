@@ -1,0 +1,27 @@
+// clamp_internal.cuh -- pieces of the C ABI implementation shared between translation units.
+#pragma once
+#include "../../include/clamp.h"
+#include "clamp_kernels.cuh"
+
+// Records an error message for clamp_last_error() and returns `s`.
+clamp_status api_fail(clamp_status s, const char* fmt, ...);
+// Per-device set-up (twiddle tables); idempotent.
+clamp_status api_ensure_device();
+
+// Per-problem constants: geometry, alpha = mean(a^2), noise floor, FFT scales.
+struct ReconPlan {
+  clamp::Geom g;
+  clamp::AgentScalars s;
+  double alpha;
+};
+
+// Reads the aperture back to compute alpha (synchronises `st`): call before any capture.
+clamp_status recon_prepare(const clamp_params* p, const float* pupil, const float* window, cudaStream_t st,
+                           ReconPlan* out);
+// Enqueues the Alg. 2 initialisation and p->max_iters iterations on `st` without any host
+// synchronisation; ws is laid out as for clamp_reconstruct.
+clamp_status recon_enqueue(const clamp_params* p, const ReconPlan& plan, const float* y, const float* pupil,
+                           const float* window, const clamp_denoiser* den, const float* r_init, float* r_out,
+                           void* ws, cudaStream_t st);
+// Device ring of per-iteration convergence errors inside a clamp_reconstruct workspace.
+const double* recon_ce_ring(const clamp_params* p, const clamp_denoiser* den, const void* ws);

@@ -27,7 +27,7 @@ __device__ float2 g_tw[kTwTotal];
 
 cudaError_t upload_twiddles() {
   std::vector<float2> h(kTwTotal);
-  for (int N = 8; N <= 256; N *= 2) {
+  for (int N : kFftLengths) {
     const int off = tw_offset(N);
     for (int m = 0; m < N; ++m) {
       const double ang = -2.0 * M_PI * (double)m / (double)N;
@@ -363,7 +363,9 @@ static cudaError_t dispatch_len(int N, F&& f) {
     case 16: return f(std::integral_constant<int, 16>{});
     case 32: return f(std::integral_constant<int, 32>{});
     case 64: return f(std::integral_constant<int, 64>{});
+    case 96: return f(std::integral_constant<int, 96>{});
     case 128: return f(std::integral_constant<int, 128>{});
+    case 192: return f(std::integral_constant<int, 192>{});
     case 256: return f(std::integral_constant<int, 256>{});
     default: return cudaErrorInvalidValue;
   }

@@ -9,7 +9,7 @@ constexpr int NT = 256;   // threads per CTA in every FFT pass
 constexpr int LC = 16;    // adjacent x-columns per CTA in the y / z passes
 
 // Rows (x-lines) per CTA in the x passes.
-__host__ __device__ constexpr int rows_per_cta(int N) { return N <= 32 ? 64 : (N <= 128 ? 32 : 16); }
+__host__ __device__ constexpr int rows_per_cta(int N) { return N <= 32 ? 64 : (N <= 128 ? 32 : 16); }  // 96 -> 32, 192 -> 16
 
 struct Geom {
   int nx, ny, nz, L;

@@ -110,12 +110,15 @@ template <> struct Plan<32>  { static constexpr int R1 = 8,  R2 = 4,  R3 = 1; };
 template <> struct Plan<64>  { static constexpr int R1 = 8,  R2 = 8,  R3 = 1; };
 template <> struct Plan<128> { static constexpr int R1 = 16, R2 = 8,  R3 = 1; };
 template <> struct Plan<256> { static constexpr int R1 = 16, R2 = 16, R3 = 1; };
+template <> struct Plan<96>  { static constexpr int R1 = 8,  R2 = 4,  R3 = 3; };
+template <> struct Plan<192> { static constexpr int R1 = 16, R2 = 4,  R3 = 3; };
 
-// Offset of the length-N twiddle table inside the packed table (N = 8..256).
+// Offset of the length-N twiddle table inside the packed table (N = 8..256 powers of two, 96, 192).
 __host__ __device__ constexpr int tw_offset(int N) {
-  return N == 8 ? 0 : N == 16 ? 8 : N == 32 ? 24 : N == 64 ? 56 : N == 128 ? 120 : 248;
+  return N == 8 ? 0 : N == 16 ? 8 : N == 32 ? 24 : N == 64 ? 56 : N == 128 ? 120 : N == 256 ? 248 : N == 96 ? 504 : 600;
 }
-constexpr int kTwTotal = 504;
+constexpr int kTwTotal = 792;
+constexpr int kFftLengths[] = {8, 16, 32, 64, 96, 128, 192, 256};
 
 // One Stockham stage over all LT lines of the tile.
 template <int N, int R, int NS, int LT, int NT, bool INV>

@@ -275,3 +275,34 @@ def make_workload(name: str, seed: int = 1, *, nx=None, ny=None, nz=None, looks=
     return Workload(name=name, nx=nx, ny=ny, nz=nz, looks=L, r_true=r, speckle=spk, noise=eta,
                     pupil=pupil, window=window, noise_var=float(nv), prox_var=1e-4,
                     iters=iters or p["iters"], denoiser=den)
+
+
+def batch_specs(count: int = 24, seed: int = 7, lateral=(64, 96, 128, 192, 256), rng_z=(32, 64, 128),
+                looks=(4, 32), iters: int = 10):
+    """Seeded shapes and parameters of a batch of uneven scenes: square lateral size from
+    ``lateral``, range size from ``rng_z``, looks uniform in ``looks`` (inclusive), pupil
+    radius U[0.3, 0.5] Nyquist, SNR U[5, 20] dB."""
+    u = uniform(seed, 500, 6 * count).reshape(count, 6)
+    specs = []
+    for i in range(count):
+        nxy = lateral[int(u[i, 0] * len(lateral)) % len(lateral)]
+        nz = rng_z[int(u[i, 1] * len(rng_z)) % len(rng_z)]
+        L = looks[0] + int(u[i, 2] * (looks[1] - looks[0] + 1)) % (looks[1] - looks[0] + 1)
+        specs.append(dict(nx=nxy, ny=nxy, nz=nz, looks=L, radius=0.3 + 0.2 * u[i, 3], snr=5.0 + 15.0 * u[i, 4],
+                          seed=seed * 1000 + i, iters=iters))
+    return specs
+
+
+def batch_scene(spec: dict, with_draws: bool = True) -> Workload:
+    """One scene of a batch (column-surface scene, Gaussian prior) from a spec of batch_specs."""
+    nx, ny, nz, L, seed = spec["nx"], spec["ny"], spec["nz"], spec["looks"], spec["seed"]
+    r = column_surface_scene(nx, ny, nz, seed)
+    pupil = circular_pupil(nx, ny, spec["radius"])
+    window = hann_window(nz)
+    nv = noise_variance_for_snr(r, pupil, window, spec["snr"])
+    shape = (L, nz, ny, nx)
+    spk = complex_normal(seed, 20, shape) if with_draws else None
+    eta = complex_normal(seed, 21, shape) if with_draws else None
+    return Workload(name="batch", nx=nx, ny=ny, nz=nz, looks=L, r_true=r, speckle=spk, noise=eta, pupil=pupil,
+                    window=window, noise_var=float(nv), prox_var=1e-4, iters=spec["iters"],
+                    denoiser={"kind": "gauss", "sigma": 0.8})

@@ -37,7 +37,7 @@ def test_params_struct_layout_matches_header():
 
 
 def test_supported_lengths(lib):
-    assert [lib.clamp_supported_length(n) for n in (4, 8, 16, 24, 32, 64, 128, 256, 512)] == [0, 1, 1, 0, 1, 1, 1, 1, 0]
+    assert [lib.clamp_supported_length(n) for n in (4, 8, 16, 24, 32, 64, 96, 128, 192, 256, 512)] == [0, 1, 1, 0, 1, 1, 1, 1, 1, 1, 0]
 
 
 @pytest.mark.parametrize("field,value", [("nx", 48), ("nz", 4), ("nx", 8), ("looks", 0), ("noise_var", 0.0),

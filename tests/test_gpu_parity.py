@@ -57,7 +57,7 @@ def params(C, wl, **kw):
 
 # ------------------------------------------------------------------ FFT (Eq. A)
 
-@pytest.mark.parametrize("shape", [(8, 16, 16), (16, 16, 16), (16, 32, 32), (64, 128, 128), (256, 16, 16), (16, 256, 16),
+@pytest.mark.parametrize("shape", [(32, 96, 96), (64, 192, 96), (32, 64, 192), (96, 16, 16), (8, 16, 16), (16, 16, 16), (16, 32, 32), (64, 128, 128), (256, 16, 16), (16, 256, 16),
                                    (16, 16, 256), (32, 64, 128), (128, 256, 256)])
 def test_fft3_matches_oracle(C, shape):
     rng = np.random.default_rng(0)
@@ -141,6 +141,23 @@ def test_forward_prox_matches_oracle(C, k):
     # the prior row is untouched
     np.testing.assert_array_equal(r.cpu().numpy()[wl.looks], st.r[wl.looks].astype(np.float32))
     assert mres.item() == pytest.approx(mres_ref, rel=1e-4)
+
+
+@pytest.mark.parametrize("nx,ny,nz", [(96, 96, 32), (192, 64, 32)])
+def test_forward_prox_radix3_sizes(C, nx, ny, nz):
+    """Lateral sizes 96 and 192 (radix-3 stages) of the batched workload."""
+    wl, a, y32, y64 = problem("cfg1", seed=9, nx=nx, ny=ny, nz=nz, looks=3)
+    st = O.init_state(y64, a)
+    st.mu = st.mu.astype(np.complex64).astype(np.complex128)
+    st.r = st.r.astype(np.float32).astype(np.float64)
+    st.w = (st.w * 1.1).astype(np.float32).astype(np.float64)
+    mu_ref, r_ref, _ = _agent_reference(st, y64, a, wl, 4)
+    p = params(C, wl)
+    mu, r, w = to_dev(st.mu.astype(np.complex64)), to_dev(st.r.astype(np.float32)), to_dev(st.w.astype(np.float32))
+    C.forward_prox(p, 4, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), mu, r, w)
+    torch.cuda.synchronize()
+    assert rel(mu.cpu().numpy(), mu_ref) < TOL_RECON
+    assert rel(r.cpu().numpy()[:wl.looks], r_ref) < TOL_RECON
 
 
 def test_forward_prox_single_look_no_aperture(C):
