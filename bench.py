@@ -365,6 +365,7 @@ def main():
     del spk, eta
     y_host = None
     den = C.Denoiser.from_desc(wl.denoiser)
+    variants = C.autotune(p, y, pupil, window)   # per-pass FFT launch variants, cached for this geometry
     mu, r, w = C.init(p, y, pupil, window)
     wbar = torch.empty((wl.nz, wl.ny, wl.nx), dtype=torch.float32, device=dev)
     ws = C.iterate_workspace(p, den)
@@ -515,6 +516,7 @@ def main():
         "gpu_launches": launches_per_iter * K,
         "clocks": clk.summary(),
         "ce_residual_last": ce_last, "finite": finite,
+        "fft_variants": {"passes": ["x", "y", "z fused", "inverse y", "inverse x"], "chosen": variants},
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -224,6 +224,18 @@ clamp_status clamp_reconstruct_host(const clamp_params* p, const float* y_host,
                                     float* r_out_host, clamp_report* report, void* stream);
 void clamp_release_cache(void);
 
+/* ---- Autotuner.  Each forward-agent FFT pass (x, y, fused z, inverse y, inverse x) has
+ * launch variants: 0 = default radix plan and tile, 1 = alternative radix plan,
+ * 2 = other tile schedule (half the rows per CTA in x passes, 32 columns per CTA in
+ * y / z passes).  The tuner times every valid variant of each pass on `ws` (a
+ * clamp_workspace_size buffer; its contents are overwritten) and caches the fastest per
+ * (device, nx, ny, nz, looks); every later call on that geometry uses the cached choice.
+ * variants_out: optional host int32[5].  Synchronises. */
+clamp_status clamp_autotune(const clamp_params* p, const float* y, const float* pupil, const float* window,
+                            void* ws, size_t ws_bytes, void* stream, int32_t* variants_out);
+/* Sets the cached choice for a geometry by hand (host int32[5]). */
+clamp_status clamp_autotune_set(const clamp_params* p, const int32_t* variants);
+
 /* ---- Batched reconstruction: many scenes of uneven size and look count in one launch. */
 
 /* One scene of a batch: its parameters (shape, looks, variances, iterations) and DEVICE
@@ -241,7 +253,8 @@ typedef struct clamp_batch clamp_batch;  /* opaque plan: captured CUDA graph + p
 /* Scratch bytes for a batch (the sum of the scenes' reconstruction workspaces). */
 size_t clamp_batch_workspace_size(const clamp_scene* scenes, int32_t count, const clamp_denoiser* den);
 
-/* Builds a batch plan: checks every scene, partitions `ws` among them and captures
+/* Builds a batch plan: checks every scene, partitions `ws` among them, autotunes the
+ * forward-agent passes of every distinct scene geometry (clamp_autotune) and captures
  * into ONE CUDA graph, for every scene as an independent branch, the Alg. 2
  * initialisation followed by p.max_iters iterations (forward agents, prior agent,
  * MACE step), with a timing event at the start and at the end of each branch.

@@ -34,7 +34,7 @@ EXPORTS = [
     "clamp_iterate", "clamp_iterate_workspace_size", "clamp_mace_step_noalloc",
     "clamp_tc_gemm_bf16", "clamp_tc_gemm_tf32x3",
     "clamp_batch_workspace_size", "clamp_batch_create", "clamp_batch_launch", "clamp_batch_latencies",
-    "clamp_batch_residuals", "clamp_batch_destroy",
+    "clamp_batch_residuals", "clamp_batch_destroy", "clamp_autotune", "clamp_autotune_set",
 ]
 
 
@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_batch_latencies": (I, [P, P, ctypes.POINTER(ctypes.c_float)]),
         "clamp_batch_residuals": (I, [P, P, ctypes.POINTER(ctypes.c_double)]),
         "clamp_batch_destroy": (V, [P]),
+        "clamp_autotune": (I, [PP, P, P, P, P, S, P, ctypes.POINTER(ctypes.c_int32)]),
+        "clamp_autotune_set": (I, [PP, ctypes.POINTER(ctypes.c_int32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -204,6 +206,21 @@ def workspace(p: Params):
     if n == 0:
         _check(load().clamp_check_params(ctypes.byref(p)), "clamp_workspace_size")
     return _ws(n)
+
+
+def autotune(p: Params, y, pupil, window, ws=None, stream=None) -> list:
+    """Times the forward-agent pass variants for this geometry and caches the fastest;
+    returns the chosen variant of each of the 5 passes."""
+    ws = workspace(p) if ws is None else ws
+    out = (ctypes.c_int32 * 5)()
+    _check(load().clamp_autotune(ctypes.byref(p), _ptr(y), _ptr(pupil), _ptr(window), _ptr(ws), ws.numel(),
+                                 _stream(stream), out), "clamp_autotune")
+    return list(out)
+
+
+def autotune_set(p: Params, variants) -> None:
+    arr = (ctypes.c_int32 * 5)(*variants)
+    _check(load().clamp_autotune_set(ctypes.byref(p), arr), "clamp_autotune_set")
 
 
 def fft3(x, inverse: bool = False, out=None, stream=None):

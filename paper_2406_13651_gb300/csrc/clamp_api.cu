@@ -10,8 +10,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <mutex>
 #include <set>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -111,8 +113,8 @@ struct AgentLayout {
 AgentLayout agent_layout(const clamp_params* p) {
   AgentLayout a{};
   const long long n = (long long)p->nx * p->ny * p->nz, L = p->looks;
-  a.pz = (p->nx / LC) * p->ny;
-  a.px = (int)((long long)p->nz * p->ny / rows_per_cta(p->nx));
+  a.pz = max_pz(p->nx, p->ny);              // largest partial counts over all launch variants
+  a.px = max_px(p->nx, p->ny, p->nz);
   a.nbc = passc_blocks(n);
   Arena ar;
   a.T = ar.take<float4>(L * n);
@@ -296,13 +298,119 @@ extern "C" clamp_status clamp_init(const clamp_params* p, const float* y, const 
 
 static float beta_of(int k) { return (float)(1.0 + 2.0 / log((double)k + 1.0)); }
 
+// ---------------------------------------------------------------- autotuner cache
+
+namespace {
+struct TuneKey {
+  int dev, nx, ny, nz, L;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, nx, ny, nz, L) < std::tie(o.dev, o.nx, o.ny, o.nz, o.L);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, AgentVariants> g_tune;
+
+TuneKey tune_key(const Geom& g) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return TuneKey{dev, g.nx, g.ny, g.nz, g.L};
+}
+
+AgentVariants tuned_variants(const Geom& g) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(tune_key(g));
+  return it == g_tune.end() ? AgentVariants{} : it->second;
+}
+}  // namespace
+
 static clamp_status agent_ffts(const Derived& d, const float* y, const float* pupil, const float* window,
                                const float2* mu, const float* r, const AgentLayout& al, void* ws, cudaStream_t st) {
+  Partials pt = partials(al, ws);
   API_CUDA(launch_agent_fft(d.g, d.s, mu, r, reinterpret_cast<const float2*>(y), pupil, window,
-                            at<float4>(ws, al.T), at<float2>(ws, al.U), partials(al, ws), st),
+                            at<float4>(ws, al.T), at<float2>(ws, al.U), pt, tuned_variants(d.g), st),
            "forward-agent FFT passes");
-  API_CUDA(launch_gamma(d.g, d.s.nv, partials(al, ws), at<float>(ws, al.gamma), at<double>(ws, al.mures), st),
-           "line search");
+  API_CUDA(launch_gamma(d.g, d.s.nv, pt, at<float>(ws, al.gamma), at<double>(ws, al.mures), st), "line search");
+  return CLAMP_OK;
+}
+
+// Times every valid launch variant of each forward-agent pass on the agent scratch `ws`
+// (contents irrelevant: the passes have no data-dependent control flow) and stores the
+// fastest per pass for this geometry.  Synchronises `st`.
+clamp_status autotune_agent(const clamp_params* p, const ReconPlan& d, const float* y, const float* pupil,
+                            const float* window, void* ws, cudaStream_t st, AgentVariants* out) {
+  const AgentLayout al = agent_layout(p);
+  float4* T = at<float4>(ws, al.T);
+  float2* U = at<float2>(ws, al.U);
+  const float2* mu = U;                                  // timing only: any buffers of the right size
+  const float* rp = reinterpret_cast<const float*>(U);
+  cudaEvent_t e0, e1;
+  API_CUDA(cudaEventCreate(&e0), "event");
+  API_CUDA(cudaEventCreate(&e1), "event");
+  AgentVariants best;
+  for (int pass = 0; pass < 5; ++pass) {
+    float best_ms = 1e30f;
+    for (int V = 0; V < kVariants; ++V) {
+      if (!variant_valid(pass, V, p->nx, p->ny, p->nz)) continue;
+      Partials pt = partials(al, ws);
+      cudaError_t e = launch_agent_pass(pass, V, d.g, d.s, mu, rp, reinterpret_cast<const float2*>(y), pupil, window,
+                                        T, U, pt, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+        e = launch_agent_pass(pass, V, d.g, d.s, mu, rp, reinterpret_cast<const float2*>(y), pupil, window, T, U, pt,
+                              st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return cuda_fail(e, "autotune");
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best.v[pass] = V;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(d.g)] = best;
+  }
+  if (out) *out = best;
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_autotune(const clamp_params* p, const float* y, const float* pupil, const float* window,
+                                       void* ws, size_t ws_bytes, void* stream, int32_t* variants_out) {
+  API_TRY(clamp_check_params(p));
+  API_TRY(need_ptrs({y, pupil, window}, "clamp_autotune"));
+  API_TRY(check_ws(ws, ws_bytes, agent_layout(p).bytes, "clamp_autotune"));
+  API_TRY(api_ensure_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  Derived d;
+  API_TRY(recon_prepare(p, pupil, window, st, &d));
+  AgentVariants v;
+  API_TRY(autotune_agent(p, d, y, pupil, window, ws, st, &v));
+  if (variants_out)
+    for (int i = 0; i < 5; ++i) variants_out[i] = v.v[i];
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_autotune_set(const clamp_params* p, const int32_t* variants) {
+  API_TRY(clamp_check_params(p));
+  if (!variants) return api_fail(CLAMP_EINVAL, "clamp_autotune_set: variants is NULL");
+  AgentVariants v;
+  for (int i = 0; i < 5; ++i) {
+    if (!variant_valid(i, variants[i], p->nx, p->ny, p->nz))
+      return api_fail(CLAMP_EINVAL, "clamp_autotune_set: variant %d not valid for pass %d", variants[i], i);
+    v.v[i] = variants[i];
+  }
+  Geom g{p->nx, p->ny, p->nz, p->looks, (long long)p->nx * p->ny * p->nz};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[tune_key(g)] = v;
   return CLAMP_OK;
 }
 
@@ -443,6 +551,8 @@ clamp_status recon_enqueue(const clamp_params* p, const ReconPlan& d, const floa
                          at<double>(ws, rl.ce_ring) + it, at<double>(ws, rl.mu_ring) + it, aws, nullptr, st));
   return CLAMP_OK;
 }
+
+size_t recon_agent_offset(const clamp_params* p, const clamp_denoiser* den) { return recon_layout(p, den).agent; }
 
 const double* recon_ce_ring(const clamp_params* p, const clamp_denoiser* den, const void* ws) {
   return reinterpret_cast<const double*>(static_cast<const char*>(ws) + recon_layout(p, den).ce_ring);

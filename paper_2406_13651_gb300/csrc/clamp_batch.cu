@@ -11,6 +11,7 @@
 #include "clamp_internal.cuh"
 #include "denoise.cuh"
 
+#include <array>
 #include <string>
 #include <vector>
 
@@ -112,8 +113,19 @@ extern "C" clamp_status clamp_batch_create(const clamp_scene* scenes, int32_t co
   // Everything that synchronises (aperture statistics) happens before the capture, and one
   // un-captured iteration per scene loads every kernel and sets its launch attributes.
   std::vector<ReconPlan> plans(count);
+  std::vector<std::array<int, 4>> tuned;
   for (int i = 0; ok && i < count; ++i) {
     st = recon_prepare(&b->scenes[i].p, b->scenes[i].pupil, b->scenes[i].window, b->streams[i], &plans[i]);
+    const clamp_params& sp = b->scenes[i].p;
+    const std::array<int, 4> key{sp.nx, sp.ny, sp.nz, sp.looks};
+    bool seen = false;
+    for (auto& k : tuned) seen |= (k == key);
+    if (st == CLAMP_OK && !seen) {   // one autotuning run per distinct geometry, on this scene's agent scratch
+      char* agent_ws = static_cast<char*>(ws) + b->ws_off[i] + recon_agent_offset(&sp, den);
+      st = autotune_agent(&sp, plans[i], b->scenes[i].y, b->scenes[i].pupil, b->scenes[i].window, agent_ws,
+                          b->streams[i], nullptr);
+      tuned.push_back(key);
+    }
     if (st == CLAMP_OK) {
       clamp_params one = b->scenes[i].p;
       one.max_iters = 1;

@@ -25,3 +25,9 @@ clamp_status recon_enqueue(const clamp_params* p, const ReconPlan& plan, const f
                            void* ws, cudaStream_t st);
 // Device ring of per-iteration convergence errors inside a clamp_reconstruct workspace.
 const double* recon_ce_ring(const clamp_params* p, const clamp_denoiser* den, const void* ws);
+// Times the launch variants of the forward-agent passes on agent scratch `ws` and caches the
+// fastest per geometry (synchronises `st`).
+clamp_status autotune_agent(const clamp_params* p, const ReconPlan& plan, const float* y, const float* pupil,
+                            const float* window, void* ws, cudaStream_t st, clamp::AgentVariants* out);
+// Byte offset of the forward-agent scratch inside a clamp_reconstruct workspace.
+size_t recon_agent_offset(const clamp_params* p, const clamp_denoiser* den);

@@ -74,11 +74,12 @@ __device__ __forceinline__ void block_reduce_store(const float (&v)[NV], double*
 
 // ---------------------------------------------------------------- pass A_x
 
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(NT) k_a_x(Geom g, AgentScalars s, const float2* __restrict__ mu,
                                             const float* __restrict__ rprev, float4* __restrict__ T,
                                             const float2* __restrict__ tw) {
-  constexpr int LX = rows_per_cta(N), LT = 2 * LX, LD = N + 1;
+  constexpr int LX = variant_rows(N, V), LT = 2 * LX, LD = N + 1;
+  using PL = std::conditional_t<V == 1, PlanB<N>, Plan<N>>;
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
   constexpr int CNT = LX * N, PER = (CNT + NT - 1) / NT;
   const long long e0 = (long long)blockIdx.x * LX * N;  // first element of the tile
@@ -103,7 +104,7 @@ __global__ void __launch_bounds__(NT) k_a_x(Geom g, AgentScalars s, const float2
     }
   }
   __syncthreads();
-  fft_tile<N, LT, NT, false>(sm, tw);
+  fft_tile<N, LT, NT, false, PL>(sm, tw);
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
@@ -118,38 +119,39 @@ __global__ void __launch_bounds__(NT) k_a_x(Geom g, AgentScalars s, const float2
 
 // ---------------------------------------------------------------- pass A_y (in place on T)
 
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(NT) k_a_y(Geom g, AgentScalars s, float4* __restrict__ T,
                                             const float2* __restrict__ tw) {
-  constexpr int LT = 2 * LC, LD = N + 1;
+  constexpr int LCV = variant_cols(V), LT = 2 * LCV, LD = N + 1;
+  using PL = std::conditional_t<V == 1, PlanB<N>, Plan<N>>;
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
   const long long S = g.nx;
-  constexpr int CNT = LC * N, PER = (CNT + NT - 1) / NT;
-  const long long base = (long long)blockIdx.z * g.n + (long long)blockIdx.y * g.ny * g.nx + blockIdx.x * LC;
+  constexpr int CNT = LCV * N, PER = (CNT + NT - 1) / NT;
+  const long long base = (long long)blockIdx.z * g.n + (long long)blockIdx.y * g.ny * g.nx + blockIdx.x * LCV;
   float4 tv[PER];
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
-    if (CNT % NT == 0 || e < CNT) tv[p] = T[base + (e / LC) * S + e % LC];
+    if (CNT % NT == 0 || e < CNT) tv[p] = T[base + (e / LCV) * S + e % LCV];
   }
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
-      const int line = e % LC, i = e / LC;
+      const int line = e % LCV, i = e / LCV;
       sm[line * LD + i] = make_float2(tv[p].x, tv[p].y);
-      sm[(LC + line) * LD + i] = make_float2(tv[p].z, tv[p].w);
+      sm[(LCV + line) * LD + i] = make_float2(tv[p].z, tv[p].w);
     }
   }
   __syncthreads();
-  fft_tile<N, LT, NT, false>(sm, tw);
+  fft_tile<N, LT, NT, false, PL>(sm, tw);
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
-      const int line = e % LC, i = e / LC;
+      const int line = e % LCV, i = e / LCV;
       const float2 a = cscale(sm[line * LD + i], s.sc_y);
-      const float2 b = cscale(sm[(LC + line) * LD + i], s.sc_y);
+      const float2 b = cscale(sm[(LCV + line) * LD + i], s.sc_y);
       T[base + i * S + line] = make_float4(a.x, a.y, b.x, b.y);
     }
   }
@@ -157,38 +159,39 @@ __global__ void __launch_bounds__(NT) k_a_y(Geom g, AgentScalars s, float4* __re
 
 // ---------------------------------------------------------------- fused z pass (A_z + gradient + B_z)
 
-template <int N>
+template <int N, int V>
 __global__ void __launch_bounds__(NT) k_ab_z(Geom g, AgentScalars s, const float4* __restrict__ T,
                                              const float2* __restrict__ y, const float* __restrict__ pupil,
                                              const float* __restrict__ window, float2* __restrict__ U,
                                              Partials p, const float2* __restrict__ tw) {
-  constexpr int LT = 2 * LC, LD = N + 1;
+  constexpr int LCV = variant_cols(V), LT = 2 * LCV, LD = N + 1;
+  using PL = std::conditional_t<V == 1, PlanB<N>, Plan<N>>;
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
   const long long S = (long long)g.nx * g.ny;
-  const int x0 = blockIdx.x * LC, ky = blockIdx.y, l = blockIdx.z;
+  const int x0 = blockIdx.x * LCV, ky = blockIdx.y, l = blockIdx.z;
   const long long base = (long long)l * g.n + (long long)ky * g.nx + x0;
-  constexpr int CNT = LC * N, PER = (CNT + NT - 1) / NT;
+  constexpr int CNT = LCV * N, PER = (CNT + NT - 1) / NT;
   float4 tv[PER];
   float2 yvs[PER];   // the data for the epilogue is fetched together with T
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
-      tv[p] = T[base + (e / LC) * S + e % LC];
-      yvs[p] = y[base + (e / LC) * S + e % LC];
+      tv[p] = T[base + (e / LCV) * S + e % LCV];
+      yvs[p] = y[base + (e / LCV) * S + e % LCV];
     }
   }
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
-      const int line = e % LC, i = e / LC;
+      const int line = e % LCV, i = e / LCV;
       sm[line * LD + i] = make_float2(tv[p].x, tv[p].y);
-      sm[(LC + line) * LD + i] = make_float2(tv[p].z, tv[p].w);
+      sm[(LCV + line) * LD + i] = make_float2(tv[p].z, tv[p].w);
     }
   }
   __syncthreads();
-  fft_tile<N, LT, NT, false>(sm, tw);
+  fft_tile<N, LT, NT, false, PL>(sm, tw);
   // frequency-domain gradient: Fd = a (y - a M) / sigma_w^2 - P
   float acc[3] = {0.f, 0.f, 0.f};
   const float inv_nv = 1.0f / s.nv;
@@ -196,9 +199,9 @@ __global__ void __launch_bounds__(NT) k_ab_z(Geom g, AgentScalars s, const float
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (!(CNT % NT == 0 || e < CNT)) continue;
-    const int line = e % LC, kz = e / LC;
+    const int line = e % LCV, kz = e / LCV;
     const float2 M = cscale(sm[line * LD + kz], s.sc_z);
-    const float2 P = cscale(sm[(LC + line) * LD + kz], s.sc_z);
+    const float2 P = cscale(sm[(LCV + line) * LD + kz], s.sc_z);
     const float av = __ldg(&pupil[ky * g.nx + x0 + line]) * __ldg(&window[kz]);
     const float2 yv = yvs[p];
     const float2 res = make_float2(fmaf(-av, M.x, yv.x), fmaf(-av, M.y, yv.y));
@@ -211,12 +214,12 @@ __global__ void __launch_bounds__(NT) k_ab_z(Geom g, AgentScalars s, const float
     sm[line * LD + kz] = fd;
   }
   __syncthreads();
-  fft_tile<N, LC, NT, true>(sm, tw);
+  fft_tile<N, LCV, NT, true, PL>(sm, tw);
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
-      const int line = e % LC, i = e / LC;
+      const int line = e % LCV, i = e / LCV;
       U[base + i * S + line] = cscale(sm[line * LD + i], s.sc_z);
     }
   }
@@ -242,9 +245,10 @@ struct RowArgs {
   int nx;
 };
 
-template <int N, bool INV, int MODE>
+template <int N, bool INV, int MODE, int V = 0>
 __global__ void __launch_bounds__(NT) k_row(RowArgs a, const float2* __restrict__ tw) {
-  constexpr int LX = rows_per_cta(N), LD = N + 1;
+  constexpr int LX = variant_rows(N, V), LD = N + 1;
+  using PL = std::conditional_t<V == 1, PlanB<N>, Plan<N>>;
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
   constexpr int CNT = LX * N, PER = (CNT + NT - 1) / NT;
   const long long e0 = (long long)blockIdx.x * LX * N;
@@ -268,7 +272,7 @@ __global__ void __launch_bounds__(NT) k_row(RowArgs a, const float2* __restrict_
     }
   }
   __syncthreads();
-  fft_tile<N, LX, NT, INV>(sm, tw);
+  fft_tile<N, LX, NT, INV, PL>(sm, tw);
   float acc[1] = {0.f};
   float rpv[PER];
   if constexpr (MODE == ROW_BX) {
@@ -311,24 +315,25 @@ struct ColArgs {
   int zaxis;           // 1 when the FFT axis is z (aperture epilogue / prologue)
 };
 
-template <int N, bool INV, int MODE>
+template <int N, bool INV, int MODE, int V = 0>
 __global__ void __launch_bounds__(NT) k_col(ColArgs a, const float2* __restrict__ tw) {
-  constexpr int LD = N + 1;
+  constexpr int LD = N + 1, LCV = variant_cols(V);
+  using PL = std::conditional_t<V == 1, PlanB<N>, Plan<N>>;
   float2* sm = reinterpret_cast<float2*>(dyn_smem);
-  const int x0 = blockIdx.x * LC, fixed = blockIdx.y, l = blockIdx.z;
+  const int x0 = blockIdx.x * LCV, fixed = blockIdx.y, l = blockIdx.z;
   const long long base = (long long)l * a.n + (long long)fixed * a.slab + x0;
-  constexpr int CNT = LC * N, PER = (CNT + NT - 1) / NT;
+  constexpr int CNT = LCV * N, PER = (CNT + NT - 1) / NT;
   float2 iv[PER];
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
-    if (CNT % NT == 0 || e < CNT) iv[p] = a.in[base + (e / LC) * a.stride + e % LC];
+    if (CNT % NT == 0 || e < CNT) iv[p] = a.in[base + (e / LCV) * a.stride + e % LCV];
   }
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
-      const int line = e % LC, i = e / LC;
+      const int line = e % LCV, i = e / LCV;
       float2 v = iv[p];
       if constexpr (MODE == COL_ADJ) {  // z axis, fixed = ky
         v = cscale(v, __ldg(&a.pupil[fixed * a.nx + x0 + line]) * __ldg(&a.window[i]));
@@ -337,12 +342,12 @@ __global__ void __launch_bounds__(NT) k_col(ColArgs a, const float2* __restrict_
     }
   }
   __syncthreads();
-  fft_tile<N, LC, NT, INV>(sm, tw);
+  fft_tile<N, LCV, NT, INV, PL>(sm, tw);
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (!(CNT % NT == 0 || e < CNT)) continue;
-    const int line = e % LC, i = e / LC;
+    const int line = e % LCV, i = e / LCV;
     float2 v = cscale(sm[line * LD + i], a.scale);
     const long long gi = base + i * a.stride + line;
     if constexpr (MODE == COL_SIM) {  // z axis, fixed = ky: y = a v + sigma_w eta
@@ -371,11 +376,11 @@ static cudaError_t dispatch_len(int N, F&& f) {
   }
 }
 
-template <int N, bool INV, int MODE>
+template <int N, bool INV, int MODE, int V = 0>
 static cudaError_t run_row(const Geom& g, const RowArgs& a, cudaStream_t st) {
-  constexpr int LX = rows_per_cta(N);
+  constexpr int LX = variant_rows(N, V);
   const size_t smem = (size_t)LX * (N + 1) * sizeof(float2);
-  auto kern = k_row<N, INV, MODE>;
+  auto kern = k_row<N, INV, MODE, V>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long rows = (long long)g.L * g.nz * g.ny;
@@ -383,13 +388,14 @@ static cudaError_t run_row(const Geom& g, const RowArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <int N, bool INV, int MODE>
+template <int N, bool INV, int MODE, int V = 0>
 static cudaError_t run_col(const Geom& g, const ColArgs& a, int fixed_count, cudaStream_t st) {
-  const size_t smem = (size_t)LC * (N + 1) * sizeof(float2);
-  auto kern = k_col<N, INV, MODE>;
+  constexpr int LCV = variant_cols(V);
+  const size_t smem = (size_t)LCV * (N + 1) * sizeof(float2);
+  auto kern = k_col<N, INV, MODE, V>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(g.nx / LC, fixed_count, g.L);
+  dim3 grid(g.nx / LCV, fixed_count, g.L);
   kern<<<grid, NT, smem, st>>>(a, tw_ptr(N));
   return cudaGetLastError();
 }
@@ -417,53 +423,117 @@ static ColArgs col_args(const Geom& g, bool zaxis) {
 
 // ---------------------------------------------------------------- forward agent FFT passes
 
+template <class F>
+static cudaError_t dispatch_var(int V, F&& f) {
+  switch (V) {
+    case 0: return f(std::integral_constant<int, 0>{});
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+bool variant_valid(int pass, int V, int nx, int ny, int nz) {
+  if (V < 0 || V >= kVariants) return false;
+  if (V != 2) return true;
+  if (pass == 0 || pass == 4) return true;   // x passes: half the rows per CTA always divides nz * ny
+  return nx % 32 == 0;                        // y / z passes: 32 adjacent columns
+}
+
+int max_pz(int nx, int ny) { return (nx / LC) * ny; }
+int max_px(int nx, int ny, int nz) {
+  int m = 0;
+  for (int V = 0; V < kVariants; ++V) {
+    const int lx = variant_rows(nx, V);
+    const int px = (int)((long long)nz * ny / lx);
+    if (px > m) m = px;
+  }
+  return m;
+}
+
+cudaError_t launch_agent_pass(int pass, int V, const Geom& g, const AgentScalars& s, const float2* mu,
+                              const float* rprev, const float2* y, const float* pupil, const float* window, float4* T,
+                              float2* U, Partials& p, cudaStream_t st) {
+  if (!variant_valid(pass, V, g.nx, g.ny, g.nz)) return cudaErrorInvalidValue;
+  switch (pass) {
+    case 0:  // A_x
+      return dispatch_var(V, [&](auto VC) -> cudaError_t {
+        constexpr int VV = decltype(VC)::value;
+        return dispatch_len(g.nx, [&](auto NC) -> cudaError_t {
+          constexpr int N = decltype(NC)::value;
+          constexpr int LX = variant_rows(N, VV);
+          const size_t smem = (size_t)2 * LX * (N + 1) * sizeof(float2);
+          CLAMP_TRY(cudaFuncSetAttribute(k_a_x<N, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          const long long rows = (long long)g.L * g.nz * g.ny;
+          k_a_x<N, VV><<<(unsigned)(rows / LX), NT, smem, st>>>(g, s, mu, rprev, T, tw_ptr(N));
+          return cudaGetLastError();
+        });
+      });
+    case 1:  // A_y
+      return dispatch_var(V, [&](auto VC) -> cudaError_t {
+        constexpr int VV = decltype(VC)::value;
+        return dispatch_len(g.ny, [&](auto NC) -> cudaError_t {
+          constexpr int N = decltype(NC)::value;
+          constexpr int LCV = variant_cols(VV);
+          const size_t smem = (size_t)2 * LCV * (N + 1) * sizeof(float2);
+          CLAMP_TRY(cudaFuncSetAttribute(k_a_y<N, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          k_a_y<N, VV><<<dim3(g.nx / LCV, g.nz, g.L), NT, smem, st>>>(g, s, T, tw_ptr(N));
+          return cudaGetLastError();
+        });
+      });
+    case 2:  // fused z pass
+      return dispatch_var(V, [&](auto VC) -> cudaError_t {
+        constexpr int VV = decltype(VC)::value;
+        return dispatch_len(g.nz, [&](auto NC) -> cudaError_t {
+          constexpr int N = decltype(NC)::value;
+          constexpr int LCV = variant_cols(VV);
+          const size_t smem = (size_t)2 * LCV * (N + 1) * sizeof(float2);
+          CLAMP_TRY(cudaFuncSetAttribute(k_ab_z<N, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+          p.pz = (g.nx / LCV) * g.ny;
+          k_ab_z<N, VV><<<dim3(g.nx / LCV, g.ny, g.L), NT, smem, st>>>(g, s, T, y, pupil, window, U, p, tw_ptr(N));
+          return cudaGetLastError();
+        });
+      });
+    case 3: {  // B_y (in place on U)
+      ColArgs cy = col_args(g, false);
+      cy.in = U;
+      cy.out = U;
+      cy.scale = s.sc_y;
+      return dispatch_var(V, [&](auto VC) -> cudaError_t {
+        constexpr int VV = decltype(VC)::value;
+        return dispatch_len(g.ny, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_PLAIN, VV>(g, cy, g.nz, st); });
+      });
+    }
+    case 4: {  // B_x (in place on U, d out, S3 partials)
+      RowArgs rx{};
+      rx.in = U;
+      rx.out = U;
+      rx.rprev = rprev;
+      rx.scale = s.sc_x;
+      rx.floor = s.floor;
+      rx.s3 = p.s3;
+      rx.n = g.n;
+      rx.nx = g.nx;
+      return dispatch_var(V, [&](auto VC) -> cudaError_t {
+        constexpr int VV = decltype(VC)::value;
+        return dispatch_len(g.nx, [&](auto NC) -> cudaError_t {
+          constexpr int N = decltype(NC)::value;
+          p.px = (int)((long long)g.nz * g.ny / variant_rows(N, VV));
+          rx.px = p.px;
+          return run_row<N, true, ROW_BX, VV>(g, rx, st);
+        });
+      });
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_agent_fft(const Geom& g, const AgentScalars& s, const float2* mu, const float* rprev,
                              const float2* y, const float* pupil, const float* window, float4* T, float2* U,
-                             const Partials& p, cudaStream_t st) {
-  // A_x
-  CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) -> cudaError_t {
-    constexpr int N = decltype(NC)::value;
-    constexpr int LX = rows_per_cta(N);
-    const size_t smem = (size_t)2 * LX * (N + 1) * sizeof(float2);
-    CLAMP_TRY(cudaFuncSetAttribute(k_a_x<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const long long rows = (long long)g.L * g.nz * g.ny;
-    k_a_x<N><<<(unsigned)(rows / LX), NT, smem, st>>>(g, s, mu, rprev, T, tw_ptr(N));
-    return cudaGetLastError();
-  }));
-  // A_y
-  CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) -> cudaError_t {
-    constexpr int N = decltype(NC)::value;
-    const size_t smem = (size_t)2 * LC * (N + 1) * sizeof(float2);
-    CLAMP_TRY(cudaFuncSetAttribute(k_a_y<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_a_y<N><<<dim3(g.nx / LC, g.nz, g.L), NT, smem, st>>>(g, s, T, tw_ptr(N));
-    return cudaGetLastError();
-  }));
-  // fused z pass
-  CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) -> cudaError_t {
-    constexpr int N = decltype(NC)::value;
-    const size_t smem = (size_t)2 * LC * (N + 1) * sizeof(float2);
-    CLAMP_TRY(cudaFuncSetAttribute(k_ab_z<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_ab_z<N><<<dim3(g.nx / LC, g.ny, g.L), NT, smem, st>>>(g, s, T, y, pupil, window, U, p, tw_ptr(N));
-    return cudaGetLastError();
-  }));
-  // B_y (in place on U)
-  ColArgs cy = col_args(g, false);
-  cy.in = U;
-  cy.out = U;
-  cy.scale = s.sc_y;
-  CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_PLAIN>(g, cy, g.nz, st); }));
-  // B_x (in place on U, d out, S3 partials)
-  RowArgs rx{};
-  rx.in = U;
-  rx.out = U;
-  rx.rprev = rprev;
-  rx.scale = s.sc_x;
-  rx.floor = s.floor;
-  rx.s3 = p.s3;
-  rx.px = p.px;
-  rx.n = g.n;
-  rx.nx = g.nx;
-  CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) { return run_row<decltype(NC)::value, true, ROW_BX>(g, rx, st); }));
+                             Partials& p, const AgentVariants& var, cudaStream_t st) {
+  for (int pass = 0; pass < 5; ++pass)
+    CLAMP_TRY(launch_agent_pass(pass, var.v[pass], g, s, mu, rprev, y, pupil, window, T, U, p, st));
   return cudaSuccess;
 }
 

@@ -11,6 +11,21 @@ constexpr int LC = 16;    // adjacent x-columns per CTA in the y / z passes
 // Rows (x-lines) per CTA in the x passes.
 __host__ __device__ constexpr int rows_per_cta(int N) { return N <= 32 ? 64 : (N <= 128 ? 32 : 16); }  // 96 -> 32, 192 -> 16
 
+// Launch variants of the forward-agent FFT passes, chosen per pass by the autotuner:
+// 0 = default radix plan and tile, 1 = alternative radix plan (PlanB), 2 = other tile
+// schedule (half the rows per CTA in x passes, 32 columns per CTA in y / z passes).
+constexpr int kVariants = 3;
+__host__ __device__ constexpr int variant_rows(int N, int V) {
+  return V == 2 ? (rows_per_cta(N) / 2 < 8 ? 8 : rows_per_cta(N) / 2) : rows_per_cta(N);
+}
+__host__ __device__ constexpr int variant_cols(int V) { return V == 2 ? 32 : LC; }
+// Passes of the forward agent: A_x, A_y, fused z, B_y, B_x.
+struct AgentVariants {
+  int v[5] = {0, 0, 0, 0, 0};
+};
+// True if variant V of pass `pass` can run on the geometry.
+bool variant_valid(int pass, int V, int nx, int ny, int nz);
+
 struct Geom {
   int nx, ny, nz, L;
   long long n;  // nx * ny * nz
@@ -37,9 +52,17 @@ struct Partials {
 cudaError_t upload_twiddles();
 
 // ---- forward agent (Alg. 2 steps 6-8): pass A (x, y), fused z pass, pass B (y, x)
+// p.pz / p.px receive the partial counts per look the chosen variants produce.
 cudaError_t launch_agent_fft(const Geom& g, const AgentScalars& s, const float2* mu, const float* rprev,
                              const float2* y, const float* pupil, const float* window, float4* T,
-                             float2* U, const Partials& p, cudaStream_t st);
+                             float2* U, Partials& p, const AgentVariants& var, cudaStream_t st);
+// One forward-agent pass alone (for timing variants): pass in 0..4.
+cudaError_t launch_agent_pass(int pass, int V, const Geom& g, const AgentScalars& s, const float2* mu,
+                              const float* rprev, const float2* y, const float* pupil, const float* window,
+                              float4* T, float2* U, Partials& p, cudaStream_t st);
+// Largest partial counts per look over all variants (workspace sizing).
+int max_pz(int nx, int ny);
+int max_px(int nx, int ny, int nz);
 // gamma_l = S1 / (S2 / sigma_w^2 + S3) and the floored mu-residual per look.
 cudaError_t launch_gamma(const Geom& g, float nv, const Partials& p, float* gamma, double* mures,
                          cudaStream_t st);

@@ -113,6 +113,17 @@ template <> struct Plan<256> { static constexpr int R1 = 16, R2 = 16, R3 = 1; };
 template <> struct Plan<96>  { static constexpr int R1 = 8,  R2 = 4,  R3 = 3; };
 template <> struct Plan<192> { static constexpr int R1 = 16, R2 = 4,  R3 = 3; };
 
+// Alternative radix plans (the autotuner's variant 1).
+template <int N> struct PlanB;
+template <> struct PlanB<8>   { static constexpr int R1 = 2,  R2 = 4,  R3 = 1; };
+template <> struct PlanB<16>  { static constexpr int R1 = 16, R2 = 1,  R3 = 1; };
+template <> struct PlanB<32>  { static constexpr int R1 = 4,  R2 = 8,  R3 = 1; };
+template <> struct PlanB<64>  { static constexpr int R1 = 16, R2 = 4,  R3 = 1; };
+template <> struct PlanB<96>  { static constexpr int R1 = 4,  R2 = 8,  R3 = 3; };
+template <> struct PlanB<128> { static constexpr int R1 = 8,  R2 = 16, R3 = 1; };
+template <> struct PlanB<192> { static constexpr int R1 = 8,  R2 = 8,  R3 = 3; };
+template <> struct PlanB<256> { static constexpr int R1 = 8,  R2 = 8,  R3 = 4; };
+
 // Offset of the length-N twiddle table inside the packed table (N = 8..256 powers of two, 96, 192).
 __host__ __device__ constexpr int tw_offset(int N) {
   return N == 8 ? 0 : N == 16 ? 8 : N == 32 ? 24 : N == 64 ? 56 : N == 128 ? 120 : N == 256 ? 248 : N == 96 ? 504 : 600;
@@ -163,13 +174,12 @@ __device__ __forceinline__ void stockham_stage(float2* __restrict__ s, const flo
   __syncthreads();
 }
 
-// Full N-point FFT (unnormalised) of every line of the tile; tw points at the
-// length-N table.  Must be called by all NT threads; ends with a barrier.
-template <int N, int LT, int NT, bool INV>
+// Full N-point FFT (unnormalised) of every line of the tile with radix plan P; tw points
+// at the length-N table.  Must be called by all NT threads; ends with a barrier.
+template <int N, int LT, int NT, bool INV, class P = Plan<N>>
 __device__ __forceinline__ void fft_tile(float2* __restrict__ s, const float2* __restrict__ tw) {
-  using P = Plan<N>;
   stockham_stage<N, P::R1, 1, LT, NT, INV>(s, tw);
-  stockham_stage<N, P::R2, P::R1, LT, NT, INV>(s, tw);
+  if constexpr (P::R2 > 1) stockham_stage<N, P::R2, P::R1, LT, NT, INV>(s, tw);
   if constexpr (P::R3 > 1) stockham_stage<N, P::R3, P::R1 * P::R2, LT, NT, INV>(s, tw);
 }
 
