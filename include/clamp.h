@@ -47,6 +47,14 @@ typedef enum clamp_status {
 
 /* Flags for clamp_params.flags. */
 #define CLAMP_FLAG_MU_INIT_NO_ALPHA 0x1 /* mu_l = A^H y_l (Alg. 2) instead of A^H y_l / alpha (Sec. IV-A) */
+/* Reflectance update by the exact prox of the EM surrogate: per voxel the positive root of
+ * r^3 - v r^2 + sigma^2 r - sigma^2 K = 0 with the smallest objective (Sec. III-B, the
+ * "closed form by solving for a root of a cubic"), instead of App. A's quadratic step. */
+#define CLAMP_FLAG_EXACT_PROX 0x2
+/* No-aperture ablation (Sec. IV-A): a = 1 everywhere (pupil and window are ignored,
+ * alpha = 1) and the mu update is the closed-form minimiser of h,
+ * mu = F^H y / (1 + sigma_w^2 / (r' + sigma_w^2)); no FFT runs per iteration. */
+#define CLAMP_FLAG_NO_APERTURE 0x4
 
 /* Problem and iteration parameters (Sec. II-B, Sec. III, Sec. IV-A). */
 typedef struct clamp_params {

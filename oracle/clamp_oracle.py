@@ -52,7 +52,7 @@ __all__ = [
     "line_search_gamma", "beta_k", "prox_quadratic", "forward_agent", "gauss_kernel1d",
     "denoise_gauss", "conv3d", "denoise_cnn", "mace_update", "convergence_error",
     "mu_residual", "reconstruct", "OracleState", "em_surrogate", "exact_nll",
-    "exact_posterior", "cubic_prox", "psnr",
+    "exact_posterior", "cubic_prox", "psnr", "cubic_prox_field", "no_aperture_mu",
 ]
 
 
@@ -321,8 +321,25 @@ def mu_residual(mu, y, r_prev, a, noise_var, alpha, floored: bool = False) -> fl
     return float(np.mean(vals))
 
 
+def cubic_prox_field(v, K, prox_var) -> np.ndarray:
+    """Exact prox of the EM surrogate for every voxel (cubic_prox elementwise)."""
+    v = np.asarray(v, dtype=np.float64)
+    K = np.broadcast_to(np.asarray(K, dtype=np.float64), v.shape)
+    out = np.empty_like(v)
+    for idx in np.ndindex(v.shape):
+        out[idx] = cubic_prox(float(v[idx]), float(K[idx]), prox_var)
+    return out
+
+
+def no_aperture_mu(y_l, r_prev, noise_var) -> np.ndarray:
+    """Closed-form mu step of the no-aperture ablation (Sec. IV-A, a = 1): the minimiser of
+    h with A = F, mu = F^H y / (1 + sigma_w^2 D), D = 1/(r' + sigma_w^2) (alpha = 1)."""
+    return ifft3(y_l) / (1.0 + noise_var / (r_prev + noise_var))
+
+
 def clamp_iteration(state: OracleState, y, a, den: dict, noise_var, prox_var,
-                    rho=0.5, prior_weight=0.5) -> OracleState:
+                    rho=0.5, prior_weight=0.5, exact_prox: bool = False,
+                    no_aperture: bool = False) -> OracleState:
     """One iteration of Alg. 2: every forward agent (C, mu, r updates), the prior agent
     on w_{L+1}, then the MACE step.  Records the convergence error (Eq.
     mace-convergence-error) and the mu-residual (Eq. residual, floored form) of the
@@ -333,10 +350,26 @@ def clamp_iteration(state: OracleState, y, a, den: dict, noise_var, prox_var,
     beta = beta_k(k)
     r_new = np.empty_like(state.r)
     mu_new = np.empty_like(state.mu)
-    state.mu_res_hist.append(mu_residual(state.mu, y, state.r[:L], a, noise_var, alpha, floored=True))
-    for l in range(L):
-        mu_new[l], r_new[l], _, _ = forward_agent(state.mu[l], state.r[l], state.w[l], y[l], a,
-                                                   noise_var, prox_var, alpha, beta)
+    if no_aperture:
+        # Sec. IV-A ablation: a = 1 and the mu update in closed form; the prox as in Alg. 2
+        state.mu_res_hist.append(0.0)
+        for l in range(L):
+            mu_new[l] = no_aperture_mu(y[l], state.r[l], noise_var)
+            K = c_update(state.r[l], noise_var, 1.0) + np.abs(mu_new[l]) ** 2
+            r_new[l] = (cubic_prox_field(state.w[l], K, prox_var) if exact_prox
+                        else prox_quadratic(state.w[l], state.r[l], K, prox_var, beta))
+    else:
+        state.mu_res_hist.append(mu_residual(state.mu, y, state.r[:L], a, noise_var, alpha, floored=True))
+        for l in range(L):
+            if exact_prox:
+                c = c_update(state.r[l], noise_var, alpha)
+                d = grad_direction(state.mu[l], y[l], state.r[l], a, noise_var, alpha)
+                mu_new[l] = state.mu[l] + line_search_gamma(state.mu[l], d, y[l], state.r[l], a, noise_var,
+                                                            alpha) * d
+                r_new[l] = cubic_prox_field(state.w[l], c + np.abs(mu_new[l]) ** 2, prox_var)
+            else:
+                mu_new[l], r_new[l], _, _ = forward_agent(state.mu[l], state.r[l], state.w[l], y[l], a,
+                                                           noise_var, prox_var, alpha, beta)
     r_new[L] = apply_prior(state.w[L], den)
     ups = consensus_weights(L, prior_weight)
     state.ce_hist.append(convergence_error(r_new, state.w, ups))
@@ -346,13 +379,16 @@ def clamp_iteration(state: OracleState, y, a, den: dict, noise_var, prox_var,
 
 
 def reconstruct(y, pupil, window, den: dict, noise_var, prox_var, iters, rho=0.5,
-                prior_weight=0.5, r_init=None, tol: float = 0.0):
+                prior_weight=0.5, r_init=None, tol: float = 0.0, exact_prox: bool = False,
+                no_aperture: bool = False):
     """CLAMP (Alg. 2): initialise (Sec. IV-A), iterate, output r* = wbar.
-    Stops early once the convergence error falls to ``tol`` (when tol > 0)."""
-    a = aperture(pupil, window)
+    Stops early once the convergence error falls to ``tol`` (when tol > 0).
+    ``exact_prox``: the cubic-root prox of the EM surrogate instead of App. A's quadratic step.
+    ``no_aperture``: the Sec. IV-A ablation (a = 1, closed-form mu update)."""
+    a = np.ones((len(window), pupil.shape[0], pupil.shape[1])) if no_aperture else aperture(pupil, window)
     st = init_state(y, a, r_init)
     for _ in range(iters):
-        st = clamp_iteration(st, y, a, den, noise_var, prox_var, rho, prior_weight)
+        st = clamp_iteration(st, y, a, den, noise_var, prox_var, rho, prior_weight, exact_prox, no_aperture)
         if tol > 0 and st.ce_hist[-1] <= tol:
             break
     ups = consensus_weights(y.shape[0], prior_weight)

@@ -22,6 +22,8 @@ CLAMP_OK = 0
 STATUS = {0: "CLAMP_OK", 1: "CLAMP_EINVAL", 2: "CLAMP_ENOMEM", 3: "CLAMP_ECUDA", 4: "CLAMP_ENOTCONV",
           5: "CLAMP_ETIMEOUT", 6: "CLAMP_ENONFINITE", 7: "CLAMP_EUNSUPPORTED"}
 FLAG_MU_INIT_NO_ALPHA = 0x1
+FLAG_EXACT_PROX = 0x2
+FLAG_NO_APERTURE = 0x4
 DENOISER_FP32 = 0
 DENOISER_BF16 = 1
 

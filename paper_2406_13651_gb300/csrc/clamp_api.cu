@@ -173,6 +173,16 @@ clamp_status recon_prepare(const clamp_params* p, const float* pupil, const floa
   d->g.nz = p->nz;
   d->g.L = p->looks;
   d->g.n = (long long)p->nx * p->ny * p->nz;
+  if (p->flags & CLAMP_FLAG_NO_APERTURE) {  // a = 1: alpha = 1, nothing to read back
+    d->alpha = 1.0;
+    d->s.nv = p->noise_var;
+    d->s.alpha = 1.0f;
+    d->s.floor = p->noise_var;
+    d->s.sc_x = (float)(1.0 / sqrt((double)p->nx));
+    d->s.sc_y = (float)(1.0 / sqrt((double)p->ny));
+    d->s.sc_z = (float)(1.0 / sqrt((double)p->nz));
+    return CLAMP_OK;
+  }
   std::vector<float> hp((size_t)p->nx * p->ny), hw(p->nz);
   API_CUDA(cudaMemcpyAsync(hp.data(), pupil, hp.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "pupil read");
   API_CUDA(cudaMemcpyAsync(hw.data(), window, hw.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "window read");
@@ -274,8 +284,9 @@ static clamp_status do_init(const clamp_params* p, const Derived& d, const float
                             const float* window, const float* r_init, float2* mu, float* r, float* w,
                             const AgentLayout& al, void* ws, cudaStream_t st) {
   const double mu_scale = (p->flags & CLAMP_FLAG_MU_INIT_NO_ALPHA) ? 1.0 : 1.0 / d.alpha;
-  API_CUDA(launch_adjoint(d.g, reinterpret_cast<const float2*>(y), pupil, window, (float)mu_scale, mu, d.s.sc_x,
-                          d.s.sc_y, d.s.sc_z, st),
+  const bool noap = (p->flags & CLAMP_FLAG_NO_APERTURE) != 0;
+  API_CUDA(launch_adjoint(d.g, reinterpret_cast<const float2*>(y), noap ? nullptr : pupil, window, (float)mu_scale,
+                          mu, d.s.sc_x, d.s.sc_y, d.s.sc_z, st),
            "adjoint launch");
   API_CUDA(launch_init_state(d.g, mu, (float)mu_scale, r_init, r, w, at<float>(ws, al.maxp), nullptr, st),
            "init launch");
@@ -433,7 +444,18 @@ static PassC passc_args(const clamp_params* p, const Derived& d, const AgentLayo
   c.part_num = at<double>(ws, al.num);
   c.part_den = at<double>(ws, al.den);
   c.err = at<int>(ws, al.err);
+  c.exact_prox = (p->flags & CLAMP_FLAG_EXACT_PROX) ? 1 : 0;
+  c.closed_mu = (p->flags & CLAMP_FLAG_NO_APERTURE) ? 1 : 0;
   return c;
+}
+
+// No-aperture ablation: U <- F^H y for all looks (the closed-form mu update reads it).
+static clamp_status ablation_prepare(const Derived& d, const float* y, const AgentLayout& al, void* ws,
+                                     cudaStream_t st) {
+  API_CUDA(launch_adjoint(d.g, reinterpret_cast<const float2*>(y), nullptr, nullptr, 1.0f, at<float2>(ws, al.U),
+                          d.s.sc_x, d.s.sc_y, d.s.sc_z, st),
+           "F^H y");
+  return CLAMP_OK;
 }
 
 extern "C" clamp_status clamp_forward_prox(const clamp_params* p, int32_t k, const float* y, const float* pupil,
@@ -448,8 +470,13 @@ extern "C" clamp_status clamp_forward_prox(const clamp_params* p, int32_t k, con
   cudaStream_t st = (cudaStream_t)stream;
   Derived d;
   API_TRY(recon_prepare(p, pupil, window, st, &d));
-  API_TRY(agent_ffts(d, y, pupil, window, reinterpret_cast<float2*>(mu), r, al, ws, st));
-  if (mu_residual) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_residual, st), "mu residual");
+  if (p->flags & CLAMP_FLAG_NO_APERTURE) {
+    API_TRY(ablation_prepare(d, y, al, ws, st));
+    if (mu_residual) API_CUDA(cudaMemsetAsync(mu_residual, 0, sizeof(double), st), "mu residual");
+  } else {
+    API_TRY(agent_ffts(d, y, pupil, window, reinterpret_cast<float2*>(mu), r, al, ws, st));
+    if (mu_residual) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_residual, st), "mu residual");
+  }
   PassC c = passc_args(p, d, al, ws, reinterpret_cast<float2*>(mu), r, const_cast<float*>(w), nullptr, k);
   c.err = nullptr;
   API_CUDA(launch_prox_only(d.g, c, st), "prox pass");
@@ -512,11 +539,17 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
   const AgentLayout al = agent_layout(p);
   void* dws = static_cast<char*>(ws) + al.bytes;
   const long long n = d.g.n;
+  const bool noap = (p->flags & CLAMP_FLAG_NO_APERTURE) != 0;
+  if (noap && iters > 0) API_TRY(ablation_prepare(d, y, al, ws, st));
   for (int it = 0; it < iters; ++it) {
     const int k = k_first + it;
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 0], st), "event");
-    API_TRY(agent_ffts(d, y, pupil, window, mu, r, al, ws, st));
-    if (mu_out) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_out + it, st), "mu residual");
+    if (noap) {
+      if (mu_out) API_CUDA(cudaMemsetAsync(mu_out + it, 0, sizeof(double), st), "mu residual");
+    } else {
+      API_TRY(agent_ffts(d, y, pupil, window, mu, r, al, ws, st));
+      if (mu_out) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_out + it, st), "mu residual");
+    }
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 1], st), "event");
     API_CUDA(denoise_apply(den, w + (long long)p->looks * n, r + (long long)p->looks * n, p->nx, p->ny, p->nz, dws,
                            at<int>(ws, al.err), st),

@@ -603,6 +603,45 @@ __device__ __forceinline__ float prox_quad(float v, float rp, float K, float s2,
   return fminf(fmaxf(rn, lo), hi);
 }
 
+// Exact prox of one voxel's EM surrogate (Sec. III-B): the positive real root of
+// r^3 - v r^2 + s2 r - s2 K = 0 minimising log r + K/r + (r - v)^2 / (2 s2), in FP64
+// (trigonometric form for three real roots, Cardano otherwise, one Newton polish each).
+__device__ double prox_exact(double v, double K, double s2) {
+  const double a2 = -v, a1 = s2, a0 = -s2 * K;
+  const double q = (3.0 * a1 - a2 * a2) / 9.0;
+  const double rr = (9.0 * a2 * a1 - 27.0 * a0 - 2.0 * a2 * a2 * a2) / 54.0;
+  const double disc = q * q * q + rr * rr;
+  double roots[3];
+  int nr;
+  if (disc > 0.0) {
+    const double sd = sqrt(disc);
+    roots[0] = cbrt(rr + sd) + cbrt(rr - sd) - a2 / 3.0;
+    nr = 1;
+  } else {
+    const double m = 2.0 * sqrt(-q);
+    const double c = fmin(fmax(rr / sqrt(-q * q * q), -1.0), 1.0);
+    const double th = acos(c);
+    const double twopi3 = 2.0943951023931954923;  // 2 pi / 3
+    roots[0] = m * cos(th / 3.0) - a2 / 3.0;
+    roots[1] = m * cos(th / 3.0 + twopi3) - a2 / 3.0;
+    roots[2] = m * cos(th / 3.0 + 2.0 * twopi3) - a2 / 3.0;
+    nr = 3;
+  }
+  double best = -1.0, best_f = 0.0;
+  for (int i = 0; i < nr; ++i) {
+    double r = roots[i];
+    const double f = ((r + a2) * r + a1) * r + a0, df = (3.0 * r + 2.0 * a2) * r + a1;
+    if (df != 0.0) r -= f / df;  // Newton polish
+    if (!(r > 0.0)) continue;
+    const double obj = log(r) + K / r + (r - v) * (r - v) / (2.0 * s2);
+    if (best < 0.0 || obj < best_f) {
+      best = r;
+      best_f = obj;
+    }
+  }
+  return best > 0.0 ? best : 1e-30;
+}
+
 // Error-free sum accumulation (Knuth two-sum) for the per-voxel look averages.
 struct CSum {
   float s = 0.f, c = 0.f;
@@ -636,13 +675,19 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
         const float rp = c.r[i];
         float2 m = c.mu[i];
         const float2 dd = c.d[i];
-        const float gm = __ldg(&c.gamma[l]);
-        m.x = fmaf(gm, dd.x, m.x);
-        m.y = fmaf(gm, dd.y, m.y);
+        if (c.closed_mu) {  // no-aperture ablation: d holds F^H y
+          const float f = 1.0f / (1.0f + c.nv / (rp + c.nv));
+          m = make_float2(dd.x * f, dd.y * f);
+        } else {
+          const float gm = __ldg(&c.gamma[l]);
+          m.x = fmaf(gm, dd.x, m.x);
+          m.y = fmaf(gm, dd.y, m.y);
+        }
         c.mu[i] = m;
         const float cc = c.nv * rp / fmaf(c.alpha, rp, c.nv);
         const float K = cc + cabs2(m);
-        rn = prox_quad(wl, rp, K, c.prox_var, c.beta);
+        rn = c.exact_prox ? (float)prox_exact((double)wl, (double)K, (double)c.prox_var)
+                          : prox_quad(wl, rp, K, c.prox_var, c.beta);
         c.r[i] = rn;
         bad |= !isfinite(rn);
       } else {
@@ -791,7 +836,10 @@ cudaError_t launch_adjoint(const Geom& g, const float2* y, const float* pupil, c
   rx.scale = sc_x * mu_scale;
   rx.n = g.n;
   rx.nx = g.nx;
-  CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_ADJ>(g, cz, g.ny, st); }));
+  if (pupil)
+    CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_ADJ>(g, cz, g.ny, st); }));
+  else
+    CLAMP_TRY(dispatch_len(g.nz, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_PLAIN>(g, cz, g.ny, st); }));
   CLAMP_TRY(dispatch_len(g.ny, [&](auto NC) { return run_col<decltype(NC)::value, true, COL_PLAIN>(g, cy, g.nz, st); }));
   CLAMP_TRY(dispatch_len(g.nx, [&](auto NC) { return run_row<decltype(NC)::value, true, ROW_PLAIN>(g, rx, st); }));
   return cudaSuccess;

@@ -82,6 +82,8 @@ struct PassC {
   double* part_num;  // CE partials (MACE variants)
   double* part_den;
   int* err;          // device error word (non-finite)
+  int exact_prox;    // 1: exact cubic-root prox instead of the quadratic-surrogate step
+  int closed_mu;     // 1: mu = d / (1 + sigma_w^2 / (r' + sigma_w^2)) with d holding F^H y (no aperture)
 };
 int passc_blocks(long long n);
 cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st);
@@ -96,7 +98,7 @@ cudaError_t launch_fft3(const Geom& g, const float2* in, float2* out, bool inver
 cudaError_t launch_simulate(const Geom& g, const float* r, const float2* z, const float2* eta,
                             const float* pupil, const float* window, float sig_w, float2* y, float sc_x,
                             float sc_y, float sc_z, cudaStream_t st);
-// mu = A^H y * mu_scale (inverse transform of a .* y)
+// mu = A^H y * mu_scale (inverse transform of a .* y); with pupil == nullptr, a = 1 (F^H y).
 cudaError_t launch_adjoint(const Geom& g, const float2* y, const float* pupil, const float* window,
                            float mu_scale, float2* mu, float sc_x, float sc_y, float sc_z, cudaStream_t st);
 // r0 = (1/L) sum |mu|^2 / mu_scale^2 (or r_init), floored at 1e-12 max, broadcast to r, w rows 0..L

@@ -244,6 +244,20 @@ def test_reconstruct_matches_oracle(C, name, iters):
     np.testing.assert_allclose(res.mu_hist, st.mu_res_hist, rtol=1e-3)
 
 
+@pytest.mark.parametrize("mode", ["exact_prox", "no_aperture", "both"])
+def test_reconstruct_paper_variants_match_oracle(C, mode):
+    """Exact cubic-root prox (Sec. III-B) and the no-aperture ablation (Sec. IV-A)."""
+    exact, noap = mode in ("exact_prox", "both"), mode in ("no_aperture", "both")
+    wl, a, y32, y64 = problem("tiny", seed=7, iters=8)
+    ref, st = O.reconstruct(y64, wl.pupil, wl.window, wl.denoiser, wl.noise_var, wl.prox_var, 8,
+                            exact_prox=exact, no_aperture=noap)
+    flags = (C.FLAG_EXACT_PROX if exact else 0) | (C.FLAG_NO_APERTURE if noap else 0)
+    p = params(C, wl, max_iters=8, flags=flags)
+    res = C.reconstruct(p, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), C.Denoiser.gauss(0.8))
+    assert rel(res.r.cpu().numpy(), ref) < TOL_RECON
+    np.testing.assert_allclose(res.ce_hist, st.ce_hist, rtol=1e-3)
+
+
 def test_reconstruct_warm_start_and_tolerance(C):
     wl, a, y32, y64 = problem("cfg1", seed=2, iters=30)
     r_init = (wl.r_true + 0.01).astype(np.float32)

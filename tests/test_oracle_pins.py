@@ -390,3 +390,28 @@ def test_paper_constants_fixture():
     # along the kx axis the disk spans 50 % of the grid
     assert pupil[0].sum() == pytest.approx(g["aperture_diameter_fraction"]["value"] * nx, abs=1)
     assert g["rho"]["value"] == 0.5
+
+
+def test_no_aperture_mu_is_the_limit_of_gradient_steps():
+    """The ablation's closed-form mu equals many exact-line-search steps of h with a = 1."""
+    rng = _rng(21)
+    shape = (2, 4, 4)
+    y = O.fft3(_crand(rng, shape))
+    r_prev = rng.uniform(0.1, 1.0, shape)
+    nv = 0.05
+    a = np.ones(shape)
+    mu = np.zeros(shape, dtype=complex)
+    for _ in range(400):
+        d = O.grad_direction(mu, y, r_prev, a, nv, 1.0)
+        mu = mu + O.line_search_gamma(mu, d, y, r_prev, a, nv, 1.0) * d
+    np.testing.assert_allclose(O.no_aperture_mu(y, r_prev, nv), mu, rtol=1e-9, atol=1e-11)
+
+
+def test_exact_prox_reconstruction_runs_and_converges():
+    wl = I.make_workload("tiny", seed=4)
+    a = O.aperture(wl.pupil, wl.window)
+    y = O.simulate_data(wl.r_true, wl.speckle, wl.noise, a, wl.noise_var)
+    r1, st1 = O.reconstruct(y, wl.pupil, wl.window, wl.denoiser, wl.noise_var, wl.prox_var, 25, exact_prox=True)
+    r2, st2 = O.reconstruct(y, wl.pupil, wl.window, wl.denoiser, wl.noise_var, wl.prox_var, 25, no_aperture=True)
+    assert np.all(np.isfinite(r1)) and np.all(np.isfinite(r2))
+    assert st1.ce_hist[-1] < st1.ce_hist[0] and st2.ce_hist[-1] < st2.ce_hist[0]
