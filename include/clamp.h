@@ -278,6 +278,76 @@ clamp_status clamp_batch_latencies(clamp_batch* b, void* stream, float* latency_
 clamp_status clamp_batch_residuals(clamp_batch* b, void* stream, double* ce);
 void clamp_batch_destroy(clamp_batch* b);
 
+
+/* The initial image of Alg. 2 alone: r0 = (1/L) sum_l |A^H y_l / alpha|^2 (the speckle
+ * average; Sec. IV-A), floored at 1e-12 of its maximum as the initialisation floors it.
+ * r0: device float [n].  ws: at least clamp_workspace_size(p) bytes. */
+clamp_status clamp_speckle_average(const clamp_params* p, const float* y, const float* pupil, const float* window,
+                                   float* r0, void* ws, size_t ws_bytes, void* stream);
+
+/* ---- Learned warm start: a 3-level 3D U-Net mapping the speckle-averaged image to an
+ * initial reflectance, trained on the GPU with these kernels.
+ *
+ * Architecture (encoder-decoder with concatenated skips, the pattern of the prior in
+ * Sec. III-C; channels c1/c2/c3 per level, 3x3x3 convs with zero padding):
+ *   e1 = relu(conv(x))  s1 = relu(conv(e1))       [c1, full size]
+ *   p1 = maxpool2(s1);  e2 = relu(conv(p1))  s2 = relu(conv(e2))   [c2, half]
+ *   p2 = maxpool2(s2);  b1 = relu(conv(p2))  b2 = relu(conv(b1))   [c3, quarter]
+ *   u2 = tconv2(b2);    d2 = relu(conv(relu(conv([u2, s2]))))      [c2, half]
+ *   u1 = tconv2(d2);    d1 = relu(conv(relu(conv([u1, s1]))))      [c1, full]
+ *   out = conv1x1(d1)                                              [1]
+ * maxpool2: 2x2x2 max-pooling; tconv2: transposed conv with a 2x2x2 kernel and stride 2.
+ * Parameters, in this order, each layer's weights then its c_out biases (float32):
+ *   3x3x3 conv: W[c_out][c_in][3][3][3] (cross-correlation, tap (dz,dy,dx) reads the
+ *   input at offset (dz-1, dy-1, dx-1));  tconv2: W[c_in][c_out][2][2][2] with
+ *   out[2v + d] = b + sum_ci W[ci][co][d] in[v];  1x1: W[1][c1].
+ * Layers: conv 1->c1, c1->c1, c1->c2, c2->c2, c2->c3, c3->c3, tconv c3->c2,
+ *   conv 2c2->c2, c2->c2, tconv c2->c1, conv 2c1->c1, c1->c1, 1x1 c1->1.
+ * Tensors are float32 [batch][channels][nz][ny][nx] on the device; nx, ny, nz must be
+ * multiples of 4.  dtype CLAMP_DENOISER_BF16: every conv rounds its weights and inputs
+ * (forward) or its two operands (gradients) to bfloat16 and accumulates in FP32;
+ * CLAMP_DENOISER_FP32: all FP32.  Master weights, gradients and Adam moments are FP32. */
+typedef struct clamp_unet clamp_unet;
+
+/* params_host: parameter_count floats, or NULL for zeros. */
+clamp_status clamp_unet_create(int32_t c1, int32_t c2, int32_t c3, int32_t dtype, const float* params_host,
+                               clamp_unet** out);
+void clamp_unet_destroy(clamp_unet* u);
+int64_t clamp_unet_param_count(const clamp_unet* u);
+/* Host copies of the state: which = 0 parameters, 1 gradients (of the last backward),
+ * 2 Adam first moments, 3 Adam second moments.  Synchronous. */
+clamp_status clamp_unet_get(const clamp_unet* u, int32_t which, float* host);
+clamp_status clamp_unet_set(clamp_unet* u, int32_t which, const float* host);
+/* Scratch bytes for a batch at (nx, ny, nz); training != 0 adds the gradient buffers. */
+size_t clamp_unet_workspace_size(const clamp_unet* u, int32_t batch, int32_t nx, int32_t ny, int32_t nz,
+                                 int32_t training);
+/* y[batch][n] = U-Net(x[batch][n]) (device pointers). */
+clamp_status clamp_unet_forward(clamp_unet* u, const float* x, float* y, int32_t batch, int32_t nx, int32_t ny,
+                                int32_t nz, void* ws, size_t ws_bytes, void* stream);
+/* Forward pass, loss = mean((U-Net(x) - target)^2) over all batch * n outputs, and the
+ * gradient of the loss with respect to every parameter (overwrites the gradient buffer).
+ * loss: optional DEVICE double. */
+clamp_status clamp_unet_backward(clamp_unet* u, const float* x, const float* target, int32_t batch, int32_t nx,
+                                 int32_t ny, int32_t nz, double* loss, void* ws, size_t ws_bytes, void* stream);
+/* Forward pass and loss = mean((U-Net(x) - target)^2) only (device double); ws as for
+ * clamp_unet_backward (training != 0). */
+clamp_status clamp_unet_loss(clamp_unet* u, const float* x, const float* target, int32_t batch, int32_t nx,
+                             int32_t ny, int32_t nz, double* loss, void* ws, size_t ws_bytes, void* stream);
+/* Per-sample normalisation of training pairs: m_b = mean(x_b) (FP64), x_out_b = x_b / m_b
+ * and, when t is non-NULL, t_out_b = t_b / m_b; a sample with m_b <= 0 is copied unscaled.
+ * x, t: device float [batch][n]; the outputs may alias the inputs. */
+clamp_status clamp_unet_normalize(int32_t batch, int64_t n, const float* x, const float* t, float* x_out,
+                                  float* t_out, void* stream);
+/* The warm start: m = mean(r0), r_init = m * max(U-Net(r0 / m), floor_rel).  r0 is the
+ * speckle average (clamp_speckle_average); r_init goes to clamp_reconstruct.  ws: at least
+ * clamp_unet_workspace_size(u, 1, nx, ny, nz, 0) bytes. */
+clamp_status clamp_unet_warm_start(clamp_unet* u, int32_t nx, int32_t ny, int32_t nz, const float* r0,
+                                   float floor_rel, float* r_init, void* ws, size_t ws_bytes, void* stream);
+/* One Adam step (Kingma and Ba, 2015, with bias correction; t >= 1 is the step number)
+ * on the parameters from the current gradients. */
+clamp_status clamp_unet_adam(clamp_unet* u, float lr, float beta1, float beta2, float eps, int32_t t,
+                             void* stream);
+
 #ifdef __cplusplus
 }
 #endif

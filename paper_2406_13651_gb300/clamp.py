@@ -37,6 +37,9 @@ EXPORTS = [
     "clamp_tc_gemm_bf16", "clamp_tc_gemm_tf32x3",
     "clamp_batch_workspace_size", "clamp_batch_create", "clamp_batch_launch", "clamp_batch_latencies",
     "clamp_batch_residuals", "clamp_batch_destroy", "clamp_autotune", "clamp_autotune_set",
+    "clamp_unet_create", "clamp_unet_destroy", "clamp_unet_param_count", "clamp_unet_get", "clamp_unet_set",
+    "clamp_unet_workspace_size", "clamp_unet_forward", "clamp_unet_backward", "clamp_unet_adam",
+    "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
 ]
 
 
@@ -115,6 +118,19 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_batch_destroy": (V, [P]),
         "clamp_autotune": (I, [PP, P, P, P, P, S, P, ctypes.POINTER(ctypes.c_int32)]),
         "clamp_autotune_set": (I, [PP, ctypes.POINTER(ctypes.c_int32)]),
+        "clamp_unet_create": (I, [I, I, I, I, P, ctypes.POINTER(P)]),
+        "clamp_unet_destroy": (V, [P]),
+        "clamp_unet_param_count": (ctypes.c_int64, [P]),
+        "clamp_unet_get": (I, [P, I, P]),
+        "clamp_unet_set": (I, [P, I, P]),
+        "clamp_unet_workspace_size": (S, [P, I, I, I, I, I]),
+        "clamp_unet_forward": (I, [P, P, P, I, I, I, I, P, S, P]),
+        "clamp_unet_backward": (I, [P, P, P, I, I, I, I, P, P, S, P]),
+        "clamp_unet_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P]),
+        "clamp_speckle_average": (I, [PP, P, P, P, P, P, S, P]),
+        "clamp_unet_normalize": (I, [I, ctypes.c_int64, P, P, P, P, P]),
+        "clamp_unet_warm_start": (I, [P, I, I, I, P, ctypes.c_float, P, P, S, P]),
+        "clamp_unet_loss": (I, [P, P, P, I, I, I, I, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -256,6 +272,16 @@ def init(p: Params, y, pupil, window, r_init=None, ws=None, stream=None):
     _check(load().clamp_init(ctypes.byref(p), _ptr(y), _ptr(pupil), _ptr(window), _ptr(r_init), _ptr(mu), _ptr(r),
                              _ptr(w), _ptr(ws), ws.numel(), _stream(stream)), "clamp_init")
     return mu, r, w
+
+
+def speckle_average(p: Params, y, pupil, window, out=None, ws=None, stream=None):
+    """r0 = (1/L) sum_l |A^H y_l / alpha|^2 (floored), device float32 [nz, ny, nx]."""
+    import torch
+    out = torch.empty((p.nz, p.ny, p.nx), dtype=torch.float32, device=y.device) if out is None else out
+    ws = workspace(p) if ws is None else ws
+    _check(load().clamp_speckle_average(ctypes.byref(p), _ptr(y), _ptr(pupil), _ptr(window), _ptr(out), _ptr(ws),
+                                        ws.numel(), _stream(stream)), "clamp_speckle_average")
+    return out
 
 
 def forward_prox(p: Params, k: int, y, pupil, window, mu, r, w, mu_residual=None, ws=None, stream=None):
@@ -404,3 +430,113 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class UNet:
+    """Owns a ``clamp_unet`` handle: the warm-start 3D U-Net (channels c1/c2/c3) with its
+    FP32 master parameters, gradients and Adam moments on the current CUDA device."""
+
+    STATE = {"params": 0, "grads": 1, "adam_m": 2, "adam_v": 3}
+
+    def __init__(self, c1: int, c2: int, c3: int, params: np.ndarray | None = None, dtype: str = "bf16"):
+        self.channels = (c1, c2, c3)
+        self.dtype = dtype
+        h = ctypes.c_void_p()
+        dt = DENOISER_BF16 if dtype == "bf16" else DENOISER_FP32
+        buf = None if params is None else np.ascontiguousarray(params, np.float32)
+        _check(load().clamp_unet_create(c1, c2, c3, dt, None if buf is None else buf.ctypes.data, ctypes.byref(h)),
+               "clamp_unet_create")
+        self.handle = h.value
+        self.count = int(load().clamp_unet_param_count(self.handle))
+        if buf is not None and buf.size != self.count:
+            self.close()
+            raise ValueError(f"expected {self.count} parameters, got {buf.size}")
+        self._ws = None
+        self.step = 0
+
+    def get(self, which: str = "params") -> np.ndarray:
+        out = np.empty(self.count, np.float32)
+        _check(load().clamp_unet_get(self.handle, self.STATE[which], out.ctypes.data), "clamp_unet_get")
+        return out
+
+    def set(self, values: np.ndarray, which: str = "params") -> None:
+        buf = np.ascontiguousarray(values, np.float32)
+        if buf.size != self.count:
+            raise ValueError(f"expected {self.count} values, got {buf.size}")
+        _check(load().clamp_unet_set(self.handle, self.STATE[which], buf.ctypes.data), "clamp_unet_set")
+
+    def workspace(self, batch: int, nx: int, ny: int, nz: int, training: bool):
+        need = load().clamp_unet_workspace_size(self.handle, batch, nx, ny, nz, int(training))
+        if need == 0:
+            raise ClampError(1, "clamp_unet_workspace_size", "nx, ny, nz must be multiples of 4")
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = None
+            self._ws = _ws(need)
+        return self._ws
+
+    def forward(self, x, out=None, stream=None):
+        """x: float32 [B, nz, ny, nx] (or [nz, ny, nx]) on the device."""
+        import torch
+        shp = x.shape if x.dim() == 4 else (1,) + tuple(x.shape)
+        B, nz, ny, nx = shp
+        if out is None:
+            out = torch.empty_like(x)
+        ws = self.workspace(B, nx, ny, nz, False)
+        _check(load().clamp_unet_forward(self.handle, _ptr(x), _ptr(out), B, nx, ny, nz, _ptr(ws), ws.numel(),
+                                         _stream(stream)), "clamp_unet_forward")
+        return out
+
+    def backward(self, x, target, loss=None, stream=None):
+        """Loss mean((U(x) - target)^2) into ``loss`` (device float64 scalar tensor, optional)
+        and every parameter's gradient into the handle's gradient buffer."""
+        shp = x.shape if x.dim() == 4 else (1,) + tuple(x.shape)
+        B, nz, ny, nx = shp
+        ws = self.workspace(B, nx, ny, nz, True)
+        _check(load().clamp_unet_backward(self.handle, _ptr(x), _ptr(target), B, nx, ny, nz, _ptr(loss),
+                                          _ptr(ws), ws.numel(), _stream(stream)), "clamp_unet_backward")
+
+    def loss(self, x, target, loss, stream=None):
+        """loss (device float64 scalar tensor) <- mean((U(x) - target)^2); no gradients."""
+        shp = x.shape if x.dim() == 4 else (1,) + tuple(x.shape)
+        B, nz, ny, nx = shp
+        ws = self.workspace(B, nx, ny, nz, True)
+        _check(load().clamp_unet_loss(self.handle, _ptr(x), _ptr(target), B, nx, ny, nz, _ptr(loss), _ptr(ws),
+                                      ws.numel(), _stream(stream)), "clamp_unet_loss")
+
+    def warm_start(self, r0, floor_rel: float = 1e-3, out=None, stream=None):
+        """r_init = m * max(U(r0 / m), floor_rel), m = mean(r0); r0 device float32 [nz, ny, nx]."""
+        import torch
+        nz, ny, nx = r0.shape
+        out = torch.empty_like(r0) if out is None else out
+        ws = self.workspace(1, nx, ny, nz, False)
+        _check(load().clamp_unet_warm_start(self.handle, nx, ny, nz, _ptr(r0), floor_rel, _ptr(out), _ptr(ws),
+                                            ws.numel(), _stream(stream)), "clamp_unet_warm_start")
+        return out
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, stream=None):
+        self.step += 1
+        _check(load().clamp_unet_adam(self.handle, lr, beta1, beta2, eps, self.step, _stream(stream)),
+               "clamp_unet_adam")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().clamp_unet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def unet_normalize(x, t=None, x_out=None, t_out=None, stream=None):
+    """Per-sample division by mean(x_b) of x [B, ...] (and t [B, ...]); in place by default."""
+    B = x.shape[0]
+    n = x.numel() // B
+    x_out = x if x_out is None else x_out
+    if t is not None and t_out is None:
+        t_out = t
+    _check(load().clamp_unet_normalize(B, n, _ptr(x), _ptr(t), _ptr(x_out), _ptr(t_out), _stream(stream)),
+           "clamp_unet_normalize")
+    return x_out, t_out

@@ -307,6 +307,28 @@ extern "C" clamp_status clamp_init(const clamp_params* p, const float* y, const 
   return do_init(p, d, y, pupil, window, r_init, reinterpret_cast<float2*>(mu), r, w, al, ws, st);
 }
 
+// The initial image of Alg. 2 on its own: r0 = (1/L) sum_l |A^H y_l / alpha|^2 (the
+// speckle average), floored as the initialisation floors it.  mu goes to the workspace's
+// U region and the broadcast state rows to its T region; row L of r is r0.
+extern "C" clamp_status clamp_speckle_average(const clamp_params* p, const float* y, const float* pupil,
+                                              const float* window, float* r0, void* ws, size_t ws_bytes,
+                                              void* stream) {
+  API_TRY(clamp_check_params(p));
+  API_TRY(need_ptrs({y, pupil, window, r0}, "clamp_speckle_average"));
+  const AgentLayout al = agent_layout(p);
+  API_TRY(check_ws(ws, ws_bytes, al.bytes, "clamp_speckle_average"));
+  API_TRY(api_ensure_device());
+  cudaStream_t st = (cudaStream_t)stream;
+  Derived d;
+  API_TRY(recon_prepare(p, pupil, window, st, &d));
+  const long long n = d.g.n, L = d.g.L;
+  float* rs = at<float>(ws, al.T);          // [L+1][n]
+  float* wsr = rs + (L + 1) * n;            // [L+1][n]  (4 L n floats >= 2 (L+1) n)
+  API_TRY(do_init(p, d, y, pupil, window, nullptr, at<float2>(ws, al.U), rs, wsr, al, ws, st));
+  API_CUDA(cudaMemcpyAsync(r0, rs + L * n, sizeof(float) * n, cudaMemcpyDeviceToDevice, st), "r0 copy");
+  return CLAMP_OK;
+}
+
 static float beta_of(int k) { return (float)(1.0 + 2.0 / log((double)k + 1.0)); }
 
 // ---------------------------------------------------------------- autotuner cache

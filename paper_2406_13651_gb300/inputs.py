@@ -208,6 +208,33 @@ def cnn_weights(layers: int, channels: int, seed: int, last_scale: float = 0.01)
     return ws, bs
 
 
+def unet_layer_shapes(c1: int, c2: int, c3: int):
+    """(weight shape, fan-in, c_out) of the 13 warm-start U-Net layers in parameter order
+    (3x3x3 conv [c_out][c_in][3][3][3], transposed conv [c_in][c_out][2][2][2], 1x1 [1][c1])."""
+    conv = lambda ci, co: ((co, ci, 3, 3, 3), 27 * ci, co)   # noqa: E731
+    tconv = lambda ci, co: ((ci, co, 2, 2, 2), ci, co)        # noqa: E731
+    return [conv(1, c1), conv(c1, c1), conv(c1, c2), conv(c2, c2), conv(c2, c3), conv(c3, c3), tconv(c3, c2),
+            conv(2 * c2, c2), conv(c2, c2), tconv(c2, c1), conv(2 * c1, c1), conv(c1, c1), ((1, c1, 1, 1, 1), c1, 1)]
+
+
+def unet_params(channels=(16, 32, 64), seed: int = 5) -> np.ndarray:
+    """Seeded He-normal initial U-Net parameters (std sqrt(2 / fan_in), zero biases), flat float32."""
+    parts = []
+    for i, (shape, fan_in, co) in enumerate(unet_layer_shapes(*channels)):
+        parts.append(normal(seed, 300 + i, int(np.prod(shape))) * math.sqrt(2.0 / fan_in))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def warmstart_specs(count: int = 2000, seed: int = 11, nx: int = 64, ny: int = 64, nz: int = 32, looks: int = 32,
+                    iters: int = 80):
+    """Training scenes of the warm start: column-surface scenes of one size, pupil radius
+    U[0.3, 0.5] Nyquist, SNR U[5, 20] dB, each with its own seed."""
+    u = uniform(seed, 600, 2 * count).reshape(count, 2)
+    return [dict(nx=nx, ny=ny, nz=nz, looks=looks, radius=0.3 + 0.2 * u[i, 0], snr=5.0 + 15.0 * u[i, 1],
+                 seed=seed * 100000 + i, iters=iters) for i in range(count)]
+
+
 # ----------------------------------------------------------------------------- workloads
 
 @dataclass
@@ -239,6 +266,7 @@ def make_workload(name: str, seed: int = 1, *, nx=None, ny=None, nz=None, looks=
     ``cfg1``      32x32x16, L=4, pupil R=0.5, Hann window, 10 dB, Gaussian sigma 0.8, 20 iterations.
     ``cfg2``      128x128x64, L=16, R=0.4, 15 dB, residual CNN 5 layers x 32 ch FP32, 50 iterations.
     ``cfg3``      256x256x128, L=32, facets, R=0.35, 10 dB, residual CNN 8 layers x 48 ch.
+    ``warm``      256x256x128, L=32, columns, R=0.4, 7.5 dB, Gaussian sigma 0.8 (warm-start comparison).
     Size keywords override the shape (same generator and parameters).
     """
     presets = {
@@ -250,6 +278,8 @@ def make_workload(name: str, seed: int = 1, *, nx=None, ny=None, nz=None, looks=
                      den={"kind": "cnn", "layers": 5, "channels": 32, "dtype": "fp32"}, iters=50),
         "cfg3": dict(nx=256, ny=256, nz=128, looks=32, radius=0.35, snr=10.0, scene="facets",
                      den={"kind": "cnn", "layers": 8, "channels": 48, "dtype": "bf16"}, iters=20),
+        "warm": dict(nx=256, ny=256, nz=128, looks=32, radius=0.4, snr=7.5, scene="columns",
+                     den={"kind": "gauss", "sigma": 0.8}, iters=400),
     }
     p = dict(presets[name])
     nx = nx or p["nx"]

@@ -1,0 +1,242 @@
+"""Learned warm start for CLAMP: a 3D U-Net maps the speckle-averaged image r0 (the
+initial image of Alg. 2) to an initial reflectance closer to the CLAMP solution.
+
+Every numerical step runs in the CUDA library: scene data come from the forward
+model (``clamp_simulate``), inputs from ``clamp_speckle_average``, training targets
+from plain CLAMP reconstructions run as one captured CUDA graph per group of
+scenes (``clamp_batch_*``), and the network is trained with the library's U-Net
+forward/backward kernels and Adam (``clamp_unet_*``).  PyTorch holds the device
+buffers and gathers mini-batches.
+
+Input and target of one training pair are both divided by mean(r0) of that scene;
+the warm start maps back with r_init = mean(r0) * max(U(r0 / mean(r0)), floor).
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import clamp as C
+from . import inputs as I
+
+CHANNELS = (16, 32, 64)
+FLOOR = 1e-3
+
+
+@dataclass
+class TrainConfig:
+    steps: int = 2000
+    batch: int = 24
+    lr: float = 1e-3
+    lr_decay: float = 0.975      # multiplied in every `decay_every` steps
+    decay_every: int = 100
+    val_every: int = 100
+    seed: int = 5
+
+
+@dataclass
+class Dataset:
+    x: object                    # device float32 [N, nz, ny, nx], r0 / mean(r0)
+    t: object                    # device float32 [N, nz, ny, nx], r* / mean(r0)
+    target_ce: np.ndarray        # final CE residual of every target reconstruction
+    seconds: float = 0.0
+
+
+@dataclass
+class TrainLog:
+    steps: list = field(default_factory=list)
+    train_loss: list = field(default_factory=list)
+    val_steps: list = field(default_factory=list)
+    val_loss: list = field(default_factory=list)
+    best_val: float = math.inf
+    best_step: int = 0
+    seconds: float = 0.0
+
+
+def _device_draws(shape, seed: int, dev):
+    """Circular complex Gaussian speckle and noise, CN(0, 1), drawn on the device (seeded)."""
+    import torch
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    s = 0.5 ** 0.5
+    spk = torch.complex(torch.randn(shape, generator=gen, device=dev), torch.randn(shape, generator=gen, device=dev)) * s
+    eta = torch.complex(torch.randn(shape, generator=gen, device=dev), torch.randn(shape, generator=gen, device=dev)) * s
+    return spk, eta
+
+
+def scene_data(spec: dict, dev):
+    """(params, y, pupil, window) of one warm-start scene: column-surface reflectance and
+    aperture from the seeded generators, looks simulated by the library's forward model."""
+    import torch
+    wl = I.batch_scene(spec, with_draws=False)
+    p = C.make_params(wl.nx, wl.ny, wl.nz, wl.looks, wl.noise_var, wl.prox_var, max_iters=spec["iters"])
+    pu = torch.from_numpy(wl.pupil).to(dev)
+    wi = torch.from_numpy(wl.window).to(dev)
+    spk, eta = _device_draws((wl.looks, wl.nz, wl.ny, wl.nx), spec["seed"], dev)
+    y = C.simulate(p, torch.from_numpy(wl.r_true.astype(np.float32)).to(dev), spk, eta, pu, wi)
+    return p, y, pu, wi
+
+
+def make_dataset(specs, dev, group: int = 24, den: C.Denoiser | None = None, log=None) -> Dataset:
+    """Training pairs for every spec: x = r0 / mean(r0), t = r* / mean(r0), where r* is the
+    plain CLAMP reconstruction after spec['iters'] iterations (Gaussian prior)."""
+    import torch
+    den = den or C.Denoiser.gauss(0.8)
+    s0 = specs[0]
+    shape = (s0["nz"], s0["ny"], s0["nx"])
+    N = len(specs)
+    X = torch.empty((N,) + shape, dtype=torch.float32, device=dev)
+    T = torch.empty_like(X)
+    ce = np.zeros(N)
+    t0 = time.perf_counter()
+    ws = None
+    for g0 in range(0, N, group):
+        chunk = specs[g0:g0 + group]
+        scenes = []
+        for i, sp in enumerate(chunk):
+            p, y, pu, wi = scene_data(sp, dev)
+            if ws is None:
+                ws = C.workspace(p)
+            C.speckle_average(p, y, pu, wi, out=X[g0 + i], ws=ws)
+            scenes.append((p, y, pu, wi, T[g0 + i]))
+        batch = C.Batch(scenes, den)
+        batch.launch()
+        ce[g0:g0 + len(chunk)] = batch.residuals()
+        batch.close()
+        del scenes, batch
+        C.unet_normalize(X[g0:g0 + len(chunk)], T[g0:g0 + len(chunk)])
+        if log:
+            log(f"data {g0 + len(chunk)}/{N}: max target CE {ce[g0:g0 + len(chunk)].max():.2e}")
+    torch.cuda.synchronize()
+    return Dataset(X, T, ce, time.perf_counter() - t0)
+
+
+def train(net: C.UNet, data: Dataset, n_train: int, cfg: TrainConfig, log=None) -> TrainLog:
+    """Adam on mean squared error over mini-batches of the first n_train pairs; the rest is
+    the validation set.  The parameters with the lowest validation loss are kept."""
+    import torch
+    dev = data.x.device
+    N = data.x.shape[0]
+    rng = np.random.default_rng(cfg.seed)
+    loss_d = torch.zeros((), dtype=torch.float64, device=dev)
+    out = TrainLog()
+    best = net.get("params")
+    order = rng.permutation(n_train)
+    pos = 0
+    lr = cfg.lr
+    t0 = time.perf_counter()
+
+    def val_loss():
+        tot, cnt = 0.0, 0
+        for v0 in range(n_train, N, cfg.batch):
+            v1 = min(N, v0 + cfg.batch)
+            net.loss(data.x[v0:v1], data.t[v0:v1], loss_d)
+            tot += float(loss_d.item()) * (v1 - v0)
+            cnt += v1 - v0
+        return tot / max(cnt, 1)
+
+    for step in range(1, cfg.steps + 1):
+        if pos + cfg.batch > n_train:
+            order = rng.permutation(n_train)
+            pos = 0
+        idx = torch.from_numpy(order[pos:pos + cfg.batch]).to(dev)
+        pos += cfg.batch
+        xb = data.x.index_select(0, idx)
+        tb = data.t.index_select(0, idx)
+        net.backward(xb, tb, loss_d)
+        net.adam(lr)
+        if step % cfg.decay_every == 0:
+            lr *= cfg.lr_decay
+        if step % 20 == 0 or step == 1:
+            out.steps.append(step)
+            out.train_loss.append(float(loss_d.item()))
+        if n_train < N and (step % cfg.val_every == 0 or step == cfg.steps):
+            vl = val_loss()
+            out.val_steps.append(step)
+            out.val_loss.append(vl)
+            if vl < out.best_val:
+                out.best_val, out.best_step = vl, step
+                best = net.get("params")
+            if log:
+                log(f"step {step}: train {out.train_loss[-1]:.4e} val {vl:.4e} lr {lr:.2e}")
+    torch.cuda.synchronize()
+    out.seconds = time.perf_counter() - t0
+    if n_train < N:
+        net.set(best, "params")
+    return out
+
+
+def warm_start(net: C.UNet, p: C.Params, y, pupil, window, ws=None, floor: float = FLOOR):
+    """r_init for clamp_reconstruct: the U-Net applied fully convolutionally to r0."""
+    r0 = C.speckle_average(p, y, pupil, window, ws=ws)
+    return net.warm_start(r0, floor)
+
+
+def first_below(ce_hist: np.ndarray, tol: float) -> int:
+    """1-based iteration at which the CE residual first reaches tol (0 if never)."""
+    hit = np.nonzero(np.asarray(ce_hist) <= tol)[0]
+    return int(hit[0]) + 1 if hit.size else 0
+
+
+def compare(net: C.UNet, p_plain: C.Params, y, pupil, window, den: C.Denoiser, tol: float = 1e-3,
+            max_iters: int = 300, ref_iters: int = 0, warm_k0: int = 0):
+    """Iterations and wall time to CE <= tol from the speckle-average init and from the warm
+    start (which includes r0, the U-Net inference and the mapping), on the same data, and
+    both results' relative L2 distance to the plain solution run for ref_iters iterations
+    (2 x the plain count when 0).  warm_k0 starts the warm run's beta_k schedule at
+    k = warm_k0 + 1 (App. A) instead of k = 1."""
+    import torch
+    p = C.make_params(p_plain.nx, p_plain.ny, p_plain.nz, p_plain.looks, p_plain.noise_var, p_plain.prox_var,
+                      max_iters=max_iters, tol=tol, check_every=1)
+    ws = C.reconstruct_workspace(p, den)
+    aws = C.workspace(p)
+    r_plain = torch.empty((p.nz, p.ny, p.nx), dtype=torch.float32, device=y.device)
+    r_warm = torch.empty_like(r_plain)
+
+    def run_plain():
+        return C.reconstruct(p, y, pupil, window, den, ws=ws, r_out=r_plain)
+
+    pw = C.make_params(p.nx, p.ny, p.nz, p.looks, p.noise_var, p.prox_var, max_iters=max_iters, tol=tol,
+                       check_every=1, k0=warm_k0)
+
+    def run_warm():
+        ri = warm_start(net, p, y, pupil, window, ws=aws)
+        return C.reconstruct(pw, y, pupil, window, den, r_init=ri, ws=ws, r_out=r_warm)
+
+    run_plain()
+    run_warm()        # warm-up (autotune, workspaces, module load)
+    out = {}
+    for name, fn in (("plain", run_plain), ("warm", run_warm)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = fn()
+        torch.cuda.synchronize()
+        out[name] = dict(seconds=time.perf_counter() - t0, iters=first_below(res.ce_hist, tol),
+                         converged=res.converged, ce_final=float(res.ce_hist[-1]) if len(res.ce_hist) else 0.0)
+    n_ref = ref_iters or 2 * max(out["plain"]["iters"], 1)
+    pr = C.make_params(p.nx, p.ny, p.nz, p.looks, p.noise_var, p.prox_var, max_iters=n_ref)
+    ref = C.reconstruct(pr, y, pupil, window, den, ws=ws)
+    rref = ref.r
+
+    def rel(a):
+        return float(torch.linalg.vector_norm(a.double() - rref.double()) / torch.linalg.vector_norm(rref.double()))
+
+    out["plain"]["rel_err_vs_ref"] = rel(r_plain)
+    out["warm"]["rel_err_vs_ref"] = rel(r_warm)
+    out["ref_iters"] = n_ref
+    out["ref_ce"] = float(ref.ce_hist[-1])
+    return out
+
+
+def save(path: str, net: C.UNet, meta: dict) -> None:
+    np.savez_compressed(path, params=net.get("params"), channels=np.array(net.channels),
+                        meta=np.array(repr(meta)))
+
+
+def load(path: str, dtype: str = "bf16") -> C.UNet:
+    z = np.load(path)
+    c1, c2, c3 = (int(v) for v in z["channels"])
+    return C.UNet(c1, c2, c3, params=z["params"], dtype=dtype)
