@@ -40,7 +40,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="clamp", choices=["clamp", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "batch"])
+    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "batch", "warm"])
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="skip the warm-start comparison (256x256x128, L=32) on the default line")
     ap.add_argument("--batch-iters", type=int, default=10)
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -321,6 +323,40 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def warm_start_leg(dev) -> dict:
+    """Time to CE residual 1e-3 from the speckle-average init and from the learned warm start
+    (speckle average + U-Net inference + mapping included), same data, 256x256x128, L=32."""
+    from paper_2406_13651_gb300 import warmstart as Wm
+    if not os.path.exists(Wm.WEIGHTS):
+        return {"unavailable": "trained warm-start weights are missing"}
+    return Wm.warm_workload_report(dev)
+
+
+def run_warm(args, rank, world, local):
+    """The warm-start comparison alone: value = wall seconds to CE residual 1e-3 with the
+    learned warm start (lower is better); the plain-init time is alongside."""
+    import torch
+    from paper_2406_13651_gb300 import build as B
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    B.build()
+    dev = torch.device("cuda", local)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        c = warm_start_leg(dev)
+    if "unavailable" in c:
+        print(json.dumps({"metric": METRIC, "unavailable": c["unavailable"]}), flush=True)
+        return 0
+    line = {"metric": METRIC, "value": c["warm"]["seconds"], "unit": "s to CE residual 1e-3 (warm start)",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": c["warm"]["seconds"] * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": c["workload"], "network": c["network"], "tol": c["tol"],
+                                            "l2": "inputs larger than L2 (12.9 GB per iteration)"},
+            "warm_start": c, "gpu_launches": None, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -330,6 +366,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "batch":
         return run_batch(args, rank, world, local)
+    if args.workload == "warm":
+        return run_warm(args, rank, world, local)
 
     import numpy as np
     import torch
@@ -503,6 +541,12 @@ def main():
         cpu = {"value": n * L / t_it, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": desc}
 
     launches_per_iter = 5 + 1 + (len(wl.denoiser.get("weights", [])) if wl.denoiser["kind"] == "cnn" else 1) + 1 + 1
+    warm = None
+    if world == 1 and not args.no_warm_start:
+        del mu, r, w, ws, y
+        torch.cuda.empty_cache()
+        warm = warm_start_leg(dev)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -517,6 +561,7 @@ def main():
         "clocks": clk.summary(),
         "ce_residual_last": ce_last, "finite": finite,
         "fft_variants": {"passes": ["x", "y", "z fused", "inverse y", "inverse x"], "chosen": variants},
+        "warm_start": warm,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

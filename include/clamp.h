@@ -333,14 +333,16 @@ clamp_status clamp_unet_backward(clamp_unet* u, const float* x, const float* tar
  * clamp_unet_backward (training != 0). */
 clamp_status clamp_unet_loss(clamp_unet* u, const float* x, const float* target, int32_t batch, int32_t nx,
                              int32_t ny, int32_t nz, double* loss, void* ws, size_t ws_bytes, void* stream);
-/* Per-sample normalisation of training pairs: m_b = mean(x_b) (FP64), x_out_b = x_b / m_b
- * and, when t is non-NULL, t_out_b = t_b / m_b; a sample with m_b <= 0 is copied unscaled.
- * x, t: device float [batch][n]; the outputs may alias the inputs. */
-clamp_status clamp_unet_normalize(int32_t batch, int64_t n, const float* x, const float* t, float* x_out,
-                                  float* t_out, void* stream);
-/* The warm start: m = mean(r0), r_init = m * max(U-Net(r0 / m), floor_rel).  r0 is the
- * speckle average (clamp_speckle_average); r_init goes to clamp_reconstruct.  ws: at least
- * clamp_unet_workspace_size(u, 1, nx, ny, nz, 0) bytes. */
+/* Per-sample normalisation of training pairs: m_b = sum(x_b) / norm_count (FP64),
+ * x_out_b = x_b / m_b and, when t is non-NULL, t_out_b = t_b / m_b; a sample with m_b <= 0
+ * is copied unscaled.  The warm start uses norm_count = nx * ny (energy per (x, y) column,
+ * which does not change with the range extent nz).  x, t: device float [batch][n]; the
+ * outputs may alias the inputs. */
+clamp_status clamp_unet_normalize(int32_t batch, int64_t n, int64_t norm_count, const float* x, const float* t,
+                                  float* x_out, float* t_out, void* stream);
+/* The warm start: m = sum(r0) / (nx ny), r_init = m * max(U-Net(r0 / m), floor_rel).  r0 is
+ * the speckle average (clamp_speckle_average); r_init goes to clamp_reconstruct.  ws: at
+ * least clamp_unet_workspace_size(u, 1, nx, ny, nz, 0) bytes. */
 clamp_status clamp_unet_warm_start(clamp_unet* u, int32_t nx, int32_t ny, int32_t nz, const float* r0,
                                    float floor_rel, float* r_init, void* ws, size_t ws_bytes, void* stream);
 /* One Adam step (Kingma and Ba, 2015, with bias correction; t >= 1 is the step number)

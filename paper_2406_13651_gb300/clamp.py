@@ -128,7 +128,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_unet_backward": (I, [P, P, P, I, I, I, I, P, P, S, P]),
         "clamp_unet_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P]),
         "clamp_speckle_average": (I, [PP, P, P, P, P, P, S, P]),
-        "clamp_unet_normalize": (I, [I, ctypes.c_int64, P, P, P, P, P]),
+        "clamp_unet_normalize": (I, [I, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]),
         "clamp_unet_warm_start": (I, [P, I, I, I, P, ctypes.c_float, P, P, S, P]),
         "clamp_unet_loss": (I, [P, P, P, I, I, I, I, P, P, S, P]),
     }
@@ -504,7 +504,7 @@ class UNet:
                                       ws.numel(), _stream(stream)), "clamp_unet_loss")
 
     def warm_start(self, r0, floor_rel: float = 1e-3, out=None, stream=None):
-        """r_init = m * max(U(r0 / m), floor_rel), m = mean(r0); r0 device float32 [nz, ny, nx]."""
+        """r_init = m * max(U(r0 / m), floor_rel), m = sum(r0) / (nx ny); r0 device float32 [nz, ny, nx]."""
         import torch
         nz, ny, nx = r0.shape
         out = torch.empty_like(r0) if out is None else out
@@ -531,12 +531,13 @@ class UNet:
 
 
 def unet_normalize(x, t=None, x_out=None, t_out=None, stream=None):
-    """Per-sample division by mean(x_b) of x [B, ...] (and t [B, ...]); in place by default."""
+    """Per-sample division of x [B, nz, ny, nx] (and t) by m_b = sum(x_b) / (nx ny); in place by default."""
     B = x.shape[0]
     n = x.numel() // B
+    cols = x.shape[-1] * x.shape[-2]
     x_out = x if x_out is None else x_out
     if t is not None and t_out is None:
         t_out = t
-    _check(load().clamp_unet_normalize(B, n, _ptr(x), _ptr(t), _ptr(x_out), _ptr(t_out), _stream(stream)),
+    _check(load().clamp_unet_normalize(B, n, cols, _ptr(x), _ptr(t), _ptr(x_out), _ptr(t_out), _stream(stream)),
            "clamp_unet_normalize")
     return x_out, t_out

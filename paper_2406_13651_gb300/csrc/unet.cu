@@ -442,11 +442,12 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
   }
 }
 
-// Per-sample normalisation by the sample's mean (one CTA per sample): xo = x / m,
-// to = t / m with m = mean(x) in FP64 (m <= 0 leaves the sample unscaled).
+// Per-sample normalisation (one CTA per sample): m = sum(x_b) / norm_count in FP64,
+// xo = x / m, to = t / m (m <= 0 leaves the sample unscaled).
 constexpr int NORM_T = 1024;
 __global__ void __launch_bounds__(NORM_T) k_sample_norm(const float* __restrict__ x, const float* __restrict__ t,
-                                                        float* __restrict__ xo, float* __restrict__ to, long long n) {
+                                                        float* __restrict__ xo, float* __restrict__ to, long long n,
+                                                        double norm_count) {
   const long long base = (long long)blockIdx.x * n;
   double acc = 0.0;
   for (long long i = threadIdx.x; i < n; i += NORM_T) acc += (double)x[base + i];
@@ -457,7 +458,7 @@ __global__ void __launch_bounds__(NORM_T) k_sample_norm(const float* __restrict_
     if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
     __syncthreads();
   }
-  const double m = red[0] / (double)n;
+  const double m = red[0] / norm_count;
   const float inv = m > 0.0 ? (float)(1.0 / m) : 1.0f;
   for (long long i = threadIdx.x; i < n; i += NORM_T) {
     xo[base + i] = x[base + i] * inv;
@@ -479,30 +480,31 @@ __global__ void __launch_bounds__(UT) k_sum_part(const float* __restrict__ x, lo
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
 }
 
-__device__ double mean_of_parts(const double* part, int np, long long n) {
+__device__ double mean_of_parts(const double* part, int np, double norm_count) {
   __shared__ double m_s;
   if (threadIdx.x == 0) {
     double a = 0.0;
     for (int i = 0; i < np; ++i) a += part[i];
-    m_s = a / (double)n;
+    m_s = a / norm_count;
   }
   __syncthreads();
   return m_s;
 }
 
-// xo = x / m  (m from the partials; m <= 0 leaves x unscaled)
+// xo = x / m, m = sum(x) / norm_count from the partials (m <= 0 leaves x unscaled)
 __global__ void __launch_bounds__(UT) k_scale_by_mean(const float* __restrict__ x, long long n,
-                                                     const double* __restrict__ part, int np, float* __restrict__ xo) {
-  const double m = mean_of_parts(part, np, n);
+                                                     const double* __restrict__ part, int np, double norm_count,
+                                                     float* __restrict__ xo) {
+  const double m = mean_of_parts(part, np, norm_count);
   const float inv = m > 0.0 ? (float)(1.0 / m) : 1.0f;
   for (long long i = (long long)blockIdx.x * UT + threadIdx.x; i < n; i += (long long)gridDim.x * UT) xo[i] = x[i] * inv;
 }
 
 // r_init = m * max(out, floor): the network's output back in the input's units, kept positive.
 __global__ void __launch_bounds__(UT) k_warm_map(const float* __restrict__ out, long long n,
-                                                 const double* __restrict__ part, int np, float floor_rel,
-                                                 float* __restrict__ r) {
-  const double m = mean_of_parts(part, np, n);
+                                                 const double* __restrict__ part, int np, double norm_count,
+                                                 float floor_rel, float* __restrict__ r) {
+  const double m = mean_of_parts(part, np, norm_count);
   const float sc = m > 0.0 ? (float)m : 1.0f;
   for (long long i = (long long)blockIdx.x * UT + threadIdx.x; i < n; i += (long long)gridDim.x * UT)
     r[i] = sc * fmaxf(out[i], floor_rel);
@@ -823,11 +825,11 @@ extern "C" clamp_status clamp_unet_adam(clamp_unet* u, float lr, float beta1, fl
   return CLAMP_OK;
 }
 
-extern "C" clamp_status clamp_unet_normalize(int32_t batch, int64_t n, const float* x, const float* t, float* x_out,
-                                             float* t_out, void* stream) {
-  if (batch < 1 || n < 1 || !x || !x_out || (t && !t_out))
+extern "C" clamp_status clamp_unet_normalize(int32_t batch, int64_t n, int64_t norm_count, const float* x,
+                                             const float* t, float* x_out, float* t_out, void* stream) {
+  if (batch < 1 || n < 1 || norm_count < 1 || !x || !x_out || (t && !t_out))
     return api_fail(CLAMP_EINVAL, "clamp_unet_normalize: bad arguments");
-  k_sample_norm<<<batch, NORM_T, 0, (cudaStream_t)stream>>>(x, t, x_out, t_out, (long long)n);
+  k_sample_norm<<<batch, NORM_T, 0, (cudaStream_t)stream>>>(x, t, x_out, t_out, (long long)n, (double)norm_count);
   U_TRY(cudaGetLastError());
   return CLAMP_OK;
 }
@@ -844,11 +846,12 @@ extern "C" clamp_status clamp_unet_warm_start(clamp_unet* u, int32_t nx, int32_t
   const long long n = (long long)nx * ny * nz;
   const unsigned np = grid_for(n);
   k_sum_part<<<np, UT, 0, st>>>(r0, n, a.part);
-  k_scale_by_mean<<<grid_for(n), UT, 0, st>>>(r0, n, a.part, (int)np, a.xin);
+  const double cols = (double)nx * ny;   // m = sum(r0) / (nx ny): energy per (x, y) column
+  k_scale_by_mean<<<grid_for(n), UT, 0, st>>>(r0, n, a.part, (int)np, cols, a.xin);
   U_TRY(cudaGetLastError());
   clamp_status s = unet_forward(u, a.xin, 1, nx, ny, nz, a, st);
   if (s != CLAMP_OK) return s;
-  k_warm_map<<<grid_for(n), UT, 0, st>>>(a.out, n, a.part, (int)np, floor_rel, r_init);
+  k_warm_map<<<grid_for(n), UT, 0, st>>>(a.out, n, a.part, (int)np, cols, floor_rel, r_init);
   U_TRY(cudaGetLastError());
   return CLAMP_OK;
 }

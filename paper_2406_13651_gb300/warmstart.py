@@ -8,12 +8,15 @@ scenes (``clamp_batch_*``), and the network is trained with the library's U-Net
 forward/backward kernels and Adam (``clamp_unet_*``).  PyTorch holds the device
 buffers and gathers mini-batches.
 
-Input and target of one training pair are both divided by mean(r0) of that scene;
-the warm start maps back with r_init = mean(r0) * max(U(r0 / mean(r0)), floor).
+Input and target of one training pair are both divided by m = sum(r0) / (nx ny), the
+energy of r0 per (x, y) column (unlike mean(r0) it does not change with the range
+extent nz, so a network trained on 64x64x32 volumes sees the same value scale on
+256x256x128); the warm start maps back with r_init = m * max(U(r0 / m), floor).
 """
 from __future__ import annotations
 
 import math
+import os
 import time
 from dataclasses import dataclass, field
 
@@ -39,8 +42,8 @@ class TrainConfig:
 
 @dataclass
 class Dataset:
-    x: object                    # device float32 [N, nz, ny, nx], r0 / mean(r0)
-    t: object                    # device float32 [N, nz, ny, nx], r* / mean(r0)
+    x: object                    # device float32 [N, nz, ny, nx], r0 / m
+    t: object                    # device float32 [N, nz, ny, nx], r* / m
     target_ce: np.ndarray        # final CE residual of every target reconstruction
     seconds: float = 0.0
 
@@ -56,7 +59,7 @@ class TrainLog:
     seconds: float = 0.0
 
 
-def _device_draws(shape, seed: int, dev):
+def device_draws(shape, seed: int, dev):
     """Circular complex Gaussian speckle and noise, CN(0, 1), drawn on the device (seeded)."""
     import torch
     gen = torch.Generator(device=dev)
@@ -75,13 +78,13 @@ def scene_data(spec: dict, dev):
     p = C.make_params(wl.nx, wl.ny, wl.nz, wl.looks, wl.noise_var, wl.prox_var, max_iters=spec["iters"])
     pu = torch.from_numpy(wl.pupil).to(dev)
     wi = torch.from_numpy(wl.window).to(dev)
-    spk, eta = _device_draws((wl.looks, wl.nz, wl.ny, wl.nx), spec["seed"], dev)
+    spk, eta = device_draws((wl.looks, wl.nz, wl.ny, wl.nx), spec["seed"], dev)
     y = C.simulate(p, torch.from_numpy(wl.r_true.astype(np.float32)).to(dev), spk, eta, pu, wi)
     return p, y, pu, wi
 
 
 def make_dataset(specs, dev, group: int = 24, den: C.Denoiser | None = None, log=None) -> Dataset:
-    """Training pairs for every spec: x = r0 / mean(r0), t = r* / mean(r0), where r* is the
+    """Training pairs for every spec: x = r0 / m, t = r* / m (m = sum(r0) / (nx ny)), where r* is the
     plain CLAMP reconstruction after spec['iters'] iterations (Gaussian prior)."""
     import torch
     den = den or C.Denoiser.gauss(0.8)
@@ -181,16 +184,27 @@ def first_below(ce_hist: np.ndarray, tol: float) -> int:
     return int(hit[0]) + 1 if hit.size else 0
 
 
+def psnr(r_hat: np.ndarray, r_true: np.ndarray) -> float:
+    """PSNR of the optimally scaled reconstruction (Sec. IV-B): 10 log10(n / ||b r_hat - r||^2)
+    with b = r_hat . r / ||r_hat||^2."""
+    rh = np.asarray(r_hat, np.float64).ravel()
+    rt = np.asarray(r_true, np.float64).ravel()
+    b = float(rh @ rt) / max(float(rh @ rh), 1e-300)
+    return float(10.0 * np.log10(rt.size / max(float(np.sum((b * rh - rt) ** 2)), 1e-300)))
+
+
 def compare(net: C.UNet, p_plain: C.Params, y, pupil, window, den: C.Denoiser, tol: float = 1e-3,
-            max_iters: int = 300, ref_iters: int = 0, warm_k0: int = 0):
+            max_iters: int = 300, ref_iters: int = 0, warm_k0: int = 0, r_true: np.ndarray | None = None):
     """Iterations and wall time to CE <= tol from the speckle-average init and from the warm
-    start (which includes r0, the U-Net inference and the mapping), on the same data, and
-    both results' relative L2 distance to the plain solution run for ref_iters iterations
-    (2 x the plain count when 0).  warm_k0 starts the warm run's beta_k schedule at
-    k = warm_k0 + 1 (App. A) instead of k = 1."""
+    start (which includes r0, the U-Net inference and the mapping), on the same data; both
+    results' relative L2 distance to the plain solution run for ref_iters iterations
+    (2 x the plain count when 0) and, given r_true, their PSNR.  warm_k0 starts the warm
+    run's beta_k schedule at k = warm_k0 + 1 (App. A) instead of k = 1."""
     import torch
     p = C.make_params(p_plain.nx, p_plain.ny, p_plain.nz, p_plain.looks, p_plain.noise_var, p_plain.prox_var,
                       max_iters=max_iters, tol=tol, check_every=1)
+    pw = C.make_params(p.nx, p.ny, p.nz, p.looks, p.noise_var, p.prox_var, max_iters=max_iters, tol=tol,
+                       check_every=1, k0=warm_k0)
     ws = C.reconstruct_workspace(p, den)
     aws = C.workspace(p)
     r_plain = torch.empty((p.nz, p.ny, p.nx), dtype=torch.float32, device=y.device)
@@ -198,9 +212,6 @@ def compare(net: C.UNet, p_plain: C.Params, y, pupil, window, den: C.Denoiser, t
 
     def run_plain():
         return C.reconstruct(p, y, pupil, window, den, ws=ws, r_out=r_plain)
-
-    pw = C.make_params(p.nx, p.ny, p.nz, p.looks, p.noise_var, p.prox_var, max_iters=max_iters, tol=tol,
-                       check_every=1, k0=warm_k0)
 
     def run_warm():
         ri = warm_start(net, p, y, pupil, window, ws=aws)
@@ -218,17 +229,43 @@ def compare(net: C.UNet, p_plain: C.Params, y, pupil, window, den: C.Denoiser, t
                          converged=res.converged, ce_final=float(res.ce_hist[-1]) if len(res.ce_hist) else 0.0)
     n_ref = ref_iters or 2 * max(out["plain"]["iters"], 1)
     pr = C.make_params(p.nx, p.ny, p.nz, p.looks, p.noise_var, p.prox_var, max_iters=n_ref)
-    ref = C.reconstruct(pr, y, pupil, window, den, ws=ws)
-    rref = ref.r
-
-    def rel(a):
-        return float(torch.linalg.vector_norm(a.double() - rref.double()) / torch.linalg.vector_norm(rref.double()))
-
-    out["plain"]["rel_err_vs_ref"] = rel(r_plain)
-    out["warm"]["rel_err_vs_ref"] = rel(r_warm)
+    ref = C.reconstruct(pr, y, pupil, window, den, ws=ws).r.cpu().numpy().astype(np.float64)
+    nref = np.linalg.norm(ref)
+    for name, r in (("plain", r_plain), ("warm", r_warm)):
+        rh = r.cpu().numpy()
+        out[name]["rel_err_vs_ref"] = float(np.linalg.norm(rh - ref) / nref)
+        if r_true is not None:
+            out[name]["psnr"] = psnr(rh, r_true)
     out["ref_iters"] = n_ref
-    out["ref_ce"] = float(ref.ce_hist[-1])
+    if r_true is not None:
+        out["ref_psnr"] = psnr(ref, r_true)
     return out
+
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "unet_warmstart.npz")
+
+
+def warm_workload_report(dev, seed: int = 1, weights: str = WEIGHTS, tol: float = 1e-3) -> dict:
+    """The warm-start comparison at 256x256x128, L = 32 (inputs.make_workload('warm')):
+    iterations and wall time to CE <= tol, plain vs warm start, with the relative distance
+    to the plain solution run twice as long and the PSNR against the ground truth."""
+    import torch
+    net = load(weights, dtype="bf16")
+    wl = I.make_workload("warm", seed=seed, with_draws=False)
+    den = C.Denoiser.from_desc(wl.denoiser)
+    p = C.make_params(wl.nx, wl.ny, wl.nz, wl.looks, wl.noise_var, wl.prox_var)
+    pu, wi = torch.from_numpy(wl.pupil).to(dev), torch.from_numpy(wl.window).to(dev)
+    spk, eta = device_draws((wl.looks, wl.nz, wl.ny, wl.nx), 1233 + seed, dev)
+    y = C.simulate(p, torch.from_numpy(wl.r_true.astype(np.float32)).to(dev), spk, eta, pu, wi)
+    del spk, eta
+    c = compare(net, p, y, pu, wi, den, tol=tol, max_iters=wl.iters, r_true=wl.r_true)
+    c["tol"] = tol
+    c["speedup_wall"] = c["plain"]["seconds"] / max(c["warm"]["seconds"], 1e-12)
+    c["workload"] = ("256x256x128 complex64, L=32, column-surface scene, pupil R=0.4, Hann window, "
+                     "SNR 1.5 dB (per-surface-voxel SNR of 7.5 dB at nz=32), Gaussian prior sigma 0.8")
+    c["network"] = ("3-level 3D U-Net 16/32/64, BF16 operands / FP32 accumulation, trained by the library's "
+                    "kernels on 2000 scenes of 64x64x32 (L=32, R~U[0.3,0.5], SNR~U[5,20] dB)")
+    return c
 
 
 def save(path: str, net: C.UNet, meta: dict) -> None:
