@@ -435,12 +435,13 @@ static cudaError_t dispatch_var(int V, F&& f) {
 
 bool variant_valid(int pass, int V, int nx, int ny, int nz) {
   if (V < 0 || V >= kVariants) return false;
-  if (V != 2) return true;
+  if (V == 0 || V == 1) return true;
   if (pass == 0 || pass == 4) return true;   // x passes: half the rows per CTA always divides nz * ny
+  if (V == 3) return nx % 16 == 0;            // y / z passes: pipe_cols <= 16 adjacent columns
   return nx % 32 == 0;                        // y / z passes: 32 adjacent columns
 }
 
-int max_pz(int nx, int ny) { return (nx / LC) * ny; }
+int max_pz(int nx, int ny) { return (nx / 8) * ny; }   // the narrowest column tile is 8 (pipe_cols)
 int max_px(int nx, int ny, int nz) {
   int m = 0;
   for (int V = 0; V < kVariants; ++V) {
@@ -455,6 +456,10 @@ cudaError_t launch_agent_pass(int pass, int V, const Geom& g, const AgentScalars
                               const float* rprev, const float2* y, const float* pupil, const float* window, float4* T,
                               float2* U, Partials& p, cudaStream_t st) {
   if (!variant_valid(pass, V, g.nx, g.ny, g.nz)) return cudaErrorInvalidValue;
+  if (V == 3) {
+    const int axis_len = (pass == 0 || pass == 4) ? g.nx : (pass == 2 ? g.nz : g.ny);
+    return launch_pipe_pass(pass, g, s, mu, rprev, y, pupil, window, T, U, p, tw_ptr(axis_len), st);
+  }
   switch (pass) {
     case 0:  // A_x
       return dispatch_var(V, [&](auto VC) -> cudaError_t {
@@ -659,22 +664,49 @@ int passc_blocks(long long n) {
   return (int)(b < 152 * 8 ? b : 152 * 8);
 }
 
-template <bool PROX, bool MACE>
+// Each thread walks the L looks of one voxel at a time.  The look loops are software-
+// pipelined: look l + 1's loads are issued before look l's arithmetic and stores (the
+// arrays do not alias), so two looks' loads are in flight per thread.
+template <bool PROX, bool MACE, bool EXACT = false>
 __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
   const long long n = g.n;
   const int L = g.L;
+  const float* __restrict__ Wi = c.w;
+  float* __restrict__ Wo = c.w;
+  const float* __restrict__ Ri = c.r;
+  float* __restrict__ Ro = c.r;
+  const float2* __restrict__ MUi = c.mu;
+  float2* __restrict__ MUo = c.mu;
+  const float2* __restrict__ Di = c.d;
   float acc[2] = {0.f, 0.f};
   for (long long v = (long long)blockIdx.x * NT + threadIdx.x; v < n; v += (long long)gridDim.x * NT) {
     CSum wbar_old, xbar;
     bool bad = false;
+    float wl_n = Wi[v], rp_n = 0.f;
+    float2 m_n = make_float2(0.f, 0.f), d_n = m_n;
+    if constexpr (PROX) {
+      rp_n = Ri[v];
+      m_n = MUi[v];
+      d_n = Di[v];
+    } else {
+      rp_n = Ri[v];
+    }
     for (int l = 0; l < L; ++l) {
       const long long i = (long long)l * n + v;
-      const float wl = c.w[i];
+      const float wl = wl_n, rp = rp_n;
+      const float2 m0 = m_n, dd = d_n;
+      if (l + 1 < L) {
+        const long long in = i + n;
+        wl_n = Wi[in];
+        rp_n = Ri[in];
+        if constexpr (PROX) {
+          m_n = MUi[in];
+          d_n = Di[in];
+        }
+      }
       float rn;
       if constexpr (PROX) {
-        const float rp = c.r[i];
-        float2 m = c.mu[i];
-        const float2 dd = c.d[i];
+        float2 m = m0;
         if (c.closed_mu) {  // no-aperture ablation: d holds F^H y
           const float f = 1.0f / (1.0f + c.nv / (rp + c.nv));
           m = make_float2(dd.x * f, dd.y * f);
@@ -683,15 +715,15 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
           m.x = fmaf(gm, dd.x, m.x);
           m.y = fmaf(gm, dd.y, m.y);
         }
-        c.mu[i] = m;
+        MUo[i] = m;
         const float cc = c.nv * rp / fmaf(c.alpha, rp, c.nv);
         const float K = cc + cabs2(m);
-        rn = c.exact_prox ? (float)prox_exact((double)wl, (double)K, (double)c.prox_var)
-                          : prox_quad(wl, rp, K, c.prox_var, c.beta);
-        c.r[i] = rn;
+        if constexpr (EXACT) rn = (float)prox_exact((double)wl, (double)K, (double)c.prox_var);
+        else rn = prox_quad(wl, rp, K, c.prox_var, c.beta);
+        Ro[i] = rn;
         bad |= !isfinite(rn);
       } else {
-        rn = c.r[i];
+        rn = rp;
       }
       if constexpr (MACE) {
         wbar_old.add(c.ups_look * wl);
@@ -700,19 +732,25 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
     }
     if constexpr (MACE) {
       const long long ip = (long long)L * n + v;
-      const float rpr = c.r[ip], wpr = c.w[ip];
+      const float rpr = Ri[ip], wpr = Wi[ip];
       wbar_old.add(c.ups_prior * wpr);
       xbar.add(c.ups_prior * (2.0f * rpr - wpr));
       const float wb = wbar_old.get(), xb = xbar.get();
       float num = 0.f;
       CSum wbar_new;
+      // r and w of this voxel were just touched: these reads are L2 hits
+      float rj_n = Ri[v], wj_n = Wi[v];
       for (int j = 0; j <= L; ++j) {
         const long long i = (long long)j * n + v;
-        const float rj = c.r[i], wj = c.w[i];
+        const float rj = rj_n, wj = wj_n;
+        if (j < L) {
+          rj_n = Ri[i + n];
+          wj_n = Wi[i + n];
+        }
         const float dv = rj - wb;
         num = fmaf(dv, dv, num);
         const float wn = fmaf(2.0f * c.rho, xb - rj, wj);
-        c.w[i] = wn;
+        Wo[i] = wn;
         wbar_new.add((j < L ? c.ups_look : c.ups_prior) * wn);
         bad |= !isfinite(wn);
       }
@@ -729,11 +767,13 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
 }
 
 cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st) {
-  k_pass_c<true, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  if (c.exact_prox) k_pass_c<true, true, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  else k_pass_c<true, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
   return cudaGetLastError();
 }
 cudaError_t launch_prox_only(const Geom& g, const PassC& c, cudaStream_t st) {
-  k_pass_c<true, false><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  if (c.exact_prox) k_pass_c<true, false, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  else k_pass_c<true, false><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
   return cudaGetLastError();
 }
 cudaError_t launch_mace_only(const Geom& g, const PassC& c, cudaStream_t st) {

@@ -13,12 +13,17 @@ __host__ __device__ constexpr int rows_per_cta(int N) { return N <= 32 ? 64 : (N
 
 // Launch variants of the forward-agent FFT passes, chosen per pass by the autotuner:
 // 0 = default radix plan and tile, 1 = alternative radix plan (PlanB), 2 = other tile
-// schedule (half the rows per CTA in x passes, 32 columns per CTA in y / z passes).
-constexpr int kVariants = 3;
+// schedule (half the rows per CTA in x passes, 32 columns per CTA in y / z passes),
+// 3 = persistent CTAs with a two-stage cp.async pipeline (half the rows per tile in x
+// passes, pipe_cols(N) columns in y / z passes).
+constexpr int kVariants = 4;
 __host__ __device__ constexpr int variant_rows(int N, int V) {
-  return V == 2 ? (rows_per_cta(N) / 2 < 8 ? 8 : rows_per_cta(N) / 2) : rows_per_cta(N);
+  return (V == 2 || V == 3) ? (rows_per_cta(N) / 2 < 8 ? 8 : rows_per_cta(N) / 2) : rows_per_cta(N);
 }
 __host__ __device__ constexpr int variant_cols(int V) { return V == 2 ? 32 : LC; }
+// Columns per tile of the pipelined y / z passes (length-N transforms): two tile buffers
+// must fit shared memory at least once per SM.
+__host__ __device__ constexpr int pipe_cols(int N) { return N > 128 ? 8 : 16; }
 // Passes of the forward agent: A_x, A_y, fused z, B_y, B_x.
 struct AgentVariants {
   int v[5] = {0, 0, 0, 0, 0};
@@ -56,6 +61,11 @@ cudaError_t upload_twiddles();
 cudaError_t launch_agent_fft(const Geom& g, const AgentScalars& s, const float2* mu, const float* rprev,
                              const float2* y, const float* pupil, const float* window, float4* T,
                              float2* U, Partials& p, const AgentVariants& var, cudaStream_t st);
+// Variant 3 of pass `pass` (persistent, cp.async-pipelined); tw: the length-N twiddle
+// table of that pass's axis.
+cudaError_t launch_pipe_pass(int pass, const Geom& g, const AgentScalars& s, const float2* mu, const float* rprev,
+                             const float2* y, const float* pupil, const float* window, float4* T, float2* U,
+                             Partials& p, const float2* tw, cudaStream_t st);
 // One forward-agent pass alone (for timing variants): pass in 0..4.
 cudaError_t launch_agent_pass(int pass, int V, const Geom& g, const AgentScalars& s, const float2* mu,
                               const float* rprev, const float2* y, const float* pupil, const float* window,

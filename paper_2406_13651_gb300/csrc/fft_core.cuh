@@ -68,6 +68,25 @@ __device__ __forceinline__ void bitrev_permute(float2 (&v)[R], std::integer_sequ
   ((v[I] = t[I]), ...);
 }
 
+// Radix-2 decimation-in-time butterfly levels LEN, 2 LEN, ..., R on bit-reversed input.
+// Compile-time recursion over the level keeps every index constant, so the array stays
+// in registers.
+template <int R, bool INV, int LEN>
+__device__ __forceinline__ void dit_stages(float2 (&v)[R]) {
+  if constexpr (LEN <= R) {
+#pragma unroll
+    for (int i = 0; i < R / LEN; ++i) {
+#pragma unroll
+      for (int k = 0; k < LEN / 2; ++k) {
+        const float2 t = w16mul<INV>(v[i * LEN + k + LEN / 2], k * (16 / LEN));
+        v[i * LEN + k + LEN / 2] = csub(v[i * LEN + k], t);
+        v[i * LEN + k] = cadd(v[i * LEN + k], t);
+      }
+    }
+    dit_stages<R, INV, 2 * LEN>(v);
+  }
+}
+
 // In-place R-point DFT in registers, natural order in and out.
 // Forward: V[s] = sum_r v[r] exp(-2 pi i r s / R); inverse uses +.
 template <int R, bool INV>
@@ -87,18 +106,7 @@ __device__ __forceinline__ void dft(float2 (&v)[R]) {
   } else {
     static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
     bitrev_permute(v, std::make_integer_sequence<int, R>{});
-#pragma unroll
-    for (int len = 2; len <= R; len <<= 1) {
-#pragma unroll
-      for (int i = 0; i < R; i += len) {
-#pragma unroll
-        for (int k = 0; k < len / 2; ++k) {
-          float2 t = w16mul<INV>(v[i + k + len / 2], k * (16 / len));
-          v[i + k + len / 2] = csub(v[i + k], t);
-          v[i + k] = cadd(v[i + k], t);
-        }
-      }
-    }
+    dit_stages<R, INV, 2>(v);
   }
 }
 

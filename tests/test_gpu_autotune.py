@@ -41,7 +41,7 @@ def _case(nx, ny, nz, L, seed):
 
 
 @pytest.mark.parametrize("shape", [(32, 32, 16, 3), (96, 64, 32, 2), (256, 16, 16, 2)])
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_every_variant_matches_oracle(C, shape, variant):
     nx, ny, nz, L = shape
     wl, y32, st, mu_ref, r_ref = _case(nx, ny, nz, L, seed=nx + variant)
@@ -68,6 +68,6 @@ def test_autotune_picks_valid_variants(C):
     try:
         v = C.autotune(p, torch.from_numpy(y32).to(dev), torch.from_numpy(wl.pupil).to(dev),
                        torch.from_numpy(wl.window).to(dev))
-        assert len(v) == 5 and all(x in (0, 1, 2) for x in v)
+        assert len(v) == 5 and all(x in (0, 1, 2, 3) for x in v)
     finally:
         C.autotune_set(p, [0] * 5)
