@@ -173,7 +173,7 @@ clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser** out);
  * biases_host: all layers' [c_out] concatenated.  dtype: CLAMP_DENOISER_FP32 or _BF16.
  * BF16: weights and every layer's input are rounded to bfloat16, products accumulate in
  * FP32 on the tensor cores; needs channels in {16, 32, 48, 64} and volumes with
- * nx % 128 == 0, ny % 4 == 0, nz % 2 == 0 (else CLAMP_EUNSUPPORTED at use).
+ * nx % 128 == 0, ny % 2 == 0, nz % 2 == 0 (else CLAMP_EUNSUPPORTED at use).
  * FP32: on the tensor cores through a TF32x3 split when channels are in {16, 32, 48} and
  * nx % 128 == 0, ny % 2 == 0, nz % 2 == 0; otherwise on FP32 CUDA cores. */
 clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channels, int32_t dtype,

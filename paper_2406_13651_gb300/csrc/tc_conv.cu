@@ -5,9 +5,17 @@
 // such tiles.  For each chunk of input channels it stages the zero-padded input halo
 // (130 x (TY+2) x (TZ+2) voxels, channels-last in 16-byte channel groups) and the
 // chunk's weights in shared memory in the no-swizzle K-major core-matrix layout; a tap
-// is then only an offset of the A descriptor's start address.  One thread issues the
-// chunk's MMAs into FP32 accumulators in TMEM and commits them to an mbarrier (a
-// warp-wide elected issue measured slower here); the
+// is then only an offset of the A descriptor's start address.
+//
+// Tiles of one z-row that read the same shifted halo window (tile ty with tap dy reads
+// halo row ty + dy) share one MMA: the weights are packed per (dz, dx) as three
+// consecutive dy blocks in the order dy = 2, 1, 0, so the taps of tiles ty_lo..ty_hi for
+// halo row hy (dy = hy - ty) form one contiguous N range, and those tiles' accumulators
+// are adjacent TMEM columns.  One MMA with N = (tiles) x C_out replaces one per tile,
+// which halves the A-operand reads for the inner rows.  At the first chunk every
+// accumulator is cleared by one MMA against a zero weight block, so every later MMA
+// accumulates.  One thread issues the chunk's MMAs into FP32 accumulators in TMEM and
+// commits them to an mbarrier (a warp-wide elected issue measured slower here); the
 // epilogue reads TMEM (tcgen05.ld), adds the bias, applies ReLU and writes the next
 // layer's activations, or (last layer) FP32 plus the residual input.
 //
@@ -48,7 +56,11 @@ template <>
 struct TcKind<TC_BF16> {
   static constexpr int EPV = 8;      // channels per 16-byte group
   static constexpr int SPLIT = 1;    // operand copies (hi only)
-  static constexpr int TY = 4, TZ = 2;
+  // 2 x 2 rows per CTA: about 107 KB of shared memory and at most 256 TMEM columns at
+  // 48 channels, so two CTAs share an SM and one stages its next chunk while the
+  // other's MMAs run.
+  static constexpr int TY = 2, TZ = 2;
+  static constexpr int MIN_CTAS = 2;
   __host__ __device__ static constexpr uint32_t idesc(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
   }
@@ -58,6 +70,7 @@ struct TcKind<TC_TF32X3> {
   static constexpr int EPV = 4;
   static constexpr int SPLIT = 2;    // hi and lo copies
   static constexpr int TY = 2, TZ = 2;
+  static constexpr int MIN_CTAS = 1;
   __host__ __device__ static constexpr uint32_t idesc(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
   }
@@ -83,10 +96,11 @@ struct TcCfg {
   static constexpr int CH = 2 * K::EPV;               // input channels per chunk (one MMA K step)
   static constexpr int CHUNKS = CIN / CH;
   static constexpr int HALO_VEC = 2 * HZ * HY * TC_HX;  // 16-byte vectors per chunk, per split
-  static constexpr int W_VEC = 27 * 2 * NPAD;
+  static constexpr int W_VEC = 27 * 2 * NPAD;          // [dz][dx][2][dy = 2, 1, 0][NPAD]
+  static constexpr int ZB_VEC = 2 * NPAD;              // zero weight block (accumulator clear)
   static constexpr int TMEM_COLS = pow2_cols(MT * NPAD);
-  static constexpr size_t SMEM = 1024 + 16 * (size_t)K::SPLIT * (HALO_VEC + W_VEC) + 64;
-  static_assert(CIN % CH == 0 && NPAD % 16 == 0 && MT * NPAD <= 512, "tile");
+  static constexpr size_t SMEM = 1024 + 16 * ((size_t)K::SPLIT * (HALO_VEC + W_VEC) + ZB_VEC) + 64;
+  static_assert(CIN % CH == 0 && NPAD % 16 == 0 && MT * NPAD <= 512 && TY * NPAD <= 256, "tile");
   static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -113,7 +127,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 
 template <int KIND, int CIN, int NPAD, bool LAST>
-__global__ void __launch_bounds__(TC_NT, 1)
+__global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
     k_conv3_tc(const uint4* __restrict__ in, const uint4* __restrict__ wpk, const float* __restrict__ bias,
                uint4* __restrict__ out_act, float* __restrict__ out_f32, const float* __restrict__ resid, int nx,
                int ny, int nz, int* err) {
@@ -123,8 +137,9 @@ __global__ void __launch_bounds__(TC_NT, 1)
   extern __shared__ unsigned char tc_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   uint4* s_halo = reinterpret_cast<uint4*>(base);              // [SPLIT][2][HZ][HY][HX]
-  uint4* s_w = s_halo + Kd::SPLIT * Cfg::HALO_VEC;             // [SPLIT][27][2][NPAD]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_w + Kd::SPLIT * Cfg::W_VEC);
+  uint4* s_w = s_halo + Kd::SPLIT * Cfg::HALO_VEC;             // [SPLIT][3 dz][3 dx][2][3 dy][NPAD]
+  uint4* s_zero = s_w + Kd::SPLIT * Cfg::W_VEC;                 // [2][NPAD] zeros
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_zero + Cfg::ZB_VEC);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
@@ -136,6 +151,7 @@ __global__ void __launch_bounds__(TC_NT, 1)
     tc::mbar_init(mbar, 1);
     *abort_flag = 0;
   }
+  for (int e = tid; e < Cfg::ZB_VEC; e += TC_NT) s_zero[e] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) {
     tc::tmem_alloc(tslot, Cfg::TMEM_COLS);
     tc::tmem_relinquish();
@@ -144,10 +160,9 @@ __global__ void __launch_bounds__(TC_NT, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
-  const uint32_t idesc = Kd::idesc(128, NPAD);
-  const uint32_t halo_s = tc::smem_addr(s_halo), w_s = tc::smem_addr(s_w);
+  const uint32_t halo_s = tc::smem_addr(s_halo), w_s = tc::smem_addr(s_w), z_s = tc::smem_addr(s_zero);
   constexpr uint32_t LBO_A = HZ * HY * TC_HX * 16;  // channel group 0 -> 1
-  constexpr uint32_t LBO_B = NPAD * 16;
+  constexpr uint32_t LBO_B = 3 * NPAD * 16;         // channel group 0 -> 1 within a (dz, dx) block
   constexpr uint32_t SPLIT_A = 16u * Cfg::HALO_VEC, SPLIT_B = 16u * Cfg::W_VEC;  // hi -> lo copies
   bool aborted = false;
   uint32_t fail_parity = 0;
@@ -188,26 +203,39 @@ __global__ void __launch_bounds__(TC_NT, 1)
     if (tid == 0) {
       tc::fence_after_sync();
       // Descriptors differ only in the start-address field (bits 0-13, 16-byte units), so
-      // each MMA adds a compile-time tap / tile offset to a base descriptor.  Consecutive
-      // MMAs write different accumulators.
+      // each MMA adds a compile-time offset to a base descriptor.
       const uint64_t a0 = tc::make_desc(halo_s, LBO_A, 128);
       const uint64_t b0 = tc::make_desc(w_s, LBO_B, 128);
-      const uint32_t first = c > 0 ? 1u : 0u;
+      if (c == 0) {  // clear every accumulator: D = A x 0
+        const uint64_t bz = tc::make_desc(z_s, NPAD * 16, 128);
 #pragma unroll
-      for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-        const uint64_t boff = (uint64_t)(tap * 2 * NPAD);
+        for (int mt = 0; mt < MT; ++mt)
+          mma_kind(KIND, tbase + (uint32_t)(mt * NPAD), a0, bz, Kd::idesc(128, NPAD), 0u);
+      }
 #pragma unroll
-        for (int sp = 0; sp < (KIND == TC_BF16 ? 1 : 3); ++sp) {
-          // TF32x3 terms: (a_lo, b_hi), (a_hi, b_lo), (a_hi, b_hi)
-          const uint64_t a_sp = (KIND == TC_BF16 || sp > 0) ? 0 : (uint64_t)(SPLIT_A >> 4);
-          const uint64_t b_sp = (KIND != TC_BF16 && sp == 1) ? (uint64_t)(SPLIT_B >> 4) : 0;
+      for (int dz = 0; dz < 3; ++dz) {
 #pragma unroll
-          for (int mt = 0; mt < MT; ++mt) {
-            const int ty = mt % TY, tz = mt / TY;
-            const uint64_t aoff = (uint64_t)(((tz + dz) * HY + (ty + dy)) * TC_HX + dx);
-            const uint32_t acc = (tap == 0 && sp == 0) ? first : 1u;
-            mma_kind(KIND, tbase + (uint32_t)(mt * NPAD), a0 + a_sp + aoff, b0 + b_sp + boff, idesc, acc);
+        for (int tz = 0; tz < Cfg::TZ; ++tz) {
+#pragma unroll
+          for (int hy = 0; hy < HY; ++hy) {
+            // tiles ty_lo..ty_hi of z-row tz read halo row hy with taps dy = hy - ty
+            const int ty_lo = hy - 2 > 0 ? hy - 2 : 0, ty_hi = hy < TY - 1 ? hy : TY - 1;
+            const int ntile = ty_hi - ty_lo + 1;
+            const uint32_t idesc = Kd::idesc(128, ntile * NPAD);
+            const uint32_t dcol = tbase + (uint32_t)((tz * TY + ty_lo) * NPAD);
+            const int dyp = 2 - (hy - ty_lo);   // block index of the first tile's tap (dy = hy - ty_lo)
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+              const uint64_t aoff = (uint64_t)(((tz + dz) * HY + hy) * TC_HX + dx);
+              const uint64_t boff = (uint64_t)((dz * 3 + dx) * 6 * NPAD + dyp * NPAD);
+#pragma unroll
+              for (int sp = 0; sp < (KIND == TC_BF16 ? 1 : 3); ++sp) {
+                // TF32x3 terms: (a_lo, b_hi), (a_hi, b_lo), (a_hi, b_hi)
+                const uint64_t a_sp = (KIND == TC_BF16 || sp > 0) ? 0 : (uint64_t)(SPLIT_A >> 4);
+                const uint64_t b_sp = (KIND != TC_BF16 && sp == 1) ? (uint64_t)(SPLIT_B >> 4) : 0;
+                mma_kind(KIND, dcol, a0 + a_sp + aoff, b0 + b_sp + boff, idesc, 1u);
+              }
+            }
           }
         }
       }
@@ -512,9 +540,10 @@ cudaError_t tc_denoise_apply(const clamp_denoiser* d, const float* in, float* ou
   }
 }
 
-// Packs layer weights W[cout][cin][27] (float) for the tensor-core kernels.
-// BF16: [cin/16][27][2][npad][8] BF16 (RNE).  TF32x3: hi copy then lo copy, each
-// [cin/8][27][2][npad][4] FP32.  Output channels >= cout are zero.
+// Packs layer weights W[cout][cin][27] (float, tap = 9 dz + 3 dy + dx) for the
+// tensor-core kernels: per chunk of input channels [dz][dx][2 channel groups]
+// [dy = 2, 1, 0][npad][epv].  BF16: BF16 (RNE), epv = 8.  TF32x3: hi copy then lo copy,
+// FP32, epv = 4.  Output channels >= cout are zero.
 std::vector<uint8_t> pack_tc_weights(const float* W, int cin, int cout, int npad, bool bf16) {
   const int epv = bf16 ? 8 : 4, ch = 2 * epv, chunks = cin / ch;
   const size_t per = (size_t)chunks * 27 * 2 * npad * epv;  // elements per copy
@@ -525,7 +554,9 @@ std::vector<uint8_t> pack_tc_weights(const float* W, int cin, int cout, int npad
         for (int co = 0; co < cout; ++co)
           for (int e = 0; e < epv; ++e) {
             const int ci = ch * c + epv * cg + e;
-            const size_t dst = ((((size_t)c * 27 + tap) * 2 + cg) * npad + co) * epv + e;
+            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+            const size_t blk = ((size_t)c * 9 + dz * 3 + dx) * 2 + cg;
+            const size_t dst = ((blk * 3 + (2 - dy)) * npad + co) * epv + e;
             const float w = W[((size_t)co * cin + ci) * 27 + tap];
             if (bf16) {
               reinterpret_cast<uint16_t*>(p.data())[dst] = bf16_bits(w);
