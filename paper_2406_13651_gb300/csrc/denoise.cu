@@ -317,15 +317,17 @@ extern "C" clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channe
     void *wd = nullptr, *bd = nullptr, *w16 = nullptr;
     bool ok = upload(&bd, bp, co * sizeof(float));
     const bool bf = dtype == CLAMP_DENOISER_BF16;
+    const bool last = i == layers - 1;
     if (!bf || i == 0) {
-      // float weights: every FP32 layer (SIMT fallback), and the first layer (SIMT) of both kinds
+      // float weights: every FP32 layer (CUDA-core paths, including the tensor path's last
+      // layer) and the first BF16 layer (BF16-rounded values)
       std::vector<float> wf(wp, wp + wn);
       if (bf)
         for (auto& v : wf) v = clamp::bf16_round_value(v);
       ok = ok && upload(&wd, wf.data(), wn * sizeof(float));
     }
     const int chunk = bf ? 16 : 8;
-    if (i > 0 && ci % chunk == 0) {
+    if (i > 0 && (!last || bf) && ci % chunk == 0) {   // layers on the tensor cores
       const std::vector<uint8_t> pk = clamp::pack_tc_weights(wp, ci, co, co == 1 ? 16 : co, bf);
       ok = ok && upload(&w16, pk.data(), pk.size());
     }

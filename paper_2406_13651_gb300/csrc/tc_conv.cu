@@ -258,33 +258,33 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
       const int gy = y0 + mt % TY, gz = z0 + mt / TY, gx = x0 + 32 * q + lane;
       const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
       const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * NPAD);
-      if constexpr (LAST) {
+      if constexpr (LAST) {   // one output channel (column 0): FP32 plus the residual input
         if (h == 0) {
           float v[8];
           tc::tmem_ld_x8(trow, v);
           out_f32[vox] = v[0] + __ldg(&bias[0]) + resid[vox];
         }
-      } else {
-        constexpr int HALF = NPAD / 2;
+        continue;
+      }
+      constexpr int HALF = NPAD / 2;
 #pragma unroll
-        for (int j = 0; j < HALF / 8; ++j) {
-          const int col = h * HALF + 8 * j;
-          float v[8];
-          tc::tmem_ld_x8(trow + (uint32_t)col, v);
+      for (int j = 0; j < HALF / 8; ++j) {
+        const int col = h * HALF + 8 * j;
+        float v[8];
+        tc::tmem_ld_x8(trow + (uint32_t)col, v);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
-          if constexpr (KIND == TC_BF16) {
-            uint4 o;
-            o.x = pack_bf16x2(v[0], v[1]);
-            o.y = pack_bf16x2(v[2], v[3]);
-            o.z = pack_bf16x2(v[4], v[5]);
-            o.w = pack_bf16x2(v[6], v[7]);
-            out_act[(long long)(col / 8) * n + vox] = o;
-          } else {
-            float4* o4 = reinterpret_cast<float4*>(out_act);
-            o4[(long long)(col / 4) * n + vox] = make_float4(v[0], v[1], v[2], v[3]);
-            o4[(long long)(col / 4 + 1) * n + vox] = make_float4(v[4], v[5], v[6], v[7]);
-          }
+        for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
+        if constexpr (KIND == TC_BF16) {
+          uint4 o;
+          o.x = pack_bf16x2(v[0], v[1]);
+          o.y = pack_bf16x2(v[2], v[3]);
+          o.z = pack_bf16x2(v[4], v[5]);
+          o.w = pack_bf16x2(v[6], v[7]);
+          out_act[(long long)(col / 8) * n + vox] = o;
+        } else {
+          float4* o4 = reinterpret_cast<float4*>(out_act);
+          o4[(long long)(col / 4) * n + vox] = make_float4(v[0], v[1], v[2], v[3]);
+          o4[(long long)(col / 4 + 1) * n + vox] = make_float4(v[4], v[5], v[6], v[7]);
         }
       }
     }
@@ -352,6 +352,70 @@ __global__ void __launch_bounds__(NT) k_conv_first(const float* __restrict__ in,
       for (int g = 0; g < C / 4; ++g)
         o4[(long long)g * n + v] = make_float4(acc[4 * g], acc[4 * g + 1], acc[4 * g + 2], acc[4 * g + 3]);
     }
+  }
+}
+
+// Last layer of the FP32 residual CNN (C -> 1) on FP32 CUDA cores, reading the tensor
+// path's [C/4][nz][ny][nx][4] activations: out = x + b + sum_{c, tap} W[c][tap] act_c(v + tap).
+// A TF32x3 tensor-core tile would pad the single output channel to 16 columns and stage
+// the same hi/lo halo as a hidden layer for 1/C of its useful work.  CTA tile: 64
+// x-voxels x 8 rows of one z plane, two x-voxels per thread; one 4-channel group of the
+// halo in shared memory at a time.
+constexpr int CL_X = 64, CL_Y = 8, CL_NT = 256;
+template <int C>
+__global__ void __launch_bounds__(CL_NT) k_conv_last(const float4* __restrict__ act, const float* __restrict__ w,
+                                                     const float* __restrict__ bias, const float* __restrict__ resid,
+                                                     float* __restrict__ out, int nx, int ny, int nz) {
+  constexpr int G = C / 4;
+  constexpr int HX = CL_X + 2, HY = CL_Y + 2, HV = 3 * HY * HX;
+  __shared__ float4 s_h[HV];
+  __shared__ float s_w[27 * C];   // [tap][c]
+  const int tid = threadIdx.x, tx = tid % (CL_X / 2), ty = tid / (CL_X / 2);
+  const int x0 = blockIdx.x * CL_X, y0 = blockIdx.y * CL_Y, z = blockIdx.z;
+  const long long plane = (long long)nx * ny, n = plane * nz;
+  for (int e = tid; e < 27 * C; e += CL_NT) {
+    const int c = e % C, tap = e / C;
+    s_w[e] = w[c * 27 + tap];
+  }
+  float acc[2] = {0.f, 0.f};
+  for (int g = 0; g < G; ++g) {
+    __syncthreads();
+    for (int e = tid; e < HV; e += CL_NT) {
+      const int xr = e % HX, yr = (e / HX) % HY, zr = e / (HX * HY);
+      const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z + zr - 1;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+        v = act[(long long)g * n + (long long)gz * plane + (long long)gy * nx + gx];
+      s_h[e] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz) {
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+        const float4* row = s_h + (dz * HY + ty + dy) * HX + 2 * tx;
+        float4 f[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) f[q] = row[q];
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const float* wp = s_w + (dz * 9 + dy * 3 + dx) * C + 4 * g;
+          acc[0] = fmaf(wp[0], f[dx].x, fmaf(wp[1], f[dx].y, fmaf(wp[2], f[dx].z, fmaf(wp[3], f[dx].w, acc[0]))));
+          acc[1] = fmaf(wp[0], f[dx + 1].x,
+                        fmaf(wp[1], f[dx + 1].y, fmaf(wp[2], f[dx + 1].z, fmaf(wp[3], f[dx + 1].w, acc[1]))));
+        }
+      }
+    }
+  }
+  const int gy = y0 + ty;
+  if (gy >= ny) return;
+  const float b = __ldg(&bias[0]);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const int gx = x0 + 2 * tx + j;
+    if (gx >= nx) continue;
+    const long long vox = (long long)z * plane + (long long)gy * nx + gx;
+    out[vox] = acc[j] + b + resid[vox];
   }
 }
 
@@ -495,7 +559,16 @@ static cudaError_t apply_tc_c(const clamp_denoiser* d, const float* in, float* o
   for (int i = 1; i < d->layers; ++i) {
     const uint4* wp = static_cast<const uint4*>(d->w16[i]);
     if (i == d->layers - 1) {
-      e = run_tc<KIND, C, 16, true>(cur, wp, d->b[i], nullptr, out, in, nx, ny, nz, err, st);
+      if constexpr (KIND == TC_BF16) {
+        // BF16: the padded MMA tile is cheaper than unpacking BF16 on the CUDA cores
+        e = run_tc<KIND, C, 16, true>(cur, wp, d->b[i], nullptr, out, in, nx, ny, nz, err, st);
+      } else {
+        // TF32x3: the padded tile costs as much as a hidden layer; CUDA cores instead
+        dim3 grid((nx + CL_X - 1) / CL_X, (ny + CL_Y - 1) / CL_Y, nz);
+        k_conv_last<C><<<grid, CL_NT, 0, st>>>(reinterpret_cast<const float4*>(cur), d->w[i], d->b[i], in, out,
+                                               nx, ny, nz);
+        e = cudaGetLastError();
+      }
     } else {
       uint4* dst = cur == A ? B : A;
       e = run_tc<KIND, C, C, false>(cur, wp, d->b[i], dst, nullptr, nullptr, nx, ny, nz, err, st);
