@@ -43,6 +43,13 @@ def parse():
     ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "batch", "warm"])
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the warm-start comparison (256x256x128, L=32) on the default line")
+    ap.add_argument("--probe", choices=["prior", "agent"], default=None,
+                    help="profiling driver: run only the prior agent (CNN, --probe-shape / --probe-dtype) or "
+                         "only the forward agents + MACE step of --workload, --steps times")
+    ap.add_argument("--probe-shape", default="128,128,64", help="nx,ny,nz of the prior probe")
+    ap.add_argument("--probe-dtype", choices=["fp32", "bf16"], default="fp32",
+                    help="prior probe: fp32 = CNN 5 x 32 (TF32x3), bf16 = CNN 8 x 48")
+    ap.add_argument("--probe-variants", default="2,0,2,3,1", help="agent probe: FFT launch variants per pass")
     ap.add_argument("--batch-iters", type=int, default=10)
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -332,6 +339,64 @@ def warm_start_leg(dev) -> dict:
     return Wm.warm_workload_report(dev)
 
 
+def run_probe(args, local):
+    """Profiling drivers (one GPU, no timing contract): the prior agent alone on a seeded
+    random volume, or forward_prox + mace_step on a workload's geometry with fixed FFT
+    launch variants; prints the mean time per repetition."""
+    import numpy as np
+    import torch
+    from paper_2406_13651_gb300 import build as B
+    from paper_2406_13651_gb300 import clamp as C
+    from paper_2406_13651_gb300 import inputs as I
+    torch.cuda.set_device(local)
+    B.build()
+    dev = torch.device("cuda", local)
+    reps = max(1, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.probe == "prior":
+        nx, ny, nz = (int(v) for v in args.probe_shape.split(","))
+        layers, ch = (8, 48) if args.probe_dtype == "bf16" else (5, 32)
+        ws_, bs_ = I.cnn_weights(layers, ch, seed=1)
+        den = C.Denoiser.cnn(ws_, bs_, args.probe_dtype)
+        x = torch.rand((nz, ny, nx), generator=torch.Generator(device=dev).manual_seed(3), device=dev)
+        out = torch.empty_like(x)
+        wsb = C._ws(den.workspace_size(nx, ny, nz))
+        C.denoise(den, x, out, ws=wsb)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            C.denoise(den, x, out, ws=wsb)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        macs = 27 * (ch + (layers - 2) * ch * ch + ch)
+        print(json.dumps({"probe": "prior", "shape": [nx, ny, nz], "dtype": args.probe_dtype, "ms": ms,
+                          "tflops": 2 * macs * nx * ny * nz / ms / 1e9}), flush=True)
+        return 0
+    wl = I.make_workload(args.workload, seed=1, with_draws=False)
+    L = wl.looks
+    p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var)
+    pu, wi = torch.from_numpy(wl.pupil).to(dev), torch.from_numpy(wl.window).to(dev)
+    g = torch.Generator(device=dev).manual_seed(5)
+    shape = (L, wl.nz, wl.ny, wl.nx)
+    y = torch.complex(torch.randn(shape, generator=g, device=dev), torch.randn(shape, generator=g, device=dev))
+    mu, r, w = C.init(p, y, pu, wi)
+    wbar = torch.empty((wl.nz, wl.ny, wl.nx), device=dev)
+    ws = C.workspace(p)
+    variants = [int(v) for v in args.probe_variants.split(",")]
+    C.autotune_set(p, variants)
+    torch.cuda.synchronize()
+    e0.record()
+    for k in range(reps):
+        C.forward_prox(p, k + 2, y, pu, wi, mu, r, w, ws=ws)
+        C.mace_step(p, r, w, wbar, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": "agent", "workload": args.workload, "variants": variants,
+                      "ms": e0.elapsed_time(e1) / reps}), flush=True)
+    return 0
+
+
 def run_warm(args, rank, world, local):
     """The warm-start comparison alone: value = wall seconds to CE residual 1e-3 with the
     learned warm start (lower is better); the plain-init time is alongside."""
@@ -368,6 +433,8 @@ def main():
         return run_batch(args, rank, world, local)
     if args.workload == "warm":
         return run_warm(args, rank, world, local)
+    if args.probe:
+        return run_probe(args, local)
 
     import numpy as np
     import torch

@@ -285,6 +285,20 @@ void clamp_batch_destroy(clamp_batch* b);
 clamp_status clamp_speckle_average(const clamp_params* p, const float* y, const float* pupil, const float* window,
                                    float* r0, void* ws, size_t ws_bytes, void* stream);
 
+/* ---- Point-cloud metrics of a reconstruction (Sec. IV-B, Eqs. pc-distance, nrmse).
+ * P = voxels of r_hat above `threshold` (the paper's noise floor sigma_w^2 / alpha), Q =
+ * voxels of r_true above 0, with voxel-grid coordinates.  Each p in P is matched to its
+ * nearest q in Q (Euclidean, in voxels; ties to the smallest linear index); points with
+ * no q within max_dist (the paper: 3 x the Rayleigh resolution) are removed.
+ * out (host double[6]): mean distance of the kept points, false-positive rate (removed /
+ * |P|), NRMSE(beta* r_hat, r) over the kept points, kept count, removed count, beta* =
+ * sum r_hat r_q / sum r_hat^2.  r_hat, r_true: device float [nz][ny][nx]; max_dist in
+ * [0, 64]; ws: clamp_point_cloud_workspace_size() bytes.  Synchronises `stream`. */
+size_t clamp_point_cloud_workspace_size(void);
+clamp_status clamp_point_cloud_metrics(const float* r_hat, const float* r_true, int32_t nx, int32_t ny, int32_t nz,
+                                       float threshold, float max_dist, double* out, void* ws, size_t ws_bytes,
+                                       void* stream);
+
 /* ---- Learned warm start: a 3-level 3D U-Net mapping the speckle-averaged image to an
  * initial reflectance, trained on the GPU with these kernels.
  *

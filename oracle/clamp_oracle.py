@@ -443,3 +443,46 @@ def psnr(r_hat: np.ndarray, r: np.ndarray) -> float:
     (Eq. psnr)."""
     beta = float(np.vdot(r_hat, r) / np.vdot(r_hat, r_hat))
     return 10.0 * math.log10(r.size / float(np.sum((beta * r_hat - r) ** 2)))
+
+
+# ---------------------------------------------------------------------- point-cloud metrics
+
+def point_cloud_metrics(r_hat: np.ndarray, r_true: np.ndarray, threshold: float, max_dist: float) -> dict:
+    """Point-cloud metrics of Sec. IV-B (Eqs. pc-distance, nrmse).
+
+    P = voxels of r_hat above ``threshold``, Q = voxels of r_true above 0, with voxel
+    coordinates (x, y, z).  Each p is matched to its nearest q (Euclidean; ties to the
+    smallest linear index of q, a reading: the paper leaves ties open); p with no q within
+    ``max_dist`` is removed, and the false-positive rate is the removed fraction.  The mean
+    distance and NRMSE(beta* r_hat, r) = sqrt(sum (b r_hat_p - r_q)^2 / sum r_q^2) with
+    b = argmin (closed form sum r_hat r_q / sum r_hat^2) run over the kept points.
+    scipy's k-d tree gives the nearest distance; a ball query at that distance applies the
+    tie rule.
+    """
+    from scipy.spatial import cKDTree
+    nz, ny, nx = r_true.shape
+    qi = np.flatnonzero(r_true.ravel() > 0)
+    pi = np.flatnonzero(r_hat.ravel() > threshold)
+
+    def coords(idx):
+        return np.stack([idx % nx, (idx // nx) % ny, idx // (nx * ny)], axis=1).astype(np.float64)
+
+    if pi.size == 0 or qi.size == 0:
+        return dict(distance=0.0, false_positive_rate=1.0 if pi.size else 0.0, nrmse=0.0, kept=0,
+                    removed=int(pi.size), beta=0.0)
+    tree = cKDTree(coords(qi))
+    pc = coords(pi)
+    d, _ = tree.query(pc, k=1)
+    match = np.empty(pi.size, dtype=np.int64)
+    for j in range(pi.size):
+        cand = tree.query_ball_point(pc[j], d[j] + 1e-9)
+        cand = [c for c in cand if abs(np.linalg.norm(coords(qi[[c]])[0] - pc[j]) - d[j]) < 1e-9]
+        match[j] = qi[min(cand, key=lambda c: qi[c])]
+    keep = d <= max_dist
+    rh = r_hat.ravel()[pi[keep]].astype(np.float64)
+    rq = r_true.ravel()[match[keep]].astype(np.float64)
+    b = float(rh @ rq / (rh @ rh)) if rh.size else 0.0
+    nrmse = float(np.sqrt(np.sum((b * rh - rq) ** 2) / np.sum(rq * rq))) if rh.size else 0.0
+    return dict(distance=float(d[keep].mean()) if keep.any() else 0.0,
+                false_positive_rate=float((~keep).sum() / pi.size), nrmse=nrmse, kept=int(keep.sum()),
+                removed=int((~keep).sum()), beta=b)

@@ -40,6 +40,7 @@ EXPORTS = [
     "clamp_unet_create", "clamp_unet_destroy", "clamp_unet_param_count", "clamp_unet_get", "clamp_unet_set",
     "clamp_unet_workspace_size", "clamp_unet_forward", "clamp_unet_backward", "clamp_unet_adam",
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
+    "clamp_point_cloud_workspace_size", "clamp_point_cloud_metrics",
 ]
 
 
@@ -131,6 +132,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_unet_normalize": (I, [I, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]),
         "clamp_unet_warm_start": (I, [P, I, I, I, P, ctypes.c_float, P, P, S, P]),
         "clamp_unet_loss": (I, [P, P, P, I, I, I, I, P, P, S, P]),
+        "clamp_point_cloud_workspace_size": (S, []),
+        "clamp_point_cloud_metrics": (I, [P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -541,3 +544,15 @@ def unet_normalize(x, t=None, x_out=None, t_out=None, stream=None):
     _check(load().clamp_unet_normalize(B, n, cols, _ptr(x), _ptr(t), _ptr(x_out), _ptr(t_out), _stream(stream)),
            "clamp_unet_normalize")
     return x_out, t_out
+
+
+def point_cloud_metrics(r_hat, r_true, threshold: float, max_dist: float, stream=None) -> dict:
+    """Point-cloud metrics (Sec. IV-B) of device volumes r_hat, r_true [nz, ny, nx]."""
+    nz, ny, nx = r_hat.shape
+    out = np.zeros(6, np.float64)
+    ws = _ws(load().clamp_point_cloud_workspace_size())
+    _check(load().clamp_point_cloud_metrics(_ptr(r_hat), _ptr(r_true), nx, ny, nz, threshold, max_dist,
+                                            out.ctypes.data, _ptr(ws), ws.numel(), _stream(stream)),
+           "clamp_point_cloud_metrics")
+    return dict(distance=float(out[0]), false_positive_rate=float(out[1]), nrmse=float(out[2]), kept=int(out[3]),
+                removed=int(out[4]), beta=float(out[5]))

@@ -107,6 +107,16 @@ def hann_window(nz: int) -> np.ndarray:
     return (0.5 * (1.0 + np.cos(2.0 * math.pi * fz / nz))).astype(np.float32)
 
 
+def band_window(nz: int, q: float) -> np.ndarray:
+    """Range window of data zero-padded by ``q`` (Sec. II-B): the periodic Hann window of
+    the measured band of m = nz / q bins, centred on DC, embedded in the padded spectrum,
+    zero outside it.  q = 1 gives ``hann_window(nz)``."""
+    m = nz / q
+    fz = signed_freq(nz)
+    h = np.where(np.abs(fz) <= m / 2.0, 0.5 * (1.0 + np.cos(2.0 * math.pi * fz / m)), 0.0)
+    return h.astype(np.float32)
+
+
 def rect_window(nz: int) -> np.ndarray:
     """All-pass range window (binary aperture along range)."""
     return np.ones(nz, dtype=np.float32)
@@ -259,7 +269,7 @@ class Workload:
 
 
 def make_workload(name: str, seed: int = 1, *, nx=None, ny=None, nz=None, looks=None,
-                  iters=None, with_draws: bool = True) -> Workload:
+                  iters=None, with_draws: bool = True, q: float = 1.0) -> Workload:
     """Build one of the named synthetic workloads.
 
     ``tiny``      16x16x8, L=2, Gaussian denoiser (unit tests).
@@ -269,7 +279,10 @@ def make_workload(name: str, seed: int = 1, *, nx=None, ny=None, nz=None, looks=
     ``warm``      256x256x128, L=32, columns, R=0.4, 1.5 dB, Gaussian sigma 0.8 (warm-start comparison;
                   the SNR is relative to mean(r), so 1.5 dB at nz = 128 is the per-surface-voxel SNR
                   of 7.5 dB at nz = 32).
-    Size keywords override the shape (same generator and parameters).
+    Size keywords override the shape (same generator and parameters).  ``q`` > 1 is the
+    zero-padding factor (Sec. II-B, Sec. IV): the shape is the padded grid, the measured
+    band is 1/q of it in every dimension (pupil radius R / q of the padded Nyquist,
+    ``band_window(nz, q)``), and the scene lives on the padded (finer) grid.
     """
     presets = {
         "tiny": dict(nx=16, ny=16, nz=8, looks=2, radius=0.5, snr=10.0, scene="columns",
@@ -292,8 +305,8 @@ def make_workload(name: str, seed: int = 1, *, nx=None, ny=None, nz=None, looks=
         r = column_surface_scene(nx, ny, nz, seed)
     else:
         r = facet_scene(nx, ny, nz, seed)
-    pupil = circular_pupil(nx, ny, p["radius"])
-    window = hann_window(nz)
+    pupil = circular_pupil(nx, ny, p["radius"] / q)
+    window = band_window(nz, q)
     nv = noise_variance_for_snr(r, pupil, window, p["snr"])
     shape = (L, nz, ny, nx)
     if with_draws:

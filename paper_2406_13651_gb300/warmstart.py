@@ -194,12 +194,14 @@ def psnr(r_hat: np.ndarray, r_true: np.ndarray) -> float:
 
 
 def compare(net: C.UNet, p_plain: C.Params, y, pupil, window, den: C.Denoiser, tol: float = 1e-3,
-            max_iters: int = 300, ref_iters: int = 0, warm_k0: int = 0, r_true: np.ndarray | None = None):
+            max_iters: int = 300, ref_iters: int = 0, warm_k0: int = 0, r_true: np.ndarray | None = None,
+            pc_threshold: float | None = None, pc_max_dist: float | None = None):
     """Iterations and wall time to CE <= tol from the speckle-average init and from the warm
     start (which includes r0, the U-Net inference and the mapping), on the same data; both
     results' relative L2 distance to the plain solution run for ref_iters iterations
-    (2 x the plain count when 0) and, given r_true, their PSNR.  warm_k0 starts the warm
-    run's beta_k schedule at k = warm_k0 + 1 (App. A) instead of k = 1."""
+    (2 x the plain count when 0) and, given r_true, their PSNR and (with pc_threshold and
+    pc_max_dist) their point-cloud metrics (Sec. IV-B).  warm_k0 starts the warm run's
+    beta_k schedule at k = warm_k0 + 1 (App. A) instead of k = 1."""
     import torch
     p = C.make_params(p_plain.nx, p_plain.ny, p_plain.nz, p_plain.looks, p_plain.noise_var, p_plain.prox_var,
                       max_iters=max_iters, tol=tol, check_every=1)
@@ -231,11 +233,20 @@ def compare(net: C.UNet, p_plain: C.Params, y, pupil, window, den: C.Denoiser, t
     pr = C.make_params(p.nx, p.ny, p.nz, p.looks, p.noise_var, p.prox_var, max_iters=n_ref)
     ref = C.reconstruct(pr, y, pupil, window, den, ws=ws).r.cpu().numpy().astype(np.float64)
     nref = np.linalg.norm(ref)
+    rt_dev = None
+    if r_true is not None and pc_threshold is not None:
+        rt_dev = torch.from_numpy(np.ascontiguousarray(r_true, np.float32)).to(y.device)
     for name, r in (("plain", r_plain), ("warm", r_warm)):
         rh = r.cpu().numpy()
         out[name]["rel_err_vs_ref"] = float(np.linalg.norm(rh - ref) / nref)
         if r_true is not None:
             out[name]["psnr"] = psnr(rh, r_true)
+        if rt_dev is not None:
+            # points where the optimally scaled reconstruction b r_hat (the scale of the PSNR
+            # and NRMSE of Sec. IV-B) exceeds the noise floor
+            rhd, rtd = rh.astype(np.float64).ravel(), np.asarray(r_true, np.float64).ravel()
+            b = float(rhd @ rtd) / max(float(rhd @ rhd), 1e-300)
+            out[name]["point_cloud"] = C.point_cloud_metrics(r, rt_dev, pc_threshold / b, pc_max_dist)
     out["ref_iters"] = n_ref
     if r_true is not None:
         out["ref_psnr"] = psnr(ref, r_true)
@@ -258,7 +269,11 @@ def warm_workload_report(dev, seed: int = 1, weights: str = WEIGHTS, tol: float 
     spk, eta = device_draws((wl.looks, wl.nz, wl.ny, wl.nx), 1233 + seed, dev)
     y = C.simulate(p, torch.from_numpy(wl.r_true.astype(np.float32)).to(dev), spk, eta, pu, wi)
     del spk, eta
-    c = compare(net, p, y, pu, wi, den, tol=tol, max_iters=wl.iters, r_true=wl.r_true)
+    # point clouds (Sec. IV-B): threshold = noise floor sigma_w^2 / alpha, outliers beyond 3x
+    # the lateral Rayleigh distance 1.22 / R voxels (pupil radius R x Nyquist)
+    alpha = float(np.mean(wl.window.astype(np.float64) ** 2) * np.mean(wl.pupil.astype(np.float64) ** 2))
+    c = compare(net, p, y, pu, wi, den, tol=tol, max_iters=wl.iters, r_true=wl.r_true,
+                pc_threshold=wl.noise_var / alpha, pc_max_dist=3.0 * 1.22 / 0.4)
     c["tol"] = tol
     c["speedup_wall"] = c["plain"]["seconds"] / max(c["warm"]["seconds"], 1e-12)
     c["workload"] = ("256x256x128 complex64, L=32, column-surface scene, pupil R=0.4, Hann window, "

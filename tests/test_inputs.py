@@ -83,3 +83,32 @@ def test_chunked_draws_equal_full_draw():
     spk, eta = I.look_draws(wl, 2, 1)
     np.testing.assert_array_equal(spk, wl.speckle[1])
     np.testing.assert_array_equal(eta, wl.noise[1])
+
+
+def test_band_window_for_zero_padding():
+    """q = 1 is the plain Hann window; q > 1 keeps the measured band of nz / q bins (the
+    Hann window of that length, DC = 1) and is zero outside it."""
+    np.testing.assert_array_equal(I.band_window(32, 1.0), I.hann_window(32))
+    for nz, q in ((96, 1.5), (64, 2.0)):
+        h = I.band_window(nz, q)
+        m = int(round(nz / q))
+        f = I.signed_freq(nz)
+        assert h[0] == 1.0
+        assert np.all(h[np.abs(f) > m / 2] == 0.0)
+        inside = np.abs(f) < m / 2
+        np.testing.assert_allclose(h[inside], 0.5 * (1 + np.cos(2 * np.pi * f[inside] / m)), rtol=1e-6)
+        # the embedded band equals the un-padded Hann window of length m, bin for bin
+        hm = I.hann_window(m)
+        fm = I.signed_freq(m)
+        for k in range(m):
+            if abs(fm[k]) < m / 2:
+                j = int(fm[k]) % nz
+                assert abs(h[j] - hm[k]) < 1e-6
+
+
+def test_zero_padded_workload_shrinks_the_band():
+    w1 = I.make_workload("cfg1", seed=3, nx=64, ny=64, nz=32, looks=2, with_draws=False)
+    w2 = I.make_workload("cfg1", seed=3, nx=96, ny=96, nz=48, looks=2, with_draws=False, q=1.5)
+    frac = lambda w: float(np.count_nonzero(w.pupil)) / w.pupil.size   # noqa: E731
+    assert abs(frac(w2) / frac(w1) - 1 / 1.5 ** 2) < 0.05
+    assert np.count_nonzero(w2.window) < np.count_nonzero(w1.window) * 48 / 32

@@ -415,3 +415,58 @@ def test_exact_prox_reconstruction_runs_and_converges():
     r2, st2 = O.reconstruct(y, wl.pupil, wl.window, wl.denoiser, wl.noise_var, wl.prox_var, 25, no_aperture=True)
     assert np.all(np.isfinite(r1)) and np.all(np.isfinite(r2))
     assert st1.ce_hist[-1] < st1.ce_hist[0] and st2.ce_hist[-1] < st2.ce_hist[0]
+
+
+# ---------------------------------------------------------------------- point-cloud metrics (Sec. IV-B)
+
+def _brute_pc(r_hat, r_true, thr, max_dist):
+    """All-pairs nearest neighbour with the smallest-index tie rule (independent of the k-d tree)."""
+    nz, ny, nx = r_true.shape
+    P = [(i, np.array([i % nx, (i // nx) % ny, i // (nx * ny)], float)) for i in np.flatnonzero(r_hat.ravel() > thr)]
+    Q = [(i, np.array([i % nx, (i // nx) % ny, i // (nx * ny)], float)) for i in np.flatnonzero(r_true.ravel() > 0)]
+    kept_d, rh, rq, removed = [], [], [], 0
+    for ip, sp in P:
+        best = min(Q, key=lambda t: (np.sum((t[1] - sp) ** 2), t[0]))
+        d = float(np.sqrt(np.sum((best[1] - sp) ** 2)))
+        if d <= max_dist:
+            kept_d.append(d)
+            rh.append(r_hat.ravel()[ip])
+            rq.append(r_true.ravel()[best[0]])
+        else:
+            removed += 1
+    rh, rq = np.array(rh), np.array(rq)
+    b = rh @ rq / (rh @ rh)
+    return dict(distance=float(np.mean(kept_d)), false_positive_rate=removed / len(P),
+                nrmse=float(np.sqrt(np.sum((b * rh - rq) ** 2) / np.sum(rq ** 2))), kept=len(kept_d), removed=removed,
+                beta=float(b))
+
+
+def test_point_cloud_metrics_match_brute_force():
+    rng = np.random.default_rng(11)
+    r_true = np.where(rng.uniform(size=(6, 7, 8)) < 0.15, rng.uniform(0.2, 1.0, (6, 7, 8)), 0.0)
+    r_hat = np.where(rng.uniform(size=(6, 7, 8)) < 0.3, rng.uniform(0.0, 1.0, (6, 7, 8)), 0.0)
+    for thr, md in ((0.1, 2.5), (0.0, 1.0), (0.5, 10.0)):
+        got = O.point_cloud_metrics(r_hat, r_true, thr, md)
+        ref = _brute_pc(r_hat, r_true, thr, md)
+        assert got["kept"] == ref["kept"] and got["removed"] == ref["removed"]
+        for k in ("distance", "false_positive_rate", "nrmse", "beta"):
+            assert abs(got[k] - ref[k]) < 1e-12, (k, got[k], ref[k])
+
+
+def test_point_cloud_metrics_closed_forms():
+    rng = np.random.default_rng(12)
+    r = np.zeros((8, 8, 8))
+    pts = [(1, 2, 3), (4, 4, 1), (6, 1, 6)]
+    for (z, y, x) in pts:
+        r[z, y, x] = rng.uniform(0.3, 1.0)
+    m = O.point_cloud_metrics(r, r, 0.0, 3.0)            # identical clouds
+    assert m["distance"] == 0 and m["false_positive_rate"] == 0 and m["nrmse"] < 1e-15 and abs(m["beta"] - 1) < 1e-15
+    m = O.point_cloud_metrics(3.0 * r, r, 0.0, 3.0)      # scale is absorbed by beta*
+    assert m["nrmse"] < 1e-15 and abs(m["beta"] - 1 / 3) < 1e-15
+    shifted = np.roll(r, 1, axis=2)                       # every point one voxel off in x
+    m = O.point_cloud_metrics(shifted, r, 0.0, 3.0)
+    assert abs(m["distance"] - 1.0) < 1e-15 and m["nrmse"] < 1e-15
+    far = r.copy()
+    far[7, 7, 0] = 0.5                                    # an outlier 5+ voxels from every true point
+    m = O.point_cloud_metrics(far, r, 0.0, 2.0)
+    assert m["removed"] == 1 and abs(m["false_positive_rate"] - 0.25) < 1e-15
