@@ -45,7 +45,7 @@ def parse():
                     help="skip the warm-start comparison (256x256x128, L=32) on the default line")
     ap.add_argument("--probe", choices=["prior", "agent"], default=None,
                     help="profiling driver: run only the prior agent (CNN, --probe-shape / --probe-dtype) or "
-                         "only the forward agents + MACE step of --workload, --steps times")
+                         "--steps iterations of --workload with a Gaussian prior")
     ap.add_argument("--probe-shape", default="128,128,64", help="nx,ny,nz of the prior probe")
     ap.add_argument("--probe-dtype", choices=["fp32", "bf16"], default="fp32",
                     help="prior probe: fp32 = CNN 5 x 32 (TF32x3), bf16 = CNN 8 x 48")
@@ -341,8 +341,9 @@ def warm_start_leg(dev) -> dict:
 
 def run_probe(args, local):
     """Profiling drivers (one GPU, no timing contract): the prior agent alone on a seeded
-    random volume, or forward_prox + mace_step on a workload's geometry with fixed FFT
-    launch variants; prints the mean time per repetition."""
+    random volume, or whole iterations (forward agents, a Gaussian prior, the fused
+    prox/Mann pass) on a workload's geometry with fixed FFT launch variants; prints the
+    mean time per repetition."""
     import numpy as np
     import torch
     from paper_2406_13651_gb300 import build as B
@@ -382,14 +383,14 @@ def run_probe(args, local):
     y = torch.complex(torch.randn(shape, generator=g, device=dev), torch.randn(shape, generator=g, device=dev))
     mu, r, w = C.init(p, y, pu, wi)
     wbar = torch.empty((wl.nz, wl.ny, wl.nx), device=dev)
-    ws = C.workspace(p)
+    den = C.Denoiser.gauss(0.8)   # a cheap prior: the iteration's other kernels are the subject
+    ws = C.iterate_workspace(p, den)
     variants = [int(v) for v in args.probe_variants.split(",")]
     C.autotune_set(p, variants)
     torch.cuda.synchronize()
     e0.record()
     for k in range(reps):
-        C.forward_prox(p, k + 2, y, pu, wi, mu, r, w, ws=ws)
-        C.mace_step(p, r, w, wbar, ws=ws)
+        C.iterate(p, k + 1, 1, y, pu, wi, den, mu, r, w, wbar, ws=ws)
     e1.record()
     torch.cuda.synchronize()
     print(json.dumps({"probe": "agent", "workload": args.workload, "variants": variants,
