@@ -766,8 +766,98 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
   }
 }
 
+// Fused pass C on pairs of adjacent voxels: the same arithmetic as k_pass_c<true, true,
+// false> per voxel, with 16-byte loads of mu and d and 8-byte loads of r and w, so each
+// memory request carries two voxels (n even; the launcher checks the pointers'
+// alignment and otherwise uses the one-voxel kernel).
+__global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
+  const long long n2 = g.n / 2;
+  const int L = g.L;
+  const float2* __restrict__ Wi = reinterpret_cast<const float2*>(c.w);
+  float2* __restrict__ Wo = reinterpret_cast<float2*>(c.w);
+  const float2* __restrict__ Ri = reinterpret_cast<const float2*>(c.r);
+  float2* __restrict__ Ro = reinterpret_cast<float2*>(c.r);
+  const float4* __restrict__ MUi = reinterpret_cast<const float4*>(c.mu);
+  float4* __restrict__ MUo = reinterpret_cast<float4*>(c.mu);
+  const float4* __restrict__ Di = reinterpret_cast<const float4*>(c.d);
+  float acc[2] = {0.f, 0.f};
+  for (long long vp = (long long)blockIdx.x * NT + threadIdx.x; vp < n2; vp += (long long)gridDim.x * NT) {
+    CSum wb0, xb0, wb1, xb1;
+    bool bad = false;
+    float2 w_n = Wi[vp], r_n = Ri[vp];
+    float4 m_n = MUi[vp], d_n = Di[vp];
+    for (int l = 0; l < L; ++l) {
+      const long long i = (long long)l * n2 + vp;
+      const float2 wl = w_n, rp = r_n;
+      float4 m = m_n;
+      const float4 dd = d_n;
+      if (l + 1 < L) {
+        w_n = Wi[i + n2];
+        r_n = Ri[i + n2];
+        m_n = MUi[i + n2];
+        d_n = Di[i + n2];
+      }
+      if (c.closed_mu) {  // no-aperture ablation: d holds F^H y
+        const float f0 = 1.0f / (1.0f + c.nv / (rp.x + c.nv)), f1 = 1.0f / (1.0f + c.nv / (rp.y + c.nv));
+        m = make_float4(dd.x * f0, dd.y * f0, dd.z * f1, dd.w * f1);
+      } else {
+        const float gm = __ldg(&c.gamma[l]);
+        m = make_float4(fmaf(gm, dd.x, m.x), fmaf(gm, dd.y, m.y), fmaf(gm, dd.z, m.z), fmaf(gm, dd.w, m.w));
+      }
+      MUo[i] = m;
+      const float c0 = c.nv * rp.x / fmaf(c.alpha, rp.x, c.nv), c1 = c.nv * rp.y / fmaf(c.alpha, rp.y, c.nv);
+      const float K0 = c0 + fmaf(m.x, m.x, m.y * m.y), K1 = c1 + fmaf(m.z, m.z, m.w * m.w);
+      const float2 rn = make_float2(prox_quad(wl.x, rp.x, K0, c.prox_var, c.beta),
+                                    prox_quad(wl.y, rp.y, K1, c.prox_var, c.beta));
+      Ro[i] = rn;
+      bad |= !isfinite(rn.x) || !isfinite(rn.y);
+      wb0.add(c.ups_look * wl.x);
+      wb1.add(c.ups_look * wl.y);
+      xb0.add(c.ups_look * (2.0f * rn.x - wl.x));
+      xb1.add(c.ups_look * (2.0f * rn.y - wl.y));
+    }
+    const long long ip = (long long)L * n2 + vp;
+    const float2 rpr = Ri[ip], wpr = Wi[ip];
+    wb0.add(c.ups_prior * wpr.x);
+    wb1.add(c.ups_prior * wpr.y);
+    xb0.add(c.ups_prior * (2.0f * rpr.x - wpr.x));
+    xb1.add(c.ups_prior * (2.0f * rpr.y - wpr.y));
+    const float w0 = wb0.get(), w1 = wb1.get(), x0 = xb0.get(), x1 = xb1.get();
+    float num = 0.f;
+    CSum wn0, wn1;
+    float2 rj_n = Ri[vp], wj_n = Wi[vp];
+    for (int j = 0; j <= L; ++j) {
+      const long long i = (long long)j * n2 + vp;
+      const float2 rj = rj_n, wj = wj_n;
+      if (j < L) {
+        rj_n = Ri[i + n2];
+        wj_n = Wi[i + n2];
+      }
+      const float dv0 = rj.x - w0, dv1 = rj.y - w1;
+      num = fmaf(dv0, dv0, fmaf(dv1, dv1, num));
+      const float2 wn = make_float2(fmaf(2.0f * c.rho, x0 - rj.x, wj.x), fmaf(2.0f * c.rho, x1 - rj.y, wj.y));
+      Wo[i] = wn;
+      const float ups = j < L ? c.ups_look : c.ups_prior;
+      wn0.add(ups * wn.x);
+      wn1.add(ups * wn.y);
+      bad |= !isfinite(wn.x) || !isfinite(wn.y);
+    }
+    reinterpret_cast<float2*>(c.wbar)[vp] = make_float2(wn0.get(), wn1.get());
+    acc[0] += num;
+    acc[1] += (float)(L + 1) * (w0 * w0 + w1 * w1);
+    if (bad && c.err) atomicOr(c.err, 1);
+  }
+  double* const outs[2] = {c.part_num, c.part_den};
+  block_reduce_store<2>(acc, outs, blockIdx.x);
+}
+
+static bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
+
 cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st) {
+  const bool pair = g.n % 2 == 0 && aligned(c.w, 8) && aligned(c.r, 8) && aligned(c.wbar, 8) &&
+                    aligned(c.mu, 16) && aligned(c.d, 16);
   if (c.exact_prox) k_pass_c<true, true, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  else if (pair) k_pass_c_pair<<<passc_blocks(g.n), NT, 0, st>>>(g, c);
   else k_pass_c<true, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
   return cudaGetLastError();
 }
