@@ -359,6 +359,12 @@ clamp_status clamp_unet_normalize(int32_t batch, int64_t n, int64_t norm_count, 
  * least clamp_unet_workspace_size(u, 1, nx, ny, nz, 0) bytes. */
 clamp_status clamp_unet_warm_start(clamp_unet* u, int32_t nx, int32_t ny, int32_t nz, const float* r0,
                                    float floor_rel, float* r_init, void* ws, size_t ws_bytes, void* stream);
+/* The 3D U-Net prior agent (Sec. III-C): a denoiser H(w) = m max(U(w / m), floor_rel),
+ * m = sum(w) / (nx ny), U a clamp_unet trained as a denoiser.  The denoiser borrows `net`:
+ * the caller keeps it alive, unchanged, while the denoiser is in use, and destroys it
+ * after clamp_denoiser_destroy.  Volumes need nx, ny, nz multiples of 4 (else
+ * CLAMP_EUNSUPPORTED at use); workspace: clamp_unet_workspace_size(net, 1, nx, ny, nz, 0). */
+clamp_status clamp_denoiser_create_unet(clamp_unet* net, float floor_rel, clamp_denoiser** out);
 /* One Adam step (Kingma and Ba, 2015, with bias correction; t >= 1 is the step number)
  * on the parameters from the current gradients. */
 clamp_status clamp_unet_adam(clamp_unet* u, float lr, float beta1, float beta2, float eps, int32_t t,

@@ -276,7 +276,24 @@ def apply_prior(x: np.ndarray, den: dict) -> np.ndarray:
         return denoise_cnn(x, den["weights"], den["biases"], bf16=den.get("dtype") == "bf16")
     if den["kind"] == "identity":
         return np.asarray(x, dtype=np.float64).copy()
+    if den["kind"] == "unet":
+        return denoise_unet(x, den["params"], tuple(den["channels"]), den.get("dtype") == "bf16",
+                            den.get("floor", 1e-3))
     raise ValueError(den["kind"])
+
+
+def denoise_unet(x: np.ndarray, params, channels, bf16: bool, floor: float) -> np.ndarray:
+    """U-Net prior agent (Sec. III-C): m max(U(x / m), floor) with m = sum(x) / (nx ny), the
+    energy per (x, y) column (reading: the normalisation that makes one trained network
+    apply at any range extent); U is the U-Net of ``oracle.unet_oracle``."""
+    from . import unet_oracle
+    x = np.asarray(x, dtype=np.float64)
+    nz, ny, nx = x.shape
+    m = x.sum() / (nx * ny)
+    if not m > 0:
+        m = 1.0
+    u = unet_oracle.forward(np.asarray(params, np.float64), (x / m)[None], channels, bf16=bf16).numpy()[0]
+    return m * np.maximum(u, floor)
 
 
 # ---------------------------------------------------------------------- MACE

@@ -40,7 +40,7 @@ EXPORTS = [
     "clamp_unet_create", "clamp_unet_destroy", "clamp_unet_param_count", "clamp_unet_get", "clamp_unet_set",
     "clamp_unet_workspace_size", "clamp_unet_forward", "clamp_unet_backward", "clamp_unet_adam",
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
-    "clamp_point_cloud_workspace_size", "clamp_point_cloud_metrics",
+    "clamp_point_cloud_workspace_size", "clamp_point_cloud_metrics", "clamp_denoiser_create_unet",
 ]
 
 
@@ -133,6 +133,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_unet_warm_start": (I, [P, I, I, I, P, ctypes.c_float, P, P, S, P]),
         "clamp_unet_loss": (I, [P, P, P, I, I, I, I, P, P, S, P]),
         "clamp_point_cloud_workspace_size": (S, []),
+        "clamp_denoiser_create_unet": (I, [P, ctypes.c_float, ctypes.POINTER(P)]),
         "clamp_point_cloud_metrics": (I, [P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
@@ -195,9 +196,22 @@ class Denoiser:
         return cls(h.value, {"kind": "cnn", "layers": layers, "channels": channels, "dtype": dtype})
 
     @classmethod
+    def unet(cls, net: "UNet", floor: float = 1e-3) -> "Denoiser":
+        """The U-Net prior agent H(w) = m max(U(w / m), floor), m = sum(w) / (nx ny)."""
+        h = ctypes.c_void_p()
+        _check(load().clamp_denoiser_create_unet(net.handle, floor, ctypes.byref(h)), "clamp_denoiser_create_unet")
+        d = cls(h.value, {"kind": "unet", "params": net.get("params"), "channels": net.channels,
+                          "dtype": net.dtype, "floor": floor})
+        d._net = net   # the denoiser borrows the network: keep it alive as long as the denoiser
+        return d
+
+    @classmethod
     def from_desc(cls, desc: dict) -> "Denoiser":
         if desc["kind"] == "gauss":
             return cls.gauss(desc["sigma"])
+        if desc["kind"] == "unet":
+            net = UNet(*desc["channels"], params=desc["params"], dtype=desc.get("dtype", "bf16"))
+            return cls.unet(net, desc.get("floor", 1e-3))
         return cls.cnn(desc["weights"], desc["biases"], desc.get("dtype", "fp32"))
 
     def workspace_size(self, nx, ny, nz) -> int:
@@ -207,6 +221,7 @@ class Denoiser:
         if self.handle:
             load().clamp_denoiser_destroy(self.handle)
             self.handle = None
+        self._net = None
 
     def __del__(self):
         try:

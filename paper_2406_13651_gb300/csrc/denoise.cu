@@ -222,6 +222,7 @@ static cudaError_t run_conv_c1(const float* in, int cin, float* out, const float
 using namespace clamp;
 
 size_t denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz) {
+  if (d && d->kind == 2) return clamp_unet_workspace_size(d->unet, 1, nx, ny, nz, 0);
   if (!d || d->kind != 1) return 0;
   if (d->dtype == CLAMP_DENOISER_BF16) return tc_denoise_ws_bytes(d, nx, ny, nz);
   const size_t n = (size_t)nx * ny * nz;
@@ -229,6 +230,7 @@ size_t denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz) {
 }
 
 bool denoise_supports(const clamp_denoiser* d, int nx, int ny, int nz) {
+  if (d->kind == 2) return nx % 4 == 0 && ny % 4 == 0 && nz % 4 == 0;
   if (d->kind == 1 && d->dtype == CLAMP_DENOISER_BF16) return tc_denoiser_supports(d, nx, ny, nz);
   return true;
 }
@@ -237,6 +239,11 @@ cudaError_t denoise_apply(const clamp_denoiser* d, const float* in, float* out, 
                           int* err, cudaStream_t st) {
   if (d->kind == 0) {
     return launch_gauss3(nx, ny, nz, in, out, d->g0, d->g1, st);
+  }
+  if (d->kind == 2) {  // U-Net prior: the warm-start map m max(U(w / m), floor) on w
+    const clamp_status s = clamp_unet_warm_start(d->unet, nx, ny, nz, in, d->floor_rel, out, ws,
+                                                 denoise_ws_bytes(d, nx, ny, nz), st);
+    return s == CLAMP_OK ? cudaSuccess : cudaErrorInvalidValue;
   }
   // tensor-core path (BF16, or FP32 through TF32x3) when the volume fits its tiling
   if (tc_denoiser_supports(d, nx, ny, nz)) return tc_denoise_apply(d, in, out, nx, ny, nz, ws, err, st);
@@ -274,6 +281,17 @@ extern "C" clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser*
   const double e = exp(-1.0 / (2.0 * (double)sigma * sigma));
   d->g0 = (float)(e / (1.0 + 2.0 * e));
   d->g1 = (float)(1.0 / (1.0 + 2.0 * e));
+  cudaGetDevice(&d->dev);
+  *out = d;
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_denoiser_create_unet(clamp_unet* net, float floor_rel, clamp_denoiser** out) {
+  if (!out || !net || !(floor_rel >= 0.f) || !isfinite(floor_rel)) return CLAMP_EINVAL;
+  clamp_denoiser* d = new clamp_denoiser();
+  d->kind = 2;
+  d->unet = net;
+  d->floor_rel = floor_rel;
   cudaGetDevice(&d->dev);
   *out = d;
   return CLAMP_OK;

@@ -245,6 +245,16 @@ def warmstart_specs(count: int = 2000, seed: int = 11, nx: int = 64, ny: int = 6
                  seed=seed * 100000 + i, iters=iters) for i in range(count)]
 
 
+def prior_training_scenes(count: int, seed: int = 31, n: int = 32) -> np.ndarray:
+    """Clean n^3 volumes for training the U-Net prior agent: alternating column-surface and
+    facet scenes, each with its own seed.  float32 [count][n][n][n]."""
+    out = np.empty((count, n, n, n), np.float32)
+    for i in range(count):
+        sd = seed * 100000 + i
+        out[i] = column_surface_scene(n, n, n, sd) if i % 2 == 0 else facet_scene(n, n, n, sd)
+    return out
+
+
 # ----------------------------------------------------------------------------- workloads
 
 @dataclass
