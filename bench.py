@@ -176,6 +176,31 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------- reference arm
 
+# ---- multi-rank bookkeeping (replicas only: every rank runs its own seeded problem)
+
+def replica_seed(rank: int, base: int = 1) -> int:
+    """Seed of rank `rank`'s problem: independent replicas with fixed work per rank (weak
+    scaling); there is no data-path exchange between ranks."""
+    return base + rank
+
+
+def max_over_ranks(seconds: float, world: int, device) -> float:
+    """The job's time for a timed region: the slowest rank's (every rank must call it;
+    one rank returns its own)."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank_step: float, steps: int, world: int, t_max: float) -> float:
+    """Whole-job rate: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank_step * steps * world / t_max
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle on the host cores, rank 0 only.  Each step runs one
     work unit of a CLAMP iteration, round robin: one look's forward agent on the full
@@ -270,7 +295,7 @@ def run_batch(args, rank, world, local):
     B.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    specs = I.batch_specs(24, seed=7 + rank, iters=args.batch_iters)
+    specs = I.batch_specs(24, seed=replica_seed(rank, base=7), iters=args.batch_iters)
     den = C.Denoiser.gauss(0.8)
     scenes = []
     gen = torch.Generator(device=dev)
@@ -306,15 +331,12 @@ def run_batch(args, rank, world, local):
         torch.cuda.synchronize()
     elapsed = t_start.elapsed_time(t_end) / 1e3
     lat = batch.latencies()   # of the last launch
-    t_max = elapsed
+    t_max = max_over_ranks(elapsed, world, dev)
     if world > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
         dist.destroy_process_group()
     if rank != 0:
         return 0
-    value = units * K * world / t_max
+    value = job_throughput(units, K, world, t_max)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": t_max / K * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
@@ -454,7 +476,7 @@ def main():
     stream = torch.cuda.current_stream()
 
     # ---- inputs: seeded scene and draws on the host, data simulated on the device
-    seed = 1 + rank
+    seed = replica_seed(rank)
     wl = I.make_workload(args.workload, seed=seed, with_draws=False)
     L, n = wl.looks, wl.nx * wl.ny * wl.nz
     p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var)
@@ -502,11 +524,7 @@ def main():
     agent = sum(events[4 * i].elapsed_time(events[4 * i + 1]) for i in range(K)) / K / 1e3
     prior = sum(events[4 * i + 1].elapsed_time(events[4 * i + 2]) for i in range(K)) / K / 1e3
     passc = sum(events[4 * i + 2].elapsed_time(events[4 * i + 3]) for i in range(K)) / K / 1e3
-    t_max = elapsed
-    if world > 1:
-        t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(elapsed, world, dev)
     ce_last = float(ce[-1].item())
     finite = bool(torch.isfinite(wbar).all().item())
 
@@ -538,12 +556,8 @@ def main():
         for _ in range(args.e2e_calls):
             e2e_call()
         torch.cuda.synchronize()
-        e2e_t = (time.perf_counter() - t0) / args.e2e_calls
-        if world > 1:
-            t = torch.tensor([e2e_t], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_t = float(t.item())
-        e2e_value = n * L * e2e_iters * world / e2e_t
+        e2e_t = max_over_ranks((time.perf_counter() - t0) / args.e2e_calls, world, dev)
+        e2e_value = job_throughput(n * L * e2e_iters, 1, world, e2e_t)
     h2d = L * n * 8 + wl.nx * wl.ny * 4 + wl.nz * 4
     d2h = n * 4 + 2 * 8 * e2e_iters
 
@@ -561,7 +575,7 @@ def main():
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12   # TFLOP/s at the 2070 MHz max SM clock
 
-    value = n * L * K * world / t_max
+    value = job_throughput(n * L, K, world, t_max)
     # prior agent: residual CNN FLOPs per voxel (2 per MAC)
     if wl.denoiser["kind"] == "cnn":
         ch = wl.denoiser["channels"]
