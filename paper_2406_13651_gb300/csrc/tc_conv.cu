@@ -359,30 +359,34 @@ __global__ void __launch_bounds__(NT) k_conv_first(const float* __restrict__ in,
 // path's [C/4][nz][ny][nx][4] activations: out = x + b + sum_{c, tap} W[c][tap] act_c(v + tap).
 // A TF32x3 tensor-core tile would pad the single output channel to 16 columns and stage
 // the same hi/lo halo as a hidden layer for 1/C of its useful work.  CTA tile: 64
-// x-voxels x 8 rows of one z plane, two x-voxels per thread; one 4-channel group of the
-// halo in shared memory at a time.
-constexpr int CL_X = 64, CL_Y = 8, CL_NT = 256;
+// x-voxels x 8 rows x CL_Z planes, two x-voxels and CL_Z planes per thread; one 4-channel
+// group of the halo (CL_Z + 2 planes) in shared memory at a time, each staged row feeding
+// every output plane it borders.
+constexpr int CL_X = 64, CL_Y = 8, CL_Z = 4, CL_NT = 256;
+constexpr int CL_HX = CL_X + 2, CL_HY = CL_Y + 2, CL_HZ = CL_Z + 2;
+constexpr size_t CL_SMEM = sizeof(float4) * CL_HZ * CL_HY * CL_HX;
 template <int C>
-__global__ void __launch_bounds__(CL_NT) k_conv_last(const float4* __restrict__ act, const float* __restrict__ w,
+__global__ void __launch_bounds__(CL_NT, 2) k_conv_last(const float4* __restrict__ act, const float* __restrict__ w,
                                                      const float* __restrict__ bias, const float* __restrict__ resid,
                                                      float* __restrict__ out, int nx, int ny, int nz) {
-  constexpr int G = C / 4;
-  constexpr int HX = CL_X + 2, HY = CL_Y + 2, HV = 3 * HY * HX;
-  __shared__ float4 s_h[HV];
-  __shared__ float s_w[27 * C];   // [tap][c]
+  constexpr int G = C / 4, HV = CL_HZ * CL_HY * CL_HX;
+  extern __shared__ float4 s_h[];   // [CL_HZ][CL_HY][CL_HX]
+  __shared__ float s_w[27 * C];     // [tap][c]
   const int tid = threadIdx.x, tx = tid % (CL_X / 2), ty = tid / (CL_X / 2);
-  const int x0 = blockIdx.x * CL_X, y0 = blockIdx.y * CL_Y, z = blockIdx.z;
+  const int x0 = blockIdx.x * CL_X, y0 = blockIdx.y * CL_Y, z0 = blockIdx.z * CL_Z;
   const long long plane = (long long)nx * ny, n = plane * nz;
   for (int e = tid; e < 27 * C; e += CL_NT) {
     const int c = e % C, tap = e / C;
     s_w[e] = w[c * 27 + tap];
   }
-  float acc[2] = {0.f, 0.f};
+  float acc[CL_Z][2];
+#pragma unroll
+  for (int zo = 0; zo < CL_Z; ++zo) acc[zo][0] = acc[zo][1] = 0.f;
   for (int g = 0; g < G; ++g) {
     __syncthreads();
     for (int e = tid; e < HV; e += CL_NT) {
-      const int xr = e % HX, yr = (e / HX) % HY, zr = e / (HX * HY);
-      const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z + zr - 1;
+      const int xr = e % CL_HX, yr = (e / CL_HX) % CL_HY, zr = e / (CL_HX * CL_HY);
+      const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z0 + zr - 1;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
         v = act[(long long)g * n + (long long)gz * plane + (long long)gy * nx + gx];
@@ -390,19 +394,22 @@ __global__ void __launch_bounds__(CL_NT) k_conv_last(const float4* __restrict__ 
     }
     __syncthreads();
 #pragma unroll
-    for (int dz = 0; dz < 3; ++dz) {
+    for (int pz = 0; pz < CL_HZ; ++pz) {
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy) {
-        const float4* row = s_h + (dz * HY + ty + dy) * HX + 2 * tx;
-        float4 f[4];
+        const float4* row = s_h + (pz * CL_HY + ty + dy) * CL_HX + 2 * tx;
+        const float4 f[4] = {row[0], row[1], row[2], row[3]};
 #pragma unroll
-        for (int q = 0; q < 4; ++q) f[q] = row[q];
+        for (int dz = 0; dz < 3; ++dz) {
+          const int zo = pz - dz;   // output plane this staged plane feeds with tap dz
+          if (zo < 0 || zo >= CL_Z) continue;
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          const float* wp = s_w + (dz * 9 + dy * 3 + dx) * C + 4 * g;
-          acc[0] = fmaf(wp[0], f[dx].x, fmaf(wp[1], f[dx].y, fmaf(wp[2], f[dx].z, fmaf(wp[3], f[dx].w, acc[0]))));
-          acc[1] = fmaf(wp[0], f[dx + 1].x,
-                        fmaf(wp[1], f[dx + 1].y, fmaf(wp[2], f[dx + 1].z, fmaf(wp[3], f[dx + 1].w, acc[1]))));
+          for (int dx = 0; dx < 3; ++dx) {
+            const float* wp = s_w + (dz * 9 + dy * 3 + dx) * C + 4 * g;
+            acc[zo][0] = fmaf(wp[0], f[dx].x, fmaf(wp[1], f[dx].y, fmaf(wp[2], f[dx].z, fmaf(wp[3], f[dx].w, acc[zo][0]))));
+            acc[zo][1] = fmaf(wp[0], f[dx + 1].x,
+                              fmaf(wp[1], f[dx + 1].y, fmaf(wp[2], f[dx + 1].z, fmaf(wp[3], f[dx + 1].w, acc[zo][1]))));
+          }
         }
       }
     }
@@ -411,11 +418,16 @@ __global__ void __launch_bounds__(CL_NT) k_conv_last(const float4* __restrict__ 
   if (gy >= ny) return;
   const float b = __ldg(&bias[0]);
 #pragma unroll
-  for (int j = 0; j < 2; ++j) {
-    const int gx = x0 + 2 * tx + j;
-    if (gx >= nx) continue;
-    const long long vox = (long long)z * plane + (long long)gy * nx + gx;
-    out[vox] = acc[j] + b + resid[vox];
+  for (int zo = 0; zo < CL_Z; ++zo) {
+    const int gz = z0 + zo;
+    if (gz >= nz) continue;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int gx = x0 + 2 * tx + j;
+      if (gx >= nx) continue;
+      const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
+      out[vox] = acc[zo][j] + b + resid[vox];
+    }
   }
 }
 
@@ -564,9 +576,11 @@ static cudaError_t apply_tc_c(const clamp_denoiser* d, const float* in, float* o
         e = run_tc<KIND, C, 16, true>(cur, wp, d->b[i], nullptr, out, in, nx, ny, nz, err, st);
       } else {
         // TF32x3: the padded tile costs as much as a hidden layer; CUDA cores instead
-        dim3 grid((nx + CL_X - 1) / CL_X, (ny + CL_Y - 1) / CL_Y, nz);
-        k_conv_last<C><<<grid, CL_NT, 0, st>>>(reinterpret_cast<const float4*>(cur), d->w[i], d->b[i], in, out,
-                                               nx, ny, nz);
+        e = cudaFuncSetAttribute(k_conv_last<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CL_SMEM);
+        if (e != cudaSuccess) return e;
+        dim3 grid((nx + CL_X - 1) / CL_X, (ny + CL_Y - 1) / CL_Y, (nz + CL_Z - 1) / CL_Z);
+        k_conv_last<C><<<grid, CL_NT, CL_SMEM, st>>>(reinterpret_cast<const float4*>(cur), d->w[i], d->b[i], in,
+                                                     out, nx, ny, nz);
         e = cudaGetLastError();
       }
     } else {

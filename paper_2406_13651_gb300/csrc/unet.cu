@@ -654,6 +654,16 @@ extern "C" size_t clamp_unet_workspace_size(const clamp_unet* u, int32_t batch, 
   return acts_layout(u, batch, nx, ny, nz, nullptr, training != 0).bytes;
 }
 
+// The network's buffers live on the device it was created on.
+static bool on_unet_device(const clamp_unet* u, const char* where) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != u->dev) {
+    api_fail(CLAMP_EINVAL, "%s: the network was created on device %d, current device is %d", where, u->dev, dev);
+    return false;
+  }
+  return true;
+}
+
 #define U_TRY(x)                                                                       \
   do {                                                                                 \
     cudaError_t _e = (x);                                                              \
@@ -694,6 +704,7 @@ static clamp_status unet_forward(clamp_unet* u, const float* x, int B, int nx, i
 extern "C" clamp_status clamp_unet_forward(clamp_unet* u, const float* x, float* y, int32_t batch, int32_t nx,
                                            int32_t ny, int32_t nz, void* ws, size_t ws_bytes, void* stream) {
   if (!u || !x || !y) return api_fail(CLAMP_EINVAL, "clamp_unet_forward: NULL argument");
+  if (!on_unet_device(u, "clamp_unet_forward")) return CLAMP_EINVAL;
   if (!unet_shape_ok(batch, nx, ny, nz))
     return api_fail(CLAMP_EINVAL, "clamp_unet_forward: nx, ny, nz must be multiples of 4");
   const Acts a = acts_layout(u, batch, nx, ny, nz, ws, false);
@@ -735,6 +746,7 @@ extern "C" clamp_status clamp_unet_backward(clamp_unet* u, const float* x, const
                                             int32_t nx, int32_t ny, int32_t nz, double* loss, void* ws,
                                             size_t ws_bytes, void* stream) {
   if (!u || !x || !target) return api_fail(CLAMP_EINVAL, "clamp_unet_backward: NULL argument");
+  if (!on_unet_device(u, "clamp_unet_backward")) return CLAMP_EINVAL;
   if (!unet_shape_ok(batch, nx, ny, nz))
     return api_fail(CLAMP_EINVAL, "clamp_unet_backward: nx, ny, nz must be multiples of 4");
   const Acts a = acts_layout(u, batch, nx, ny, nz, ws, true);
@@ -817,6 +829,7 @@ extern "C" clamp_status clamp_unet_backward(clamp_unet* u, const float* x, const
 extern "C" clamp_status clamp_unet_adam(clamp_unet* u, float lr, float beta1, float beta2, float eps, int32_t t,
                                         void* stream) {
   if (!u || t < 1) return api_fail(CLAMP_EINVAL, "clamp_unet_adam: bad arguments");
+  if (!on_unet_device(u, "clamp_unet_adam")) return CLAMP_EINVAL;
   const double bc1 = 1.0 - pow((double)beta1, t), bc2 = 1.0 - pow((double)beta2, t);
   const float lr_t = (float)(lr * sqrt(bc2) / bc1), eps_t = (float)(eps * sqrt(bc2));
   k_adam<<<grid_for((long long)u->count), UT, 0, (cudaStream_t)stream>>>(u->p, u->g, u->m, u->v, (long long)u->count,
@@ -838,6 +851,7 @@ extern "C" clamp_status clamp_unet_warm_start(clamp_unet* u, int32_t nx, int32_t
                                               float floor_rel, float* r_init, void* ws, size_t ws_bytes,
                                               void* stream) {
   if (!u || !r0 || !r_init) return api_fail(CLAMP_EINVAL, "clamp_unet_warm_start: NULL argument");
+  if (!on_unet_device(u, "clamp_unet_warm_start")) return CLAMP_EINVAL;
   if (!unet_shape_ok(1, nx, ny, nz))
     return api_fail(CLAMP_EINVAL, "clamp_unet_warm_start: nx, ny, nz must be multiples of 4");
   const Acts a = acts_layout(u, 1, nx, ny, nz, ws, false);
@@ -860,6 +874,7 @@ extern "C" clamp_status clamp_unet_loss(clamp_unet* u, const float* x, const flo
                                         int32_t nx, int32_t ny, int32_t nz, double* loss, void* ws, size_t ws_bytes,
                                         void* stream) {
   if (!u || !x || !target || !loss) return api_fail(CLAMP_EINVAL, "clamp_unet_loss: NULL argument");
+  if (!on_unet_device(u, "clamp_unet_loss")) return CLAMP_EINVAL;
   if (!unet_shape_ok(batch, nx, ny, nz))
     return api_fail(CLAMP_EINVAL, "clamp_unet_loss: nx, ny, nz must be multiples of 4");
   const Acts a = acts_layout(u, batch, nx, ny, nz, ws, true);   // the loss gradient goes to gout
