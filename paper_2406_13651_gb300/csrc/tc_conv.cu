@@ -89,10 +89,15 @@ __device__ __forceinline__ void mma_kind(int kind, uint32_t d, uint64_t a, uint6
   }
 }
 
+__host__ __device__ constexpr bool tc_tall(int kind, int cin) { return kind == TC_TF32X3 && cin <= 32; }
+
 template <int KIND, int CIN, int NPAD>
 struct TcCfg {
   using K = TcKind<KIND>;
-  static constexpr int TY = K::TY, TZ = K::TZ, MT = TY * TZ, HY = TY + 2, HZ = TZ + 2;
+  // TF32x3 at <= 32 channels: 4 rows x 1 plane (one MMA then spans up to 3 tiles, N <= 96);
+  // the hi/lo copies leave one CTA per SM either way
+  static constexpr bool TALL = tc_tall(KIND, CIN);
+  static constexpr int TY = TALL ? 4 : K::TY, TZ = TALL ? 1 : K::TZ, MT = TY * TZ, HY = TY + 2, HZ = TZ + 2;
   static constexpr int CH = 2 * K::EPV;               // input channels per chunk (one MMA K step)
   static constexpr int CHUNKS = CIN / CH;
   static constexpr int HALO_VEC = 2 * HZ * HY * TC_HX;  // 16-byte vectors per chunk, per split
@@ -597,8 +602,9 @@ bool tc_denoiser_supports(const clamp_denoiser* d, int nx, int ny, int nz) {
   const bool bf = d->dtype == CLAMP_DENOISER_BF16;
   const int C = d->channels;
   const bool ch = bf ? (C == 16 || C == 32 || C == 48 || C == 64) : (C == 16 || C == 32 || C == 48);
-  const int ty = bf ? TcKind<TC_BF16>::TY : TcKind<TC_TF32X3>::TY;
-  const int tz = bf ? TcKind<TC_BF16>::TZ : TcKind<TC_TF32X3>::TZ;
+  const bool tall = tc_tall(bf ? TC_BF16 : TC_TF32X3, C);
+  const int ty = tall ? 4 : bf ? TcKind<TC_BF16>::TY : TcKind<TC_TF32X3>::TY;
+  const int tz = tall ? 1 : bf ? TcKind<TC_BF16>::TZ : TcKind<TC_TF32X3>::TZ;
   return ch && nx % TCX == 0 && ny % ty == 0 && nz % tz == 0;
 }
 
