@@ -181,6 +181,14 @@ clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channels, int32_t
                                        clamp_denoiser** out);
 void clamp_denoiser_destroy(clamp_denoiser* den);
 
+/* Self-check of the bounded waits the tensor-core kernels use so that a missing MMA
+ * completion makes them report CLAMP_ETIMEOUT instead of hanging: one mbarrier receives
+ * its arrival (the wait must succeed), nothing arrives on another (the wait must give up
+ * after `limit` polls, 1 <= limit <= 2^20).  result: host int32[2] = {first wait
+ * succeeded, second wait succeeded}; a sound build gives {1, 0}.  Synchronous.  The paper
+ * has no counterpart. */
+clamp_status clamp_selftest_bounded_wait(int32_t limit, int32_t* result);
+
 /* Tensor-core building block check: D[128][n] = A[128][k] B[n][k]^T with A, B BF16
  * (row-major, k contiguous) and D FP32, on one CTA through tcgen05 MMAs with TMEM
  * accumulators -- the same descriptor conventions the BF16 CNN prior uses.

@@ -41,6 +41,7 @@ EXPORTS = [
     "clamp_unet_workspace_size", "clamp_unet_forward", "clamp_unet_backward", "clamp_unet_adam",
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
     "clamp_point_cloud_workspace_size", "clamp_point_cloud_metrics", "clamp_denoiser_create_unet",
+    "clamp_selftest_bounded_wait",
 ]
 
 
@@ -134,6 +135,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_unet_loss": (I, [P, P, P, I, I, I, I, P, P, S, P]),
         "clamp_point_cloud_workspace_size": (S, []),
         "clamp_denoiser_create_unet": (I, [P, ctypes.c_float, ctypes.POINTER(P)]),
+        "clamp_selftest_bounded_wait": (I, [I, ctypes.POINTER(ctypes.c_int32)]),
         "clamp_point_cloud_metrics": (I, [P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
@@ -571,3 +573,10 @@ def point_cloud_metrics(r_hat, r_true, threshold: float, max_dist: float, stream
            "clamp_point_cloud_metrics")
     return dict(distance=float(out[0]), false_positive_rate=float(out[1]), nrmse=float(out[2]), kept=int(out[3]),
                 removed=int(out[4]), beta=float(out[5]))
+
+
+def selftest_bounded_wait(limit: int = 1000) -> tuple:
+    """(first wait succeeded, second wait succeeded): (1, 0) for a sound build."""
+    out = (ctypes.c_int32 * 2)(-1, -1)
+    _check(load().clamp_selftest_bounded_wait(limit, out), "clamp_selftest_bounded_wait")
+    return int(out[0]), int(out[1])

@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
         if constexpr (EXACT) rn = (float)prox_exact((double)wl, (double)K, (double)c.prox_var);
         else rn = prox_quad(wl, rp, K, c.prox_var, c.beta);
         Ro[i] = rn;
-        bad |= !isfinite(rn);
+        bad |= !isfinite(rn) || !isfinite(K);   // K covers mu: the prox's clip would hide a NaN there
       } else {
         rn = rp;
       }
@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
       const float2 rn = make_float2(prox_quad(wl.x, rp.x, K0, c.prox_var, c.beta),
                                     prox_quad(wl.y, rp.y, K1, c.prox_var, c.beta));
       Ro[i] = rn;
-      bad |= !isfinite(rn.x) || !isfinite(rn.y);
+      bad |= !isfinite(rn.x) || !isfinite(rn.y) || !isfinite(K0) || !isfinite(K1);   // K covers mu
       wb0.add(c.ups_look * wl.x);
       wb1.add(c.ups_look * wl.y);
       xb0.add(c.ups_look * (2.0f * rn.x - wl.x));

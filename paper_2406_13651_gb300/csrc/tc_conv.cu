@@ -436,6 +436,24 @@ __global__ void __launch_bounds__(CL_NT, 2) k_conv_last(const float4* __restrict
   }
 }
 
+// Self-check of the bounded mbarrier wait the tensor-core kernels use instead of an
+// unbounded spin: barrier 0 receives its one arrival, so its wait must succeed; nothing
+// arrives on barrier 1, so its wait must give up after `limit` polls.
+__global__ void k_wait_selftest(uint32_t limit, int* out) {
+  __shared__ uint64_t mbar[2];
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&mbar[0], 1);
+    tc::mbar_init(&mbar[1], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(tc::smem_addr(&mbar[0]))
+                 : "memory");
+    out[0] = tc::mbar_wait_bounded(&mbar[0], 0u, limit) ? 1 : 0;
+    out[1] = tc::mbar_wait_bounded(&mbar[1], 0u, limit) ? 1 : 0;
+  }
+}
+
 // One-tile GEMM on the tensor core: D[128][N] = A[128][K] B[N][K]^T, FP32 out.  BF16 operands
 // (KIND = BF16) or FP32 operands through the TF32x3 split.  Checks the descriptor,
 // instruction-descriptor and TMEM conventions the conv kernels rely on.
@@ -685,4 +703,22 @@ extern "C" clamp_status clamp_tc_gemm_tf32x3(int32_t n, int32_t k, const float* 
     return CLAMP_ECUDA;
   kern<<<1, 128, smem, (cudaStream_t)stream>>>(a, b, d, n, k);
   return cudaGetLastError() == cudaSuccess ? CLAMP_OK : CLAMP_ECUDA;
+}
+
+extern "C" clamp_status clamp_selftest_bounded_wait(int32_t limit, int32_t* result) {
+  if (!result || limit < 1 || limit > (1 << 20)) return CLAMP_EINVAL;
+  int* d = nullptr;
+  if (cudaMalloc(&d, 2 * sizeof(int)) != cudaSuccess) return CLAMP_ENOMEM;
+  cudaError_t e = cudaMemset(d, 0xff, 2 * sizeof(int));
+  if (e == cudaSuccess) {
+    clamp::k_wait_selftest<<<1, 32>>>((uint32_t)limit, d);
+    e = cudaGetLastError();
+  }
+  int h[2] = {-1, -1};
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return CLAMP_ECUDA;
+  result[0] = h[0];
+  result[1] = h[1];
+  return CLAMP_OK;
 }
