@@ -7,6 +7,7 @@ header is newer than the library.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import fcntl
 import glob
 import os
 import shutil
@@ -46,9 +47,22 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile and link; returns the library path."""
+    """Compile and link; returns the library path.  Concurrent callers (one process per
+    GPU) serialise on a lock file, so only the first one compiles."""
     if not force and up_to_date():
         return LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    with open(os.path.join(OUT_DIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if not force and up_to_date():   # another process finished the build meanwhile
+                return LIB
+            return _compile_and_link(verbose, extra_flags)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _compile_and_link(verbose: bool, extra_flags) -> str:
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(BUILD_DIR, exist_ok=True)
