@@ -69,6 +69,10 @@ typedef struct clamp_params {
   int32_t flags;        /* CLAMP_FLAG_* */
   int32_t check_every;  /* clamp_reconstruct reads the residual back every this many iterations (tol > 0) */
   double tol;           /* stop when the convergence error <= tol (0 = run max_iters) */
+  int32_t init_mu_steps; /* with a given r_init: this many mu updates of the forward agents
+                            (Alg. 2 steps 5-8 with r' = r_init held fixed) before the first
+                            iteration, so mu starts consistent with r_init; 0..1000 */
+  int32_t reserved;     /* set to 0 */
 } clamp_params;
 
 /* Per-run report of clamp_reconstruct (host memory). */

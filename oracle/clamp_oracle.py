@@ -395,15 +395,29 @@ def clamp_iteration(state: OracleState, y, a, den: dict, noise_var, prox_var,
                        mu_res_hist=state.mu_res_hist)
 
 
+def mu_presteps(st: OracleState, y, a, noise_var, steps: int) -> OracleState:
+    """Warm-start refinement of mu: ``steps`` times, every look's gradient step with exact
+    line search (Alg. 2 steps 6-8) with r' = r_l held fixed and no prox."""
+    alpha = alpha_of(a)
+    for l in range(y.shape[0]):
+        for _ in range(steps):
+            d = grad_direction(st.mu[l], y[l], st.r[l], a, noise_var, alpha)
+            st.mu[l] = st.mu[l] + line_search_gamma(st.mu[l], d, y[l], st.r[l], a, noise_var, alpha) * d
+    return st
+
+
 def reconstruct(y, pupil, window, den: dict, noise_var, prox_var, iters, rho=0.5,
                 prior_weight=0.5, r_init=None, tol: float = 0.0, exact_prox: bool = False,
-                no_aperture: bool = False):
+                no_aperture: bool = False, init_mu_steps: int = 0):
     """CLAMP (Alg. 2): initialise (Sec. IV-A), iterate, output r* = wbar.
     Stops early once the convergence error falls to ``tol`` (when tol > 0).
     ``exact_prox``: the cubic-root prox of the EM surrogate instead of App. A's quadratic step.
-    ``no_aperture``: the Sec. IV-A ablation (a = 1, closed-form mu update)."""
+    ``no_aperture``: the Sec. IV-A ablation (a = 1, closed-form mu update).
+    ``init_mu_steps``: with ``r_init``, that many mu refinement steps (``mu_presteps``)."""
     a = np.ones((len(window), pupil.shape[0], pupil.shape[1])) if no_aperture else aperture(pupil, window)
     st = init_state(y, a, r_init)
+    if r_init is not None and init_mu_steps > 0 and not no_aperture:
+        st = mu_presteps(st, y, a, noise_var, init_mu_steps)
     for _ in range(iters):
         st = clamp_iteration(st, y, a, den, noise_var, prox_var, rho, prior_weight, exact_prox, no_aperture)
         if tol > 0 and st.ce_hist[-1] <= tol:

@@ -57,7 +57,7 @@ class Params(ctypes.Structure):
                 ("looks", ctypes.c_int32), ("noise_var", ctypes.c_float), ("prox_var", ctypes.c_float),
                 ("rho", ctypes.c_float), ("prior_weight", ctypes.c_float), ("max_iters", ctypes.c_int32),
                 ("k0", ctypes.c_int32), ("flags", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("init_mu_steps", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Scene(ctypes.Structure):
@@ -167,9 +167,9 @@ def _stream(stream) -> int | None:
 
 
 def make_params(nx, ny, nz, looks, noise_var, prox_var, rho=0.5, prior_weight=0.5, max_iters=0, k0=0,
-                flags=0, check_every=10, tol=0.0) -> Params:
+                flags=0, check_every=10, tol=0.0, init_mu_steps=0) -> Params:
     return Params(nx, ny, nz, looks, noise_var, prox_var, rho, prior_weight, max_iters, k0, flags,
-                  check_every, tol)
+                  check_every, tol, init_mu_steps, 0)
 
 
 class Denoiser:

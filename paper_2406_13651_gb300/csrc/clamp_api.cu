@@ -88,6 +88,7 @@ extern "C" clamp_status clamp_check_params(const clamp_params* p) {
   if (p->max_iters < 0) return api_fail(CLAMP_EINVAL, "max_iters must be >= 0");
   if (p->k0 < 0) return api_fail(CLAMP_EINVAL, "k0 must be >= 0");
   if (!(p->tol >= 0.0)) return api_fail(CLAMP_EINVAL, "tol must be >= 0");
+  if (p->init_mu_steps < 0 || p->init_mu_steps > 1000) return api_fail(CLAMP_EINVAL, "init_mu_steps must be in [0, 1000]");
   return CLAMP_OK;
 }
 
@@ -293,6 +294,10 @@ static clamp_status do_init(const clamp_params* p, const Derived& d, const float
   return CLAMP_OK;
 }
 
+static clamp_status do_init_warm(const clamp_params* p, const Derived& d, const float* y, const float* pupil,
+                                 const float* window, const float* r_init, float2* mu, float* r, float* w,
+                                 const AgentLayout& al, void* ws, cudaStream_t st);
+
 extern "C" clamp_status clamp_init(const clamp_params* p, const float* y, const float* pupil, const float* window,
                                    const float* r_init, float* mu, float* r, float* w, void* ws, size_t ws_bytes,
                                    void* stream) {
@@ -304,7 +309,7 @@ extern "C" clamp_status clamp_init(const clamp_params* p, const float* y, const 
   cudaStream_t st = (cudaStream_t)stream;
   Derived d;
   API_TRY(recon_prepare(p, pupil, window, st, &d));
-  return do_init(p, d, y, pupil, window, r_init, reinterpret_cast<float2*>(mu), r, w, al, ws, st);
+  return do_init_warm(p, d, y, pupil, window, r_init, reinterpret_cast<float2*>(mu), r, w, al, ws, st);
 }
 
 // The initial image of Alg. 2 on its own: r0 = (1/L) sum_l |A^H y_l / alpha|^2 (the
@@ -363,6 +368,22 @@ static clamp_status agent_ffts(const Derived& d, const float* y, const float* pu
                             at<float4>(ws, al.T), at<float2>(ws, al.U), pt, tuned_variants(d.g), st),
            "forward-agent FFT passes");
   API_CUDA(launch_gamma(d.g, d.s.nv, pt, at<float>(ws, al.gamma), at<double>(ws, al.mures), st), "line search");
+  return CLAMP_OK;
+}
+
+// Initialisation (do_init) and, when the caller gives r_init (a warm start), p->init_mu_steps
+// mu updates of every forward agent with r' = r_init fixed (Alg. 2 steps 5-8 without the
+// prox): the back-projected mu of the initialisation is far from the posterior mean that
+// r_init implies, and the first iterations would otherwise spend themselves repairing it.
+static clamp_status do_init_warm(const clamp_params* p, const Derived& d, const float* y, const float* pupil,
+                                 const float* window, const float* r_init, float2* mu, float* r, float* w,
+                                 const AgentLayout& al, void* ws, cudaStream_t st) {
+  API_TRY(do_init(p, d, y, pupil, window, r_init, mu, r, w, al, ws, st));
+  if (!r_init || p->init_mu_steps <= 0 || (p->flags & CLAMP_FLAG_NO_APERTURE)) return CLAMP_OK;
+  for (int s = 0; s < p->init_mu_steps; ++s) {
+    API_TRY(agent_ffts(d, y, pupil, window, mu, r, al, ws, st));
+    API_CUDA(launch_mu_update(d.g, mu, at<float2>(ws, al.U), at<float>(ws, al.gamma), st), "mu update");
+  }
   return CLAMP_OK;
 }
 
@@ -597,7 +618,7 @@ clamp_status recon_enqueue(const clamp_params* p, const ReconPlan& d, const floa
   float* w = at<float>(ws, rl.w);
   const long long n = (long long)p->nx * p->ny * p->nz;
   API_CUDA(cudaMemsetAsync(at<int>(aws, al.err), 0, sizeof(int), st), "memset");
-  API_TRY(do_init(p, d, y, pupil, window, r_init, mu, r, w, al, aws, st));
+  API_TRY(do_init_warm(p, d, y, pupil, window, r_init, mu, r, w, al, aws, st));
   if (p->max_iters == 0)
     API_CUDA(cudaMemcpyAsync(r_out, r + (long long)p->looks * n, n * sizeof(float), cudaMemcpyDeviceToDevice, st),
              "copy");
@@ -649,7 +670,7 @@ static clamp_status reconstruct_impl(const clamp_params* p, const float* y, cons
   Derived d;
   API_TRY(recon_prepare(p, pupil, window, st, &d));
   API_CUDA(cudaMemsetAsync(at<int>(aws, al.err), 0, sizeof(int), st), "memset");
-  API_TRY(do_init(p, d, y, pupil, window, r_init, mu, r, w, al, aws, st));
+  API_TRY(do_init_warm(p, d, y, pupil, window, r_init, mu, r, w, al, aws, st));
   if (p->max_iters == 0) {
     // r* = wbar of the initial state = r0
     API_CUDA(cudaMemcpyAsync(r_out, r + (long long)p->looks * n, n * sizeof(float), cudaMemcpyDeviceToDevice, st),

@@ -853,6 +853,24 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
 
 static bool aligned(const void* p, uintptr_t a) { return ((uintptr_t)p % a) == 0; }
 
+__global__ void __launch_bounds__(NT) k_mu_update(long long n, long long total, float2* __restrict__ mu,
+                                                  const float2* __restrict__ d, const float* __restrict__ gamma) {
+  for (long long i = (long long)blockIdx.x * NT + threadIdx.x; i < total; i += (long long)gridDim.x * NT) {
+    const float gm = __ldg(&gamma[i / n]);
+    const float2 dd = d[i];
+    float2 m = mu[i];
+    m.x = fmaf(gm, dd.x, m.x);
+    m.y = fmaf(gm, dd.y, m.y);
+    mu[i] = m;
+  }
+}
+
+cudaError_t launch_mu_update(const Geom& g, float2* mu, const float2* d, const float* gamma, cudaStream_t st) {
+  const long long total = g.n * g.L;
+  k_mu_update<<<passc_blocks(total), NT, 0, st>>>(g.n, total, mu, d, gamma);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st) {
   const bool pair = g.n % 2 == 0 && aligned(c.w, 8) && aligned(c.r, 8) && aligned(c.wbar, 8) &&
                     aligned(c.mu, 16) && aligned(c.d, 16);

@@ -96,6 +96,8 @@ struct PassC {
   int closed_mu;     // 1: mu = d / (1 + sigma_w^2 / (r' + sigma_w^2)) with d holding F^H y (no aperture)
 };
 int passc_blocks(long long n);
+// mu <- mu + gamma_l d for all looks (the mu half of pass C: Eq. mu-update).
+cudaError_t launch_mu_update(const Geom& g, float2* mu, const float2* d, const float* gamma, cudaStream_t st);
 cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st);
 cudaError_t launch_prox_only(const Geom& g, const PassC& c, cudaStream_t st);
 cudaError_t launch_mace_only(const Geom& g, const PassC& c, cudaStream_t st);

@@ -27,6 +27,7 @@ from . import inputs as I
 
 CHANNELS = (16, 32, 64)
 FLOOR = 1e-3
+MU_STEPS = 10      # mu refinement steps after the warm start (clamp_params.init_mu_steps)
 
 
 @dataclass
@@ -195,18 +196,19 @@ def psnr(r_hat: np.ndarray, r_true: np.ndarray) -> float:
 
 def compare(net: C.UNet, p_plain: C.Params, y, pupil, window, den: C.Denoiser, tol: float = 1e-3,
             max_iters: int = 300, ref_iters: int = 0, warm_k0: int = 0, r_true: np.ndarray | None = None,
-            pc_threshold: float | None = None, pc_max_dist: float | None = None):
+            pc_threshold: float | None = None, pc_max_dist: float | None = None, warm_mu_steps: int = MU_STEPS):
     """Iterations and wall time to CE <= tol from the speckle-average init and from the warm
     start (which includes r0, the U-Net inference and the mapping), on the same data; both
     results' relative L2 distance to the plain solution run for ref_iters iterations
     (2 x the plain count when 0) and, given r_true, their PSNR and (with pc_threshold and
     pc_max_dist) their point-cloud metrics (Sec. IV-B).  warm_k0 starts the warm run's
-    beta_k schedule at k = warm_k0 + 1 (App. A) instead of k = 1."""
+    beta_k schedule at k = warm_k0 + 1 (App. A) instead of k = 1; warm_mu_steps refines the
+    forward agents' mu for r_init before the first iteration (inside the timed warm run)."""
     import torch
     p = C.make_params(p_plain.nx, p_plain.ny, p_plain.nz, p_plain.looks, p_plain.noise_var, p_plain.prox_var,
                       max_iters=max_iters, tol=tol, check_every=1)
     pw = C.make_params(p.nx, p.ny, p.nz, p.looks, p.noise_var, p.prox_var, max_iters=max_iters, tol=tol,
-                       check_every=1, k0=warm_k0)
+                       check_every=1, k0=warm_k0, init_mu_steps=warm_mu_steps)
     ws = C.reconstruct_workspace(p, den)
     aws = C.workspace(p)
     r_plain = torch.empty((p.nz, p.ny, p.nx), dtype=torch.float32, device=y.device)

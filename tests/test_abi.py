@@ -32,8 +32,9 @@ def test_exports_every_declared_symbol(lib):
 
 def test_params_struct_layout_matches_header():
     from paper_2406_13651_gb300 import clamp
-    assert ctypes.sizeof(clamp.Params) == 56
+    assert ctypes.sizeof(clamp.Params) == 64
     assert clamp.Params.tol.offset == 48
+    assert clamp.Params.init_mu_steps.offset == 56
 
 
 def test_supported_lengths(lib):

@@ -274,6 +274,21 @@ def test_reconstruct_paper_variants_match_oracle(C, mode):
     np.testing.assert_allclose(res.ce_hist, st.ce_hist, rtol=1e-3)
 
 
+def test_reconstruct_warm_start_with_mu_steps(C):
+    """A given r_init with init_mu_steps: mu refined with r' = r_init held fixed before the
+    first iteration, as the oracle's mu_presteps does."""
+    wl, a, y32, y64 = problem("cfg1", seed=8, iters=6)
+    r_init = (0.5 * wl.r_true + 0.01 + 0.004 * np.random.default_rng(8).uniform(size=wl.r_true.shape))
+    r_init = r_init.astype(np.float32)
+    ref, st = O.reconstruct(y64, wl.pupil, wl.window, wl.denoiser, wl.noise_var, wl.prox_var, 6,
+                            r_init=r_init.astype(np.float64), init_mu_steps=4)
+    p = params(C, wl, max_iters=6, init_mu_steps=4)
+    res = C.reconstruct(p, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), C.Denoiser.gauss(0.8),
+                        r_init=to_dev(r_init))
+    assert rel(res.r.cpu().numpy(), ref) < TOL_RECON
+    np.testing.assert_allclose(res.ce_hist, st.ce_hist, rtol=1e-3)
+
+
 def test_reconstruct_warm_start_and_tolerance(C):
     wl, a, y32, y64 = problem("cfg1", seed=2, iters=30)
     r_init = (wl.r_true + 0.01).astype(np.float32)

@@ -470,3 +470,18 @@ def test_point_cloud_metrics_closed_forms():
     far[7, 7, 0] = 0.5                                    # an outlier 5+ voxels from every true point
     m = O.point_cloud_metrics(far, r, 0.0, 2.0)
     assert m["removed"] == 1 and abs(m["false_positive_rate"] - 0.25) < 1e-15
+
+
+def test_mu_presteps_reach_the_exact_posterior_mean():
+    """With r' held at r_init, the warm-start mu steps minimise h (floored D, reading R5),
+    whose minimiser is the exact posterior mean at r' + sigma_w^2 / alpha."""
+    rng = np.random.default_rng(21)
+    shape = (2, 4, 4)
+    a = (rng.uniform(size=shape) < 0.6).astype(float)
+    y = (rng.normal(size=(1,) + shape) + 1j * rng.normal(size=(1,) + shape)) * a
+    r_init = rng.uniform(0.2, 1.0, shape)
+    nv = 0.05
+    st = O.init_state(y, a, r_init)
+    st = O.mu_presteps(st, y, a, nv, 400)
+    mu_ref, _ = O.exact_posterior(st.r[0] + nv / O.alpha_of(a), y[0], a, nv)
+    np.testing.assert_allclose(st.mu[0], mu_ref, rtol=1e-8, atol=1e-10)
