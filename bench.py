@@ -593,7 +593,7 @@ def main():
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
         elif tensor_path:
             tf32x3_peak = bf16_peak * (1.1 / 2.25) / 3.0
-            roofline = {"bound": "tensor", "kernel": "k_conv3_tc<TF32x3> (+ SIMT first layer): the prior agent",
+            roofline = {"bound": "tensor", "kernel": "k_conv3_tc_plane<TF32x3> (+ SIMT first and last layers): the prior agent",
                         "achieved": cnn_tflops, "peak": tf32x3_peak, "unit": "TFLOP/s",
                         "frac": cnn_tflops / tf32x3_peak, "traffic": None,
                         "peak_source": "measured bf16_tflops_sustained x nominal TF32/BF16 ratio (1.1/2.25), "

@@ -89,15 +89,13 @@ __device__ __forceinline__ void mma_kind(int kind, uint32_t d, uint64_t a, uint6
   }
 }
 
+// TF32x3 at <= 32 channels runs k_conv3_tc_plane (tiles of 4 rows x 1 plane).
 __host__ __device__ constexpr bool tc_tall(int kind, int cin) { return kind == TC_TF32X3 && cin <= 32; }
 
 template <int KIND, int CIN, int NPAD>
 struct TcCfg {
   using K = TcKind<KIND>;
-  // TF32x3 at <= 32 channels: 4 rows x 1 plane (one MMA then spans up to 3 tiles, N <= 96);
-  // the hi/lo copies leave one CTA per SM either way
-  static constexpr bool TALL = tc_tall(KIND, CIN);
-  static constexpr int TY = TALL ? 4 : K::TY, TZ = TALL ? 1 : K::TZ, MT = TY * TZ, HY = TY + 2, HZ = TZ + 2;
+  static constexpr int TY = K::TY, TZ = K::TZ, MT = TY * TZ, HY = TY + 2, HZ = TZ + 2;
   static constexpr int CH = 2 * K::EPV;               // input channels per chunk (one MMA K step)
   static constexpr int CHUNKS = CIN / CH;
   static constexpr int HALO_VEC = 2 * HZ * HY * TC_HX;  // 16-byte vectors per chunk, per split
@@ -296,6 +294,171 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   } else if (tid == 0) {
     if (err) atomicOr(err, 2);
     // the chunk's MMAs may still be in flight: give them a bounded wait before TMEM is freed
+    tc::mbar_wait_bounded(mbar, fail_parity, kWaitLimit);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, Cfg::TMEM_COLS);
+}
+
+// TF32x3 at <= 32 channels: per-plane staging, three CTAs per SM.  A CTA computes 4 rows
+// x 1 plane of 128-voxel tiles (one MMA spans up to three tiles of the row, N <= 96).  The
+// staging unit is one (channel chunk, halo plane) step: the raw FP32 halo plane (2 channel
+// groups x 6 rows x 130 voxels), split in place into TF32 hi and lo copies as in
+// k_conv3_tc, and the hi/lo weights of the matching dz, about 68 KB at 32 channels; a
+// step's MMAs are those of one dz, in k_conv3_tc's order.  Each CTA stages, issues and
+// waits step by step as k_conv3_tc does per chunk, and with about 70 KB of shared memory
+// and 128 TMEM columns per CTA three CTAs share an SM, so one CTA's staging overlaps the
+// other CTAs' MMAs (k_conv3_tc's whole-chunk halo, hi and lo, leaves one CTA per SM).
+template <int CIN, int NPAD>
+struct TcPlaneCfg {
+  static constexpr int TY = 4, HY = TY + 2, MT = TY, CTAS = 3;
+  static constexpr int CHUNKS = CIN / 8, STEPS = 3 * CHUNKS;
+  static constexpr int HALO_VEC = 2 * HY * TC_HX;   // per copy: [2 channel groups][HY][HX]
+  static constexpr int W_VEC = 3 * 2 * 3 * NPAD;    // per copy: [dx][2 channel groups][dy = 2, 1, 0][NPAD]
+  static constexpr int STAGE_VEC = 2 * (HALO_VEC + W_VEC);  // [halo hi][halo lo][w hi][w lo]
+  static constexpr int ZB_VEC = 2 * NPAD;
+  static constexpr int TMEM_COLS = pow2_cols(MT * NPAD);
+  static constexpr size_t SMEM = 1024 + 16 * ((size_t)STAGE_VEC + ZB_VEC) + 64;
+  static_assert(CIN % 8 == 0 && NPAD % 16 == 0 && TY * NPAD <= 256, "tile");
+  static_assert(CTAS * (SMEM + 1024) <= 228 * 1024 && CTAS * TMEM_COLS <= 512, "three CTAs per SM");
+};
+
+template <int CIN, int NPAD>
+__global__ void __launch_bounds__(TC_NT, TcPlaneCfg<CIN, NPAD>::CTAS)
+    k_conv3_tc_plane(const uint4* __restrict__ in, const uint4* __restrict__ wpk, const float* __restrict__ bias,
+                     uint4* __restrict__ out_act, int nx, int ny, int nz, int* err) {
+  using Cfg = TcPlaneCfg<CIN, NPAD>;
+  using Kd = TcKind<TC_TF32X3>;
+  constexpr int TY = Cfg::TY, HY = Cfg::HY, MT = Cfg::MT;
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint4* s_stage = reinterpret_cast<uint4*>(base);              // [halo hi][halo lo][w hi][w lo]
+  uint4* s_zero = s_stage + Cfg::STAGE_VEC;                      // [2][NPAD] zeros
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_zero + Cfg::ZB_VEC);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * TCX, y0 = blockIdx.y * TY, z0 = blockIdx.z;
+  const long long plane = (long long)nx * ny, n = plane * nz;
+
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    *abort_flag = 0;
+  }
+  for (int e = tid; e < Cfg::ZB_VEC; e += TC_NT) s_zero[e] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, Cfg::TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  const uint32_t stage_s = tc::smem_addr(s_stage), z_s = tc::smem_addr(s_zero);
+  constexpr uint32_t LBO_A = HY * TC_HX * 16;   // channel group 0 -> 1
+  constexpr uint32_t LBO_B = 3 * NPAD * 16;     // channel group 0 -> 1 within a dx block
+  uint4* s_raw = s_stage + Cfg::HALO_VEC;       // the raw FP32 halo lands in the lo copy
+  uint4* s_w = s_stage + 2 * Cfg::HALO_VEC;
+  bool aborted = false;
+  uint32_t fail_parity = 0;
+
+#pragma unroll 1
+  for (int s = 0; s < Cfg::STEPS; ++s) {
+    const int c = s / 3, dz = s % 3, gz = z0 + dz - 1;
+    const bool zin = gz >= 0 && gz < nz;
+    for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
+      const int xr = e % TC_HX, t = e / TC_HX;
+      const int yr = t % HY, cg = t / HY;
+      const int gx = x0 + xr - 1, gy = y0 + yr - 1;
+      const bool inb = zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+      const uint4* src = inb ? &in[(long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx + gx] : in;
+      cp_async16(&s_raw[e], src, inb);
+    }
+#pragma unroll
+    for (int sp = 0; sp < 2; ++sp) {
+      const uint4* wsrc = wpk + ((long long)sp * Cfg::CHUNKS + c) * (27 * 2 * NPAD) + dz * Cfg::W_VEC;
+      for (int e = tid; e < Cfg::W_VEC; e += TC_NT) cp_async16(&s_w[sp * Cfg::W_VEC + e], &wsrc[e], true);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    {
+      float4* hi = reinterpret_cast<float4*>(s_stage);
+      float4* lo = reinterpret_cast<float4*>(s_raw);
+      for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
+        const float4 f = lo[e];
+        const float4 h = make_float4(tf32_rn(f.x), tf32_rn(f.y), tf32_rn(f.z), tf32_rn(f.w));
+        hi[e] = h;
+        lo[e] = make_float4(tf32_rn(f.x - h.x), tf32_rn(f.y - h.y), tf32_rn(f.z - h.z), tf32_rn(f.w - h.w));
+      }
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      const uint64_t a_hi = tc::make_desc(stage_s, LBO_A, 128);
+      const uint64_t a_lo = a_hi + (uint64_t)Cfg::HALO_VEC;   // start address in 16-byte units
+      const uint64_t b_hi = tc::make_desc(stage_s + 2u * Cfg::HALO_VEC * 16u, LBO_B, 128);
+      const uint64_t b_lo = b_hi + (uint64_t)Cfg::W_VEC;
+      if (s == 0) {  // clear every accumulator: D = A x 0
+        const uint64_t bz = tc::make_desc(z_s, NPAD * 16, 128);
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+          mma_kind(TC_TF32X3, tbase + (uint32_t)(mt * NPAD), a_hi, bz, Kd::idesc(128, NPAD), 0u);
+      }
+#pragma unroll
+      for (int hy = 0; hy < HY; ++hy) {
+        // tiles ty_lo..ty_hi read halo row hy with taps dy = hy - ty
+        const int ty_lo = hy - 2 > 0 ? hy - 2 : 0, ty_hi = hy < TY - 1 ? hy : TY - 1;
+        const uint32_t idesc = Kd::idesc(128, (ty_hi - ty_lo + 1) * NPAD);
+        const uint32_t dcol = tbase + (uint32_t)(ty_lo * NPAD);
+        const int dyp = 2 - (hy - ty_lo);
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const uint64_t aoff = (uint64_t)(hy * TC_HX + dx);
+          const uint64_t boff = (uint64_t)(dx * 6 * NPAD + dyp * NPAD);
+          // TF32x3 terms: (a_lo, b_hi), (a_hi, b_lo), (a_hi, b_hi)
+          mma_kind(TC_TF32X3, dcol, a_lo + aoff, b_hi + boff, idesc, 1u);
+          mma_kind(TC_TF32X3, dcol, a_hi + aoff, b_lo + boff, idesc, 1u);
+          mma_kind(TC_TF32X3, dcol, a_hi + aoff, b_hi + boff, idesc, 1u);
+        }
+      }
+      tc::mma_commit(mbar);
+    }
+    // every thread waits for the step's MMAs: they read the buffer the next step overwrites
+    if (!tc::mbar_wait_bounded(mbar, (uint32_t)(s & 1), kWaitLimit)) atomicOr(abort_flag, 1);
+    __syncthreads();
+    if (*abort_flag) {
+      aborted = true;
+      fail_parity = (uint32_t)(s & 1);
+      break;
+    }
+  }
+  tc::fence_after_sync();
+  if (!aborted) {
+    const int q = warp & 3, h = warp >> 2;
+    float4* o4 = reinterpret_cast<float4*>(out_act);
+#pragma unroll 1
+    for (int mt = 0; mt < MT; ++mt) {
+      const int gy = y0 + mt, gx = x0 + 32 * q + lane;
+      const long long vox = (long long)z0 * plane + (long long)gy * nx + gx;
+      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * NPAD);
+      constexpr int HALF = NPAD / 2;
+#pragma unroll
+      for (int j = 0; j < HALF / 8; ++j) {
+        const int col = h * HALF + 8 * j;
+        float v[8];
+        tc::tmem_ld_x8(trow + (uint32_t)col, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
+        o4[(long long)(col / 4) * n + vox] = make_float4(v[0], v[1], v[2], v[3]);
+        o4[(long long)(col / 4 + 1) * n + vox] = make_float4(v[4], v[5], v[6], v[7]);
+      }
+    }
+  } else if (tid == 0) {
+    if (err) atomicOr(err, 2);
+    // the step's MMAs may still be in flight: give them a bounded wait before TMEM is freed
     tc::mbar_wait_bounded(mbar, fail_parity, kWaitLimit);
   }
   tc::fence_before_sync();
@@ -570,6 +733,18 @@ static cudaError_t run_tc(const uint4* in, const uint4* wpk, const float* bias, 
   return cudaGetLastError();
 }
 
+template <int CIN, int NPAD>
+static cudaError_t run_tc_plane(const uint4* in, const uint4* wpk, const float* bias, uint4* out_act, int nx, int ny,
+                                int nz, int* err, cudaStream_t st) {
+  using Cfg = TcPlaneCfg<CIN, NPAD>;
+  auto kern = k_conv3_tc_plane<CIN, NPAD>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
+  if (e != cudaSuccess) return e;
+  dim3 grid(nx / TCX, ny / Cfg::TY, nz);
+  kern<<<grid, TC_NT, Cfg::SMEM, st>>>(in, wpk, bias, out_act, nx, ny, nz, err);
+  return cudaGetLastError();
+}
+
 template <int C, bool BF16>
 static cudaError_t run_first(const float* in, const float* w, const float* b, uint4* out, int nx, int ny, int nz,
                              cudaStream_t st) {
@@ -608,7 +783,10 @@ static cudaError_t apply_tc_c(const clamp_denoiser* d, const float* in, float* o
       }
     } else {
       uint4* dst = cur == A ? B : A;
-      e = run_tc<KIND, C, C, false>(cur, wp, d->b[i], dst, nullptr, nullptr, nx, ny, nz, err, st);
+      if constexpr (tc_tall(KIND, C))
+        e = run_tc_plane<C, C>(cur, wp, d->b[i], dst, nx, ny, nz, err, st);
+      else
+        e = run_tc<KIND, C, C, false>(cur, wp, d->b[i], dst, nullptr, nullptr, nx, ny, nz, err, st);
       cur = dst;
     }
     if (e != cudaSuccess) return e;
