@@ -468,7 +468,31 @@ __global__ void __launch_bounds__(TC_NT, TcPlaneCfg<CIN, NPAD>::CTAS)
 
 // First layer (one input channel): out[co] = ReLU(b[co] + sum_taps W[co][tap] x(v + tap)), written
 // in 16-byte channel groups.  BF16: x and W are BF16-rounded and the output is BF16.
-// SIMT: K = 27 is too small for the tensor path.
+// SIMT: K = 27 is too small for the tensor path.  A thread computes the two voxels (z, z + 1)
+// of a column, so each weight load from shared memory feeds both; taps accumulate in the
+// same order for every voxel, an input outside the volume contributing zero.
+template <int C, bool BF16>
+__device__ __forceinline__ void store_first(uint4* out, long long n, long long v, float (&acc)[C]) {
+#pragma unroll
+  for (int co = 0; co < C; ++co) acc[co] = fmaxf(acc[co], 0.f);
+  if constexpr (BF16) {
+#pragma unroll
+    for (int g = 0; g < C / 8; ++g) {
+      uint4 o;
+      o.x = pack_bf16x2(acc[8 * g + 0], acc[8 * g + 1]);
+      o.y = pack_bf16x2(acc[8 * g + 2], acc[8 * g + 3]);
+      o.z = pack_bf16x2(acc[8 * g + 4], acc[8 * g + 5]);
+      o.w = pack_bf16x2(acc[8 * g + 6], acc[8 * g + 7]);
+      out[(long long)g * n + v] = o;
+    }
+  } else {
+    float4* o4 = reinterpret_cast<float4*>(out);
+#pragma unroll
+    for (int g = 0; g < C / 4; ++g)
+      o4[(long long)g * n + v] = make_float4(acc[4 * g], acc[4 * g + 1], acc[4 * g + 2], acc[4 * g + 3]);
+  }
+}
+
 template <int C, bool BF16>
 __global__ void __launch_bounds__(NT) k_conv_first(const float* __restrict__ in, const float* __restrict__ w,
                                                    const float* __restrict__ bias, uint4* __restrict__ out, int nx,
@@ -482,44 +506,41 @@ __global__ void __launch_bounds__(NT) k_conv_first(const float* __restrict__ in,
   for (int e = threadIdx.x; e < C; e += NT) s_b[e] = bias[e];
   __syncthreads();
   const long long plane = (long long)nx * ny, n = plane * nz;
-  for (long long v = (long long)blockIdx.x * NT + threadIdx.x; v < n; v += (long long)gridDim.x * NT) {
-    const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / plane);
-    float acc[C];
+  const long long pairs = plane * ((nz + 1) / 2);
+  for (long long p = (long long)blockIdx.x * NT + threadIdx.x; p < pairs; p += (long long)gridDim.x * NT) {
+    const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = 2 * (int)(p / plane);
+    const bool has1 = z + 1 < nz;
+    float a0[C], a1[C];
 #pragma unroll
-    for (int co = 0; co < C; ++co) acc[co] = s_b[co];
+    for (int co = 0; co < C; ++co) a0[co] = a1[co] = s_b[co];
 #pragma unroll 1
     for (int tap = 0; tap < 27; ++tap) {
-      const int zz = z + tap / 9 - 1, yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-      if (zz < 0 || zz >= nz || yy < 0 || yy >= ny || xx < 0 || xx >= nx) continue;
-      float xv = __ldg(&in[(long long)zz * plane + (long long)yy * nx + xx]);
-      if (BF16) xv = __bfloat162float(__float2bfloat16_rn(xv));
+      const int yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
+      if (yy < 0 || yy >= ny || xx < 0 || xx >= nx) continue;
+      const int z0 = z + tap / 9 - 1;   // input plane of voxel z; voxel z + 1 reads z0 + 1
+      const long long off = (long long)yy * nx + xx;
+      float x0 = z0 >= 0 && z0 < nz ? __ldg(&in[(long long)z0 * plane + off]) : 0.f;
+      float x1 = has1 && z0 + 1 < nz ? __ldg(&in[(long long)(z0 + 1) * plane + off]) : 0.f;
+      if (BF16) {
+        x0 = __bfloat162float(__float2bfloat16_rn(x0));
+        x1 = __bfloat162float(__float2bfloat16_rn(x1));
+      }
 #pragma unroll
       for (int q = 0; q < C / 4; ++q) {
         const float4 wv = s_w[tap * (C / 4) + q];
-        acc[4 * q + 0] = fmaf(xv, wv.x, acc[4 * q + 0]);
-        acc[4 * q + 1] = fmaf(xv, wv.y, acc[4 * q + 1]);
-        acc[4 * q + 2] = fmaf(xv, wv.z, acc[4 * q + 2]);
-        acc[4 * q + 3] = fmaf(xv, wv.w, acc[4 * q + 3]);
+        a0[4 * q + 0] = fmaf(x0, wv.x, a0[4 * q + 0]);
+        a0[4 * q + 1] = fmaf(x0, wv.y, a0[4 * q + 1]);
+        a0[4 * q + 2] = fmaf(x0, wv.z, a0[4 * q + 2]);
+        a0[4 * q + 3] = fmaf(x0, wv.w, a0[4 * q + 3]);
+        a1[4 * q + 0] = fmaf(x1, wv.x, a1[4 * q + 0]);
+        a1[4 * q + 1] = fmaf(x1, wv.y, a1[4 * q + 1]);
+        a1[4 * q + 2] = fmaf(x1, wv.z, a1[4 * q + 2]);
+        a1[4 * q + 3] = fmaf(x1, wv.w, a1[4 * q + 3]);
       }
     }
-#pragma unroll
-    for (int co = 0; co < C; ++co) acc[co] = fmaxf(acc[co], 0.f);
-    if constexpr (BF16) {
-#pragma unroll
-      for (int g = 0; g < C / 8; ++g) {
-        uint4 o;
-        o.x = pack_bf16x2(acc[8 * g + 0], acc[8 * g + 1]);
-        o.y = pack_bf16x2(acc[8 * g + 2], acc[8 * g + 3]);
-        o.z = pack_bf16x2(acc[8 * g + 4], acc[8 * g + 5]);
-        o.w = pack_bf16x2(acc[8 * g + 6], acc[8 * g + 7]);
-        out[(long long)g * n + v] = o;
-      }
-    } else {
-      float4* o4 = reinterpret_cast<float4*>(out);
-#pragma unroll
-      for (int g = 0; g < C / 4; ++g)
-        o4[(long long)g * n + v] = make_float4(acc[4 * g], acc[4 * g + 1], acc[4 * g + 2], acc[4 * g + 3]);
-    }
+    const long long v = (long long)z * plane + (long long)y * nx + x;
+    store_first<C, BF16>(out, n, v, a0);
+    if (has1) store_first<C, BF16>(out, n, v + plane, a1);
   }
 }
 
@@ -527,56 +548,61 @@ __global__ void __launch_bounds__(NT) k_conv_first(const float* __restrict__ in,
 // path's [C/4][nz][ny][nx][4] activations: out = x + b + sum_{c, tap} W[c][tap] act_c(v + tap).
 // A TF32x3 tensor-core tile would pad the single output channel to 16 columns and stage
 // the same hi/lo halo as a hidden layer for 1/C of its useful work.  CTA tile: 64
-// x-voxels x 8 rows x CL_Z planes, two x-voxels and CL_Z planes per thread; one 4-channel
-// group of the halo (CL_Z + 2 planes) in shared memory at a time, each staged row feeding
-// every output plane it borders.
-constexpr int CL_X = 64, CL_Y = 8, CL_Z = 4, CL_NT = 256;
+// x-voxels x 4 rows x CL_Z planes, 128 threads; a thread computes x-voxels tx and tx + 32
+// (so a warp's shared-memory row reads are consecutive) on CL_Z planes.  One 4-channel
+// group of the halo (CL_Z + 2 planes, 38 KB) is staged with cp.async at a time, each
+// staged row feeding every output plane it borders; four CTAs share an SM, so one
+// CTA's staging overlaps the others' arithmetic.
+constexpr int CL_X = 64, CL_Y = 4, CL_Z = 4, CL_NT = 128;
 constexpr int CL_HX = CL_X + 2, CL_HY = CL_Y + 2, CL_HZ = CL_Z + 2;
 constexpr size_t CL_SMEM = sizeof(float4) * CL_HZ * CL_HY * CL_HX;
 template <int C>
-__global__ void __launch_bounds__(CL_NT, 2) k_conv_last(const float4* __restrict__ act, const float* __restrict__ w,
+__global__ void __launch_bounds__(CL_NT, 4) k_conv_last(const float4* __restrict__ act, const float* __restrict__ w,
                                                      const float* __restrict__ bias, const float* __restrict__ resid,
                                                      float* __restrict__ out, int nx, int ny, int nz) {
   constexpr int G = C / 4, HV = CL_HZ * CL_HY * CL_HX;
-  extern __shared__ float4 s_h[];   // [CL_HZ][CL_HY][CL_HX]
-  __shared__ float s_w[27 * C];     // [tap][c]
-  const int tid = threadIdx.x, tx = tid % (CL_X / 2), ty = tid / (CL_X / 2);
+  extern __shared__ float4 s_h[];     // [CL_HZ][CL_HY][CL_HX]
+  __shared__ float4 s_w[27 * G];      // [tap][channel group]: 4 channels' weights
+  const int tid = threadIdx.x, tx = tid % 32, ty = tid / 32;
   const int x0 = blockIdx.x * CL_X, y0 = blockIdx.y * CL_Y, z0 = blockIdx.z * CL_Z;
   const long long plane = (long long)nx * ny, n = plane * nz;
-  for (int e = tid; e < 27 * C; e += CL_NT) {
-    const int c = e % C, tap = e / C;
-    s_w[e] = w[c * 27 + tap];
+  for (int e = tid; e < 27 * G; e += CL_NT) {
+    const int g = e % G, tap = e / G;
+    s_w[e] = make_float4(w[(4 * g) * 27 + tap], w[(4 * g + 1) * 27 + tap], w[(4 * g + 2) * 27 + tap],
+                         w[(4 * g + 3) * 27 + tap]);
   }
   float acc[CL_Z][2];
 #pragma unroll
   for (int zo = 0; zo < CL_Z; ++zo) acc[zo][0] = acc[zo][1] = 0.f;
+#pragma unroll 1
   for (int g = 0; g < G; ++g) {
-    __syncthreads();
+    __syncthreads();   // the previous group's reads of the halo are done
     for (int e = tid; e < HV; e += CL_NT) {
-      const int xr = e % CL_HX, yr = (e / CL_HX) % CL_HY, zr = e / (CL_HX * CL_HY);
+      const int xr = e % CL_HX, t = e / CL_HX;
+      const int yr = t % CL_HY, zr = t / CL_HY;
       const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z0 + zr - 1;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-        v = act[(long long)g * n + (long long)gz * plane + (long long)gy * nx + gx];
-      s_h[e] = v;
+      const bool inb = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+      const float4* src = inb ? &act[(long long)g * n + (long long)gz * plane + (long long)gy * nx + gx] : act;
+      cp_async16(&s_h[e], src, inb);
     }
+    cp_async_wait_all();
     __syncthreads();
 #pragma unroll
     for (int pz = 0; pz < CL_HZ; ++pz) {
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy) {
-        const float4* row = s_h + (pz * CL_HY + ty + dy) * CL_HX + 2 * tx;
-        const float4 f[4] = {row[0], row[1], row[2], row[3]};
+        const float4* row = s_h + (pz * CL_HY + ty + dy) * CL_HX + tx;
+        const float4 f[6] = {row[0], row[1], row[2], row[32], row[33], row[34]};
 #pragma unroll
         for (int dz = 0; dz < 3; ++dz) {
           const int zo = pz - dz;   // output plane this staged plane feeds with tap dz
           if (zo < 0 || zo >= CL_Z) continue;
 #pragma unroll
           for (int dx = 0; dx < 3; ++dx) {
-            const float* wp = s_w + (dz * 9 + dy * 3 + dx) * C + 4 * g;
-            acc[zo][0] = fmaf(wp[0], f[dx].x, fmaf(wp[1], f[dx].y, fmaf(wp[2], f[dx].z, fmaf(wp[3], f[dx].w, acc[zo][0]))));
-            acc[zo][1] = fmaf(wp[0], f[dx + 1].x,
-                              fmaf(wp[1], f[dx + 1].y, fmaf(wp[2], f[dx + 1].z, fmaf(wp[3], f[dx + 1].w, acc[zo][1]))));
+            const float4 wv = s_w[(dz * 9 + dy * 3 + dx) * G + g];
+            acc[zo][0] = fmaf(wv.x, f[dx].x, fmaf(wv.y, f[dx].y, fmaf(wv.z, f[dx].z, fmaf(wv.w, f[dx].w, acc[zo][0]))));
+            acc[zo][1] = fmaf(wv.x, f[dx + 3].x,
+                              fmaf(wv.y, f[dx + 3].y, fmaf(wv.z, f[dx + 3].z, fmaf(wv.w, f[dx + 3].w, acc[zo][1]))));
           }
         }
       }
@@ -591,7 +617,7 @@ __global__ void __launch_bounds__(CL_NT, 2) k_conv_last(const float4* __restrict
     if (gz >= nz) continue;
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      const int gx = x0 + 2 * tx + j;
+      const int gx = x0 + tx + 32 * j;
       if (gx >= nx) continue;
       const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
       out[vox] = acc[zo][j] + b + resid[vox];
@@ -748,8 +774,8 @@ static cudaError_t run_tc_plane(const uint4* in, const uint4* wpk, const float* 
 template <int C, bool BF16>
 static cudaError_t run_first(const float* in, const float* w, const float* b, uint4* out, int nx, int ny, int nz,
                              cudaStream_t st) {
-  const long long n = (long long)nx * ny * nz;
-  long long blocks = (n + NT - 1) / NT;
+  const long long pairs = (long long)nx * ny * ((nz + 1) / 2);
+  long long blocks = (pairs + NT - 1) / NT;
   if (blocks > 152 * 8) blocks = 152 * 8;
   k_conv_first<C, BF16><<<(unsigned)blocks, NT, 0, st>>>(in, w, b, out, nx, ny, nz);
   return cudaGetLastError();
