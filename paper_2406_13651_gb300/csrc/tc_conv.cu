@@ -468,9 +468,10 @@ __global__ void __launch_bounds__(TC_NT, TcPlaneCfg<CIN, NPAD>::CTAS)
 
 // First layer (one input channel): out[co] = ReLU(b[co] + sum_taps W[co][tap] x(v + tap)), written
 // in 16-byte channel groups.  BF16: x and W are BF16-rounded and the output is BF16.
-// SIMT: K = 27 is too small for the tensor path.  A thread computes the two voxels (z, z + 1)
-// of a column, so each weight load from shared memory feeds both; taps accumulate in the
-// same order for every voxel, an input outside the volume contributing zero.
+// SIMT: K = 27 is too small for the tensor path.  A CTA stages its input tile with a
+// one-voxel halo (zeros outside the volume) in shared memory; a thread computes the two
+// voxels (z, z + 1) of a column, so each weight load feeds both.  Taps accumulate in the
+// same order for every voxel.
 template <int C, bool BF16>
 __device__ __forceinline__ void store_first(uint4* out, long long n, long long v, float (&acc)[C]) {
 #pragma unroll
@@ -493,55 +494,62 @@ __device__ __forceinline__ void store_first(uint4* out, long long n, long long v
   }
 }
 
+constexpr int CF_X = 32, CF_Y = 8, CF_Z = 2;   // CTA tile; a thread computes one (x, y) and CF_Z planes
+constexpr int CF_HX = CF_X + 2, CF_HY = CF_Y + 2, CF_HZ = CF_Z + 2;
 template <int C, bool BF16>
 __global__ void __launch_bounds__(NT) k_conv_first(const float* __restrict__ in, const float* __restrict__ w,
                                                    const float* __restrict__ bias, uint4* __restrict__ out, int nx,
                                                    int ny, int nz) {
-  __shared__ float4 s_w[27 * C / 4];  // [tap][co]
+  static_assert(CF_X * CF_Y == NT && CF_Z == 2, "one thread per (x, y) column of two planes");
+  __shared__ float4 s_w[27 * C / 4];                 // [tap][co]
   __shared__ float s_b[C];
-  for (int e = threadIdx.x; e < 27 * C; e += NT) {
+  __shared__ float s_in[CF_HZ * CF_HY * CF_HX];      // input tile with a one-voxel halo, zeros outside
+  const int tid = threadIdx.x, tx = tid % CF_X, ty = tid / CF_X;
+  const int x0 = blockIdx.x * CF_X, y0 = blockIdx.y * CF_Y, z0 = blockIdx.z * CF_Z;
+  const long long plane = (long long)nx * ny, n = plane * nz;
+  for (int e = tid; e < 27 * C; e += NT) {
     const int co = e % C, tap = e / C;
     reinterpret_cast<float*>(s_w)[e] = w[co * 27 + tap];
   }
-  for (int e = threadIdx.x; e < C; e += NT) s_b[e] = bias[e];
-  __syncthreads();
-  const long long plane = (long long)nx * ny, n = plane * nz;
-  const long long pairs = plane * ((nz + 1) / 2);
-  for (long long p = (long long)blockIdx.x * NT + threadIdx.x; p < pairs; p += (long long)gridDim.x * NT) {
-    const int x = (int)(p % nx), y = (int)((p / nx) % ny), z = 2 * (int)(p / plane);
-    const bool has1 = z + 1 < nz;
-    float a0[C], a1[C];
-#pragma unroll
-    for (int co = 0; co < C; ++co) a0[co] = a1[co] = s_b[co];
-#pragma unroll 1
-    for (int tap = 0; tap < 27; ++tap) {
-      const int yy = y + (tap / 3) % 3 - 1, xx = x + tap % 3 - 1;
-      if (yy < 0 || yy >= ny || xx < 0 || xx >= nx) continue;
-      const int z0 = z + tap / 9 - 1;   // input plane of voxel z; voxel z + 1 reads z0 + 1
-      const long long off = (long long)yy * nx + xx;
-      float x0 = z0 >= 0 && z0 < nz ? __ldg(&in[(long long)z0 * plane + off]) : 0.f;
-      float x1 = has1 && z0 + 1 < nz ? __ldg(&in[(long long)(z0 + 1) * plane + off]) : 0.f;
-      if (BF16) {
-        x0 = __bfloat162float(__float2bfloat16_rn(x0));
-        x1 = __bfloat162float(__float2bfloat16_rn(x1));
-      }
-#pragma unroll
-      for (int q = 0; q < C / 4; ++q) {
-        const float4 wv = s_w[tap * (C / 4) + q];
-        a0[4 * q + 0] = fmaf(x0, wv.x, a0[4 * q + 0]);
-        a0[4 * q + 1] = fmaf(x0, wv.y, a0[4 * q + 1]);
-        a0[4 * q + 2] = fmaf(x0, wv.z, a0[4 * q + 2]);
-        a0[4 * q + 3] = fmaf(x0, wv.w, a0[4 * q + 3]);
-        a1[4 * q + 0] = fmaf(x1, wv.x, a1[4 * q + 0]);
-        a1[4 * q + 1] = fmaf(x1, wv.y, a1[4 * q + 1]);
-        a1[4 * q + 2] = fmaf(x1, wv.z, a1[4 * q + 2]);
-        a1[4 * q + 3] = fmaf(x1, wv.w, a1[4 * q + 3]);
-      }
+  for (int e = tid; e < C; e += NT) s_b[e] = bias[e];
+  for (int e = tid; e < CF_HZ * CF_HY * CF_HX; e += NT) {
+    const int xr = e % CF_HX, t = e / CF_HX;
+    const int yr = t % CF_HY, zr = t / CF_HY;
+    const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z0 + zr - 1;
+    float v = 0.f;
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz) {
+      v = __ldg(&in[(long long)gz * plane + (long long)gy * nx + gx]);
+      if (BF16) v = __bfloat162float(__float2bfloat16_rn(v));
     }
-    const long long v = (long long)z * plane + (long long)y * nx + x;
-    store_first<C, BF16>(out, n, v, a0);
-    if (has1) store_first<C, BF16>(out, n, v + plane, a1);
+    s_in[e] = v;
   }
+  __syncthreads();
+  const int x = x0 + tx, y = y0 + ty;
+  if (x >= nx || y >= ny) return;
+  float a0[C], a1[C];
+#pragma unroll
+  for (int co = 0; co < C; ++co) a0[co] = a1[co] = s_b[co];
+#pragma unroll 1
+  for (int tap = 0; tap < 27; ++tap) {
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    const float* col = s_in + (ty + dy) * CF_HX + tx + dx;
+    const float x0v = col[dz * CF_HY * CF_HX], x1v = col[(dz + 1) * CF_HY * CF_HX];
+#pragma unroll
+    for (int q = 0; q < C / 4; ++q) {
+      const float4 wv = s_w[tap * (C / 4) + q];
+      a0[4 * q + 0] = fmaf(x0v, wv.x, a0[4 * q + 0]);
+      a0[4 * q + 1] = fmaf(x0v, wv.y, a0[4 * q + 1]);
+      a0[4 * q + 2] = fmaf(x0v, wv.z, a0[4 * q + 2]);
+      a0[4 * q + 3] = fmaf(x0v, wv.w, a0[4 * q + 3]);
+      a1[4 * q + 0] = fmaf(x1v, wv.x, a1[4 * q + 0]);
+      a1[4 * q + 1] = fmaf(x1v, wv.y, a1[4 * q + 1]);
+      a1[4 * q + 2] = fmaf(x1v, wv.z, a1[4 * q + 2]);
+      a1[4 * q + 3] = fmaf(x1v, wv.w, a1[4 * q + 3]);
+    }
+  }
+  const long long v = (long long)z0 * plane + (long long)y * nx + x;
+  store_first<C, BF16>(out, n, v, a0);
+  if (z0 + 1 < nz) store_first<C, BF16>(out, n, v + plane, a1);
 }
 
 // Last layer of the FP32 residual CNN (C -> 1) on FP32 CUDA cores, reading the tensor
@@ -774,10 +782,8 @@ static cudaError_t run_tc_plane(const uint4* in, const uint4* wpk, const float* 
 template <int C, bool BF16>
 static cudaError_t run_first(const float* in, const float* w, const float* b, uint4* out, int nx, int ny, int nz,
                              cudaStream_t st) {
-  const long long pairs = (long long)nx * ny * ((nz + 1) / 2);
-  long long blocks = (pairs + NT - 1) / NT;
-  if (blocks > 152 * 8) blocks = 152 * 8;
-  k_conv_first<C, BF16><<<(unsigned)blocks, NT, 0, st>>>(in, w, b, out, nx, ny, nz);
+  dim3 grid((nx + CF_X - 1) / CF_X, (ny + CF_Y - 1) / CF_Y, (nz + CF_Z - 1) / CF_Z);
+  k_conv_first<C, BF16><<<grid, NT, 0, st>>>(in, w, b, out, nx, ny, nz);
   return cudaGetLastError();
 }
 
