@@ -358,5 +358,14 @@ def test_full_size_forward_agent_and_mace(C):
     z0, y0, x0, h = 20, 40, 60, 5
     crop = st.w[wl.looks, z0 - h:z0 + 8 + h, y0 - h:y0 + 16 + h, x0 - h:x0 + 16 + h]
     ref = O.denoise_cnn(crop, wl.denoiser["weights"], wl.denoiser["biases"])[h:-h, h:-h, h:-h]
-    got = out.cpu().numpy()[z0:z0 + 8, y0:y0 + 16, x0:x0 + 16]
-    assert rel(got, ref) < 1e-5
+    got_all = out.cpu().numpy()
+    assert rel(got_all[z0:z0 + 8, y0:y0 + 16, x0:x0 + 16], ref) < 1e-5
+    # the two corners: the crop keeps the volume's own edge, so its zero padding there is
+    # the volume's, and a 5-voxel halo on the inner side
+    nz, ny, nx = got_all.shape
+    for (z0, y0, x0) in [(0, 0, 0), (nz - 8, ny - 16, nx - 16)]:
+        zl, yl, xl = max(z0 - h, 0), max(y0 - h, 0), max(x0 - h, 0)
+        zh, yh, xh = min(z0 + 8 + h, nz), min(y0 + 16 + h, ny), min(x0 + 16 + h, nx)
+        ref = O.denoise_cnn(st.w[wl.looks, zl:zh, yl:yh, xl:xh], wl.denoiser["weights"], wl.denoiser["biases"])
+        ref = ref[z0 - zl:z0 - zl + 8, y0 - yl:y0 - yl + 16, x0 - xl:x0 - xl + 16]
+        assert rel(got_all[z0:z0 + 8, y0:y0 + 16, x0:x0 + 16], ref) < 1e-5, (z0, y0, x0)
