@@ -34,6 +34,11 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum over the five kernels of one FP32 prior-agent
+# call (5 layers x 32 channels, 128x128x64), from the ncu capture summarised in
+# profiles/prior_agent_traffic_128x128x64.md
+PRIOR_TRAFFIC_128 = 879_613_952
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -593,9 +598,12 @@ def main():
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
         elif tensor_path:
             tf32x3_peak = bf16_peak * (1.1 / 2.25) / 3.0
+            # DRAM bytes of one prior-agent call (5 x 32 channels at 128x128x64) from one ncu
+            # capture of its five kernels; other sizes or networks have no capture
+            measured = (wl.nx, wl.ny, wl.nz, ch, len(wl.denoiser["weights"])) == (128, 128, 64, 32, 5)
             roofline = {"bound": "tensor", "kernel": "k_conv3_tc_plane<TF32x3> (+ SIMT first and last layers): the prior agent",
                         "achieved": cnn_tflops, "peak": tf32x3_peak, "unit": "TFLOP/s",
-                        "frac": cnn_tflops / tf32x3_peak, "traffic": None,
+                        "frac": cnn_tflops / tf32x3_peak, "traffic": PRIOR_TRAFFIC_128 if measured else None,
                         "peak_source": "measured bf16_tflops_sustained x nominal TF32/BF16 ratio (1.1/2.25), "
                                        "/3 for the three TF32 MMAs per FP32 product",
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
