@@ -303,9 +303,10 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
 
 // TF32x3 at <= 32 channels: per-plane staging, three CTAs per SM.  A CTA computes 4 rows
 // x 1 plane of 128-voxel tiles (one MMA spans up to three tiles of the row, N <= 96).  The
-// staging unit is one (channel chunk, halo plane) step: the raw FP32 halo plane (2 channel
-// groups x 6 rows x 130 voxels), split in place into TF32 hi and lo copies as in
-// k_conv3_tc, and the hi/lo weights of the matching dz, about 68 KB at 32 channels; a
+// staging unit is one (channel chunk, halo plane) step: the FP32 halo plane (2 channel
+// groups x 6 rows x 130 voxels), loaded into registers and written once as TF32 hi and lo
+// copies (split as in k_conv3_tc), and the hi/lo weights of the matching dz (cp.async),
+// about 68 KB at 32 channels; a
 // step's MMAs are those of one dz, in k_conv3_tc's order.  Each CTA stages, issues and
 // waits step by step as k_conv3_tc does per chunk, and with about 70 KB of shared memory
 // and 128 TMEM columns per CTA three CTAs share an SM, so one CTA's staging overlaps the
@@ -359,7 +360,7 @@ __global__ void __launch_bounds__(TC_NT, TcPlaneCfg<CIN, NPAD>::CTAS)
   const uint32_t stage_s = tc::smem_addr(s_stage), z_s = tc::smem_addr(s_zero);
   constexpr uint32_t LBO_A = HY * TC_HX * 16;   // channel group 0 -> 1
   constexpr uint32_t LBO_B = 3 * NPAD * 16;     // channel group 0 -> 1 within a dx block
-  uint4* s_raw = s_stage + Cfg::HALO_VEC;       // the raw FP32 halo lands in the lo copy
+  uint4* s_raw = s_stage + Cfg::HALO_VEC;       // the lo copy of the halo
   uint4* s_w = s_stage + 2 * Cfg::HALO_VEC;
   bool aborted = false;
   uint32_t fail_parity = 0;
@@ -368,31 +369,29 @@ __global__ void __launch_bounds__(TC_NT, TcPlaneCfg<CIN, NPAD>::CTAS)
   for (int s = 0; s < Cfg::STEPS; ++s) {
     const int c = s / 3, dz = s % 3, gz = z0 + dz - 1;
     const bool zin = gz >= 0 && gz < nz;
-    for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
-      const int xr = e % TC_HX, t = e / TC_HX;
-      const int yr = t % HY, cg = t / HY;
-      const int gx = x0 + xr - 1, gy = y0 + yr - 1;
-      const bool inb = zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
-      const uint4* src = inb ? &in[(long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx + gx] : in;
-      cp_async16(&s_raw[e], src, inb);
-    }
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp) {
       const uint4* wsrc = wpk + ((long long)sp * Cfg::CHUNKS + c) * (27 * 2 * NPAD) + dz * Cfg::W_VEC;
       for (int e = tid; e < Cfg::W_VEC; e += TC_NT) cp_async16(&s_w[sp * Cfg::W_VEC + e], &wsrc[e], true);
     }
-    cp_async_wait_all();
-    __syncthreads();
     {
       float4* hi = reinterpret_cast<float4*>(s_stage);
       float4* lo = reinterpret_cast<float4*>(s_raw);
+      const float4* in4 = reinterpret_cast<const float4*>(in);
+#pragma unroll 4
       for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
-        const float4 f = lo[e];
+        const int xr = e % TC_HX, t = e / TC_HX;
+        const int yr = t % HY, cg = t / HY;
+        const int gx = x0 + xr - 1, gy = y0 + yr - 1;
+        const bool inb = zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
+        float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (inb) f = __ldg(&in4[(long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx + gx]);
         const float4 h = make_float4(tf32_rn(f.x), tf32_rn(f.y), tf32_rn(f.z), tf32_rn(f.w));
         hi[e] = h;
         lo[e] = make_float4(tf32_rn(f.x - h.x), tf32_rn(f.y - h.y), tf32_rn(f.z - h.z), tf32_rn(f.w - h.w));
       }
     }
+    cp_async_wait_all();
     tc::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
