@@ -27,7 +27,7 @@ from . import inputs as I
 
 CHANNELS = (16, 32, 64)
 FLOOR = 1e-3
-MU_STEPS = 10      # mu refinement steps after the warm start (clamp_params.init_mu_steps)
+MU_STEPS = 6       # mu refinement steps after the warm start (clamp_params.init_mu_steps)
 
 
 @dataclass
