@@ -55,6 +55,15 @@ typedef enum clamp_status {
  * alpha = 1) and the mu update is the closed-form minimiser of h,
  * mu = F^H y / (1 + sigma_w^2 / (r' + sigma_w^2)); no FFT runs per iteration. */
 #define CLAMP_FLAG_NO_APERTURE 0x4
+/* Prior-agent schedule.  Within an iteration the prior agent and the forward agents both
+ * read the previous w and write disjoint state, so the prior may run on a second stream
+ * beside the forward agents (forked from and joined back to the caller's stream, so stream
+ * order and graph capture are kept; see clamp_prior_concurrent).  By default it does for
+ * problems of at most 2^25 voxel-looks (n L), where the prior's few waves of tensor-core
+ * CTAs leave SMs that the FFT passes fill, and not above that, where both saturate the
+ * GPU and only contend.  These flags force either schedule (at most one may be set). */
+#define CLAMP_FLAG_PRIOR_CONCURRENT 0x8
+#define CLAMP_FLAG_PRIOR_SERIAL 0x10
 
 /* Problem and iteration parameters (Sec. II-B, Sec. III, Sec. IV-A). */
 typedef struct clamp_params {
@@ -208,16 +217,23 @@ size_t clamp_denoise_workspace_size(const clamp_denoiser* den, int32_t nx, int32
 /* Scratch bytes clamp_iterate needs (forward-agent scratch plus the denoiser's). */
 size_t clamp_iterate_workspace_size(const clamp_params* p, const clamp_denoiser* den);
 
+/* 1 if iterations with these parameters run the prior agent concurrently with the forward
+ * agents (CLAMP_FLAG_PRIOR_* and the default size rule above), else 0; -1 for invalid
+ * parameters.  Host-only.  A call made while `stream` is being captured, before the
+ * library created its side stream on this host thread and device, runs serially. */
+int32_t clamp_prior_concurrent(const clamp_params* p);
+
 /* Runs `iters` CLAMP iterations k = k_first, ..., k_first + iters - 1 (the loop body of
  * Alg. 2: all forward agents, the prior agent on w_{L+1}, the MACE step) on a
  * caller-held state, so a run can be resumed from {mu, r, w, k}.
  * mu: complex [L][n], r, w: float [L+1][n] (in/out); wbar: float [n] out (sum_j ups_j w_j
  * after the last step, the Alg. 2 output).  ce_out, mu_out: optional DEVICE double
  * arrays [iters] receiving the convergence error and mu-residual of each iteration.
- * events: optional array of 4 * iters cudaEvent_t handles recorded on `stream` per
- * iteration: before the forward agents, after their line search, after the prior
- * agent, after the MACE pass (for timing).  Stream-ordered, no host synchronisation
- * after argument checks. */
+ * events: optional array of 4 * iters cudaEvent_t handles recorded per iteration: before
+ * the forward agents (and the fork of the prior), after their line search, after the
+ * prior agent, after the MACE pass (for timing).  All are recorded on `stream` except the
+ * third under the concurrent schedule, which is recorded on the side stream the prior
+ * runs on.  Stream-ordered, no host synchronisation after argument checks. */
 clamp_status clamp_iterate(const clamp_params* p, int32_t k_first, int32_t iters, const float* y,
                            const float* pupil, const float* window, const clamp_denoiser* den,
                            float* mu, float* r, float* w, float* wbar, double* ce_out,

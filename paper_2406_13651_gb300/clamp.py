@@ -24,6 +24,8 @@ STATUS = {0: "CLAMP_OK", 1: "CLAMP_EINVAL", 2: "CLAMP_ENOMEM", 3: "CLAMP_ECUDA",
 FLAG_MU_INIT_NO_ALPHA = 0x1
 FLAG_EXACT_PROX = 0x2
 FLAG_NO_APERTURE = 0x4
+FLAG_PRIOR_CONCURRENT = 0x8
+FLAG_PRIOR_SERIAL = 0x10
 DENOISER_FP32 = 0
 DENOISER_BF16 = 1
 
@@ -41,7 +43,7 @@ EXPORTS = [
     "clamp_unet_workspace_size", "clamp_unet_forward", "clamp_unet_backward", "clamp_unet_adam",
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
     "clamp_point_cloud_workspace_size", "clamp_point_cloud_metrics", "clamp_denoiser_create_unet",
-    "clamp_selftest_bounded_wait",
+    "clamp_selftest_bounded_wait", "clamp_prior_concurrent",
 ]
 
 
@@ -92,6 +94,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_version": (ctypes.c_char_p, []),
         "clamp_supported_length": (I, [I]),
         "clamp_check_params": (I, [PP]),
+        "clamp_prior_concurrent": (I, [PP]),
         "clamp_workspace_size": (S, [PP]),
         "clamp_reconstruct_workspace_size": (S, [PP, P]),
         "clamp_fft3": (I, [I, I, I, I, P, P, I, P]),
@@ -340,6 +343,14 @@ def iterate_workspace(p: Params, den: Denoiser):
     if n == 0:
         _check(load().clamp_check_params(ctypes.byref(p)), "clamp_iterate_workspace_size")
     return _ws(n)
+
+
+def prior_concurrent(p: Params) -> bool:
+    """Whether iterations with these parameters run the prior agent beside the forward agents."""
+    v = load().clamp_prior_concurrent(ctypes.byref(p))
+    if v < 0:
+        raise ClampError(1, "clamp_prior_concurrent", load().clamp_last_error().decode())
+    return bool(v)
 
 
 def iterate(p: Params, k_first: int, iters: int, y, pupil, window, den: Denoiser, mu, r, w, wbar, ce_out=None,

@@ -89,7 +89,21 @@ extern "C" clamp_status clamp_check_params(const clamp_params* p) {
   if (p->k0 < 0) return api_fail(CLAMP_EINVAL, "k0 must be >= 0");
   if (!(p->tol >= 0.0)) return api_fail(CLAMP_EINVAL, "tol must be >= 0");
   if (p->init_mu_steps < 0 || p->init_mu_steps > 1000) return api_fail(CLAMP_EINVAL, "init_mu_steps must be in [0, 1000]");
+  if ((p->flags & CLAMP_FLAG_PRIOR_CONCURRENT) && (p->flags & CLAMP_FLAG_PRIOR_SERIAL))
+    return api_fail(CLAMP_EINVAL, "CLAMP_FLAG_PRIOR_CONCURRENT and CLAMP_FLAG_PRIOR_SERIAL are exclusive");
   return CLAMP_OK;
+}
+
+// The prior agent's schedule (the size rule and flags documented with CLAMP_FLAG_PRIOR_*).
+static bool prior_concurrent(const clamp_params* p) {
+  if (p->flags & CLAMP_FLAG_PRIOR_CONCURRENT) return true;
+  if (p->flags & CLAMP_FLAG_PRIOR_SERIAL) return false;
+  return (long long)p->nx * p->ny * p->nz * p->looks <= (1LL << 25);
+}
+
+extern "C" int32_t clamp_prior_concurrent(const clamp_params* p) {
+  if (clamp_check_params(p) != CLAMP_OK) return -1;
+  return prior_concurrent(p) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------- workspace layout
@@ -574,6 +588,37 @@ extern "C" size_t clamp_iterate_workspace_size(const clamp_params* p, const clam
   return iterate_ws_bytes(p, den);
 }
 
+// The prior agent's side stream and its fork/join events: one set per host thread and
+// device, created on first use outside stream capture (so no two callers, and no capture
+// on another thread, share them); nullptr means run serially.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
+static SideStream* side_stream(cudaStream_t st) {
+  thread_local SideStream tab[32];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 32) return nullptr;
+  SideStream& ss = tab[dev];
+  if (!ss.s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return nullptr;
+    SideStream fresh;
+    if (cudaStreamCreateWithFlags(&fresh.s, cudaStreamNonBlocking) == cudaSuccess &&
+        cudaEventCreateWithFlags(&fresh.fork, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&fresh.join, cudaEventDisableTiming) == cudaSuccess) {
+      ss = fresh;
+    } else {   // all or nothing
+      if (fresh.join) cudaEventDestroy(fresh.join);
+      if (fresh.fork) cudaEventDestroy(fresh.fork);
+      if (fresh.s) cudaStreamDestroy(fresh.s);
+      cudaGetLastError();
+      return nullptr;
+    }
+  }
+  return &ss;
+}
+
 // One to many loop bodies of Alg. 2 on the state (mu, r, w); ws = agent scratch then denoiser scratch.
 static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_first, int iters, const float* y,
                                  const float* pupil, const float* window, const clamp_denoiser* den, float2* mu,
@@ -584,9 +629,21 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
   const long long n = d.g.n;
   const bool noap = (p->flags & CLAMP_FLAG_NO_APERTURE) != 0;
   if (noap && iters > 0) API_TRY(ablation_prepare(d, y, al, ws, st));
+  // concurrent schedule: the prior agent forks off `st` after the previous MACE pass and
+  // the MACE pass joins it; within the iteration it shares no state with the forward agents
+  SideStream* ss = prior_concurrent(p) ? side_stream(st) : nullptr;
   for (int it = 0; it < iters; ++it) {
     const int k = k_first + it;
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 0], st), "event");
+    if (ss) {
+      API_CUDA(cudaEventRecord(ss->fork, st), "event");
+      API_CUDA(cudaStreamWaitEvent(ss->s, ss->fork, 0), "event");
+      API_CUDA(denoise_apply(den, w + (long long)p->looks * n, r + (long long)p->looks * n, p->nx, p->ny, p->nz,
+                             dws, at<int>(ws, al.err), ss->s),
+               "denoiser");
+      if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 2], ss->s), "event");
+      API_CUDA(cudaEventRecord(ss->join, ss->s), "event");
+    }
     if (noap) {
       if (mu_out) API_CUDA(cudaMemsetAsync(mu_out + it, 0, sizeof(double), st), "mu residual");
     } else {
@@ -594,10 +651,14 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
       if (mu_out) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_out + it, st), "mu residual");
     }
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 1], st), "event");
-    API_CUDA(denoise_apply(den, w + (long long)p->looks * n, r + (long long)p->looks * n, p->nx, p->ny, p->nz, dws,
-                           at<int>(ws, al.err), st),
-             "denoiser");
-    if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 2], st), "event");
+    if (ss) {
+      API_CUDA(cudaStreamWaitEvent(st, ss->join, 0), "event");
+    } else {
+      API_CUDA(denoise_apply(den, w + (long long)p->looks * n, r + (long long)p->looks * n, p->nx, p->ny, p->nz,
+                             dws, at<int>(ws, al.err), st),
+               "denoiser");
+      if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 2], st), "event");
+    }
     PassC c = passc_args(p, d, al, ws, mu, r, w, wbar, k);
     API_CUDA(launch_pass_c_fused(d.g, c, st), "fused prox + MACE pass");
     if (ce_out) API_CUDA(launch_ce_final(c.part_num, c.part_den, al.nbc, ce_out + it, st), "CE residual");

@@ -74,3 +74,22 @@ def test_null_pointers_rejected_without_launch(lib):
     assert st == 1
     st = lib.clamp_fft3(48, 32, 16, 1, 1, 1, 0, None)
     assert st == 7
+
+
+def test_prior_schedule_rule(lib):
+    """The prior agent runs beside the forward agents up to 2^25 voxel-looks unless a flag
+    forces a schedule; both flags together are rejected."""
+    from paper_2406_13651_gb300 import clamp
+    small = clamp.make_params(128, 128, 64, 16, 1e-3, 1e-4)          # 2^24 voxel-looks
+    edge = clamp.make_params(128, 128, 64, 32, 1e-3, 1e-4)           # 2^25
+    large = clamp.make_params(256, 256, 128, 32, 1e-3, 1e-4)         # 2^28
+    assert lib.clamp_prior_concurrent(ctypes.byref(small)) == 1
+    assert lib.clamp_prior_concurrent(ctypes.byref(edge)) == 1
+    assert lib.clamp_prior_concurrent(ctypes.byref(large)) == 0
+    large.flags = clamp.FLAG_PRIOR_CONCURRENT
+    assert lib.clamp_prior_concurrent(ctypes.byref(large)) == 1
+    small.flags = clamp.FLAG_PRIOR_SERIAL
+    assert lib.clamp_prior_concurrent(ctypes.byref(small)) == 0
+    small.flags = clamp.FLAG_PRIOR_SERIAL | clamp.FLAG_PRIOR_CONCURRENT
+    assert lib.clamp_prior_concurrent(ctypes.byref(small)) == -1
+    assert lib.clamp_check_params(ctypes.byref(small)) == 1

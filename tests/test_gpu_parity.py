@@ -369,3 +369,19 @@ def test_full_size_forward_agent_and_mace(C):
         ref = O.denoise_cnn(st.w[wl.looks, zl:zh, yl:yh, xl:xh], wl.denoiser["weights"], wl.denoiser["biases"])
         ref = ref[z0 - zl:z0 - zl + 8, y0 - yl:y0 - yl + 16, x0 - xl:x0 - xl + 16]
         assert rel(got_all[z0:z0 + 8, y0:y0 + 16, x0:x0 + 16], ref) < 1e-5, (z0, y0, x0)
+
+
+def test_prior_schedules_give_identical_results(C):
+    """The prior agent beside the forward agents (second stream) or after them: the same
+    kernels on the same inputs, so the reconstructions agree bit for bit."""
+    wl, a, y32, y64 = problem("cfg1", seed=6, iters=5)
+    ws_, bs_ = I.cnn_weights(5, 32, seed=6)
+    den = C.Denoiser.from_desc({"kind": "cnn", "weights": ws_, "biases": bs_, "dtype": "fp32"})
+    out = {}
+    for name, flag in (("serial", C.FLAG_PRIOR_SERIAL), ("concurrent", C.FLAG_PRIOR_CONCURRENT)):
+        p = C.make_params(wl.nx, wl.ny, wl.nz, wl.looks, wl.noise_var, wl.prox_var, max_iters=5, flags=flag)
+        assert C.prior_concurrent(p) == (name == "concurrent")
+        res = C.reconstruct(p, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), den)
+        out[name] = (res.r.cpu().numpy(), np.asarray(res.ce_hist))
+    assert np.array_equal(out["serial"][0], out["concurrent"][0])
+    assert np.array_equal(out["serial"][1], out["concurrent"][1])
