@@ -528,22 +528,30 @@ __global__ void __launch_bounds__(NT) k_conv_first(const float* __restrict__ in,
   float a0[C], a1[C];
 #pragma unroll
   for (int co = 0; co < C; ++co) a0[co] = a1[co] = s_b[co];
+  // taps in order tap = 9 dz + 3 dy + dx; dy and dx unrolled, so every shared-memory
+  // offset but the plane's is a constant
 #pragma unroll 1
-  for (int tap = 0; tap < 27; ++tap) {
-    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-    const float* col = s_in + (ty + dy) * CF_HX + tx + dx;
-    const float x0v = col[dz * CF_HY * CF_HX], x1v = col[(dz + 1) * CF_HY * CF_HX];
+  for (int dz = 0; dz < 3; ++dz) {
+    const float* pl = s_in + dz * CF_HY * CF_HX + ty * CF_HX + tx;
+    const float4* wz = s_w + dz * 9 * (C / 4);
 #pragma unroll
-    for (int q = 0; q < C / 4; ++q) {
-      const float4 wv = s_w[tap * (C / 4) + q];
-      a0[4 * q + 0] = fmaf(x0v, wv.x, a0[4 * q + 0]);
-      a0[4 * q + 1] = fmaf(x0v, wv.y, a0[4 * q + 1]);
-      a0[4 * q + 2] = fmaf(x0v, wv.z, a0[4 * q + 2]);
-      a0[4 * q + 3] = fmaf(x0v, wv.w, a0[4 * q + 3]);
-      a1[4 * q + 0] = fmaf(x1v, wv.x, a1[4 * q + 0]);
-      a1[4 * q + 1] = fmaf(x1v, wv.y, a1[4 * q + 1]);
-      a1[4 * q + 2] = fmaf(x1v, wv.z, a1[4 * q + 2]);
-      a1[4 * q + 3] = fmaf(x1v, wv.w, a1[4 * q + 3]);
+    for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const float x0v = pl[dy * CF_HX + dx], x1v = pl[CF_HY * CF_HX + dy * CF_HX + dx];
+#pragma unroll
+        for (int q = 0; q < C / 4; ++q) {
+          const float4 wv = wz[(dy * 3 + dx) * (C / 4) + q];
+          a0[4 * q + 0] = fmaf(x0v, wv.x, a0[4 * q + 0]);
+          a0[4 * q + 1] = fmaf(x0v, wv.y, a0[4 * q + 1]);
+          a0[4 * q + 2] = fmaf(x0v, wv.z, a0[4 * q + 2]);
+          a0[4 * q + 3] = fmaf(x0v, wv.w, a0[4 * q + 3]);
+          a1[4 * q + 0] = fmaf(x1v, wv.x, a1[4 * q + 0]);
+          a1[4 * q + 1] = fmaf(x1v, wv.y, a1[4 * q + 1]);
+          a1[4 * q + 2] = fmaf(x1v, wv.z, a1[4 * q + 2]);
+          a1[4 * q + 3] = fmaf(x1v, wv.w, a1[4 * q + 3]);
+        }
+      }
     }
   }
   const long long v = (long long)z0 * plane + (long long)y * nx + x;
@@ -584,13 +592,17 @@ __global__ void __launch_bounds__(CL_NT, 4) k_conv_last(const float4* __restrict
 #pragma unroll 1
   for (int g = 0; g < G; ++g) {
     __syncthreads();   // the previous group's reads of the halo are done
-    for (int e = tid; e < HV; e += CL_NT) {
-      const int xr = e % CL_HX, t = e / CL_HX;
-      const int yr = t % CL_HY, zr = t / CL_HY;
-      const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z0 + zr - 1;
-      const bool inb = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
-      const float4* src = inb ? &act[(long long)g * n + (long long)gz * plane + (long long)gy * nx + gx] : act;
-      cp_async16(&s_h[e], src, inb);
+    // one warp per halo row (z, y), lanes along x: the row's index arithmetic once per row
+    for (int row = tid / 32; row < CL_HZ * CL_HY; row += CL_NT / 32) {
+      const int yr = row % CL_HY, zr = row / CL_HY;
+      const int gy = y0 + yr - 1, gz = z0 + zr - 1;
+      const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+      const float4* rsrc = act + (long long)g * n + (long long)gz * plane + (long long)gy * nx;
+      for (int xr = tid % 32; xr < CL_HX; xr += 32) {
+        const int gx = x0 + xr - 1;
+        const bool inb = rin && gx >= 0 && gx < nx;
+        cp_async16(&s_h[row * CL_HX + xr], inb ? rsrc + gx : act, inb);
+      }
     }
     cp_async_wait_all();
     __syncthreads();
