@@ -37,7 +37,7 @@ FP32_LANES_PER_SM = 128
 # dram__bytes_read.sum + dram__bytes_write.sum over the five kernels of one FP32 prior-agent
 # call (5 layers x 32 channels, 128x128x64), from the ncu capture summarised in
 # profiles/prior_agent_traffic_128x128x64.md
-PRIOR_TRAFFIC_128 = 879_613_952
+PRIOR_TRAFFIC_128 = 879_373_824
 
 def parse():
     ap = argparse.ArgumentParser()
