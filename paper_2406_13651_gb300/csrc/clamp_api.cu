@@ -590,7 +590,9 @@ extern "C" size_t clamp_iterate_workspace_size(const clamp_params* p, const clam
 
 // The prior agent's side stream and its fork/join events: one set per host thread and
 // device, created on first use outside stream capture (so no two callers, and no capture
-// on another thread, share them); nullptr means run serially.
+// on another thread, share them) and kept for the thread's lifetime (three handles; no
+// destructor, which could run after the CUDA runtime has unloaded at process exit);
+// nullptr means run serially.
 struct SideStream {
   cudaStream_t s = nullptr;
   cudaEvent_t fork = nullptr, join = nullptr;
