@@ -39,6 +39,20 @@ FP32_LANES_PER_SM = 128
 # profiles/prior_agent_traffic_128x128x64.md
 PRIOR_TRAFFIC_128 = 879_373_824
 
+
+def phase_times(t01, t02, t03, concurrent: bool):
+    """Mean seconds of (forward agents, prior agent, MACE pass) per iteration from the
+    milliseconds from each iteration's first event e0 (before the forward agents and the
+    prior's fork) to e1 (after their line search), e2 (after the prior agent) and e3
+    (after the MACE pass).  Serial schedule: the phases follow one another.  Concurrent:
+    the prior's span runs from e0 on its own stream and the MACE pass starts when the
+    later branch ends."""
+    nit = len(t01)
+    agent = sum(t01) / nit / 1e3
+    if concurrent:
+        return agent, sum(t02) / nit / 1e3, sum(c - max(a, b) for a, b, c in zip(t01, t02, t03)) / nit / 1e3
+    return agent, sum(b - a for a, b in zip(t01, t02)) / nit / 1e3, sum(c - b for b, c in zip(t02, t03)) / nit / 1e3
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,17 +557,10 @@ def main():
     elapsed = t_start.elapsed_time(t_end) / 1e3
 
     def phases(evs, nit, conc):
-        """Per iteration: e0 before the forward agents (and the prior's fork), e1 after their
-        line search, e2 after the prior agent, e3 after the MACE pass.  Serial: the phases
-        follow one another.  Concurrent: the prior's span runs from e0 on its own stream and
-        the MACE pass starts when the later branch ends."""
         t01 = [evs[4 * i].elapsed_time(evs[4 * i + 1]) for i in range(nit)]
         t02 = [evs[4 * i].elapsed_time(evs[4 * i + 2]) for i in range(nit)]
         t03 = [evs[4 * i].elapsed_time(evs[4 * i + 3]) for i in range(nit)]
-        ag = sum(t01) / nit / 1e3
-        if conc:
-            return ag, sum(t02) / nit / 1e3, sum(c - max(a, b) for a, b, c in zip(t01, t02, t03)) / nit / 1e3
-        return ag, sum(b - a for a, b in zip(t01, t02)) / nit / 1e3, sum(c - b for b, c in zip(t02, t03)) / nit / 1e3
+        return phase_times(t01, t02, t03, conc)
 
     agent_span, prior_span, passc_span = phases(events, K, concurrent)
     # the rooflines use serial phase times (this run's own when it is serial)

@@ -68,3 +68,19 @@ def test_reference_arm_skips_other_ranks():
         warmup = 0
 
     assert bench.run_reference(A(), 1, 2) == 0     # rank 1 exits at once, without work
+
+
+def test_phase_times_serial_and_concurrent():
+    """The bench's per-phase arithmetic on synthetic event times (ms from each iteration's
+    first event): serial phases follow one another; under the concurrent schedule the
+    prior's span starts at e0 and the MACE pass waits for the later branch."""
+    import bench
+    # serial: agents 0.4, prior 1.2, MACE 0.15 ms
+    a, p, c = bench.phase_times([0.4, 0.4], [1.6, 1.6], [1.75, 1.75], False)
+    assert (round(a * 1e3, 9), round(p * 1e3, 9), round(c * 1e3, 9)) == (0.4, 1.2, 0.15)
+    # concurrent: agents end at 1.5, the prior at 1.54, MACE ends at 1.69 -> 0.15 after the prior
+    a, p, c = bench.phase_times([1.5], [1.54], [1.69], True)
+    assert (round(a * 1e3, 9), round(p * 1e3, 9), round(c * 1e3, 9)) == (1.5, 1.54, 0.15)
+    # concurrent with the agents finishing last: the MACE pass is timed from them
+    a, p, c = bench.phase_times([1.2], [0.9], [1.3], True)
+    assert round(c * 1e3, 9) == 0.1
