@@ -306,11 +306,11 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
 // staging unit is one (channel chunk, halo plane) step: the FP32 halo plane (2 channel
 // groups x 6 rows x 130 voxels), loaded into registers and written once as TF32 hi and lo
 // copies (split as in k_conv3_tc), and the hi/lo weights of the matching dz (cp.async),
-// about 68 KB at 32 channels; a
-// step's MMAs are those of one dz, in k_conv3_tc's order.  Each CTA stages, issues and
-// waits step by step as k_conv3_tc does per chunk, and with about 70 KB of shared memory
-// and 128 TMEM columns per CTA three CTAs share an SM, so one CTA's staging overlaps the
-// other CTAs' MMAs (k_conv3_tc's whole-chunk halo, hi and lo, leaves one CTA per SM).
+// about 68 KB at 32 channels.  A step's MMAs are those of one dz, in k_conv3_tc's order.
+// Each CTA stages, issues and waits step by step as k_conv3_tc does per chunk; with about
+// 70 KB of shared memory and 128 TMEM columns per CTA three CTAs share an SM, so one CTA's
+// staging overlaps the other CTAs' MMAs (k_conv3_tc's whole-chunk halo, hi and lo, leaves
+// one CTA per SM).
 template <int CIN, int NPAD>
 struct TcPlaneCfg {
   static constexpr int TY = 4, HY = TY + 2, MT = TY, CTAS = 3;
