@@ -69,3 +69,32 @@ def test_batch_rejects_bad_scene(C):
     with pytest.raises(C.ClampError):
         C.Batch([(p, y, torch.ones(32 * 48, device=dev), torch.ones(16, device=dev),
                   torch.empty(16 * 32 * 48, device=dev))], den)
+
+
+def test_batch_graph_with_concurrent_prior(C):
+    """Scenes whose prior agent runs on the side stream: with the side stream created
+    before capture (a reconstruction ran on this thread first) the fork and join become
+    edges of the captured graph, and the results equal single calls on the serial
+    schedule."""
+    den = C.Denoiser.gauss(0.8)
+    dev = torch.device("cuda")
+    scenes, serial = [], []
+    for sp in SPECS[:2]:
+        wl = I.batch_scene(sp)
+        a = O.aperture(wl.pupil, wl.window)
+        y32 = O.simulate_data(wl.r_true, wl.speckle, wl.noise, a, wl.noise_var).astype(np.complex64)
+        mk = lambda flag: C.make_params(wl.nx, wl.ny, wl.nz, wl.looks, wl.noise_var, wl.prox_var,
+                                        max_iters=wl.iters, flags=flag)
+        pc, ps = mk(C.FLAG_PRIOR_CONCURRENT), mk(C.FLAG_PRIOR_SERIAL)
+        assert C.prior_concurrent(pc) and not C.prior_concurrent(ps)
+        yd, pu, wi = (torch.from_numpy(v).to(dev) for v in (y32, wl.pupil, wl.window))
+        C.reconstruct(pc, yd, pu, wi, den)   # creates this thread's side stream outside capture
+        scenes.append((pc, yd, pu, wi, torch.empty((wl.nz, wl.ny, wl.nx), dtype=torch.float32, device=dev)))
+        serial.append(C.reconstruct(ps, yd, pu, wi, den))
+    batch = C.Batch(scenes, den)
+    batch.launch()
+    ce = batch.residuals()
+    for i, (p, yd, pu, wi, ro) in enumerate(scenes):
+        assert rel(ro.cpu().numpy(), serial[i].r.cpu().numpy()) < 1e-6, i
+        assert ce[i] == pytest.approx(serial[i].ce_hist[-1], rel=1e-6)
+    batch.close()
