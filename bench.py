@@ -38,6 +38,10 @@ FP32_LANES_PER_SM = 128
 # call (5 layers x 32 channels, 128x128x64), from the ncu capture summarised in
 # profiles/prior_agent_traffic_128x128x64.md
 PRIOR_TRAFFIC_128 = 879_373_824
+# the same for the forward-agent path of one iteration (five FFT passes and the fused prox /
+# Mann pass) at 128x128x64, L = 16, from the capture in
+# profiles/forward_agent_passes_128x128x64_L16.md
+AGENT_TRAFFIC_128 = 2_543_945_728
 
 
 def phase_times(t01, t02, t03, concurrent: bool):
@@ -654,9 +658,10 @@ def main():
     # forward-agent FFT + prox + Mann path: 136 B per voxel-look (two HBM passes per 3D FFT)
     agent_bytes = 136.0 * n * L
     agent_gbs = agent_bytes / (agent + passc) / 1e9
+    agent_measured = (wl.nx, wl.ny, wl.nz, L) == (128, 128, 64, 16)
     roof_agent = {"bound": "hbm", "kernel": "forward-agent FFT passes + line search + fused prox/Mann pass",
                   "achieved": agent_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": agent_gbs / hbm_peak,
-                  "traffic": None, "peak_source": hbm_src,
+                  "traffic": AGENT_TRAFFIC_128 if agent_measured else None, "peak_source": hbm_src,
                   "algorithmic": "136 B per voxel-look per iteration (two HBM passes per 3D FFT)"}
     if roofline is None:
         roofline = roof_agent
