@@ -38,6 +38,8 @@ Readings where the paper is silent or garbled (each is used below):
   R11 for a non-binary aperture, A^H A = F^H D(a^2) F and alpha = mean(a^2), which
       equals ||a||_1 / n when a is binary (Sec. III-B).
   R12 the speckle-average initial image is floored at 1e-12 max to keep r > 0.
+  R13 the l2,1 comparison prior (Sec. IV) groups the voxels of each range bin: the norm is
+      sum_z ||r_z||_2 over the (y, x) planes r_z (l2 in cross-range, l1 in range).
 """
 from __future__ import annotations
 
@@ -52,7 +54,7 @@ __all__ = [
     "line_search_gamma", "beta_k", "prox_quadratic", "forward_agent", "gauss_kernel1d",
     "denoise_gauss", "conv3d", "denoise_cnn", "mace_update", "convergence_error",
     "mu_residual", "reconstruct", "OracleState", "em_surrogate", "exact_nll",
-    "exact_posterior", "cubic_prox", "psnr", "cubic_prox_field", "no_aperture_mu",
+    "exact_posterior", "cubic_prox", "psnr", "cubic_prox_field", "no_aperture_mu", "denoise_l21",
 ]
 
 
@@ -269,9 +271,25 @@ def denoise_cnn(x: np.ndarray, weights, biases, bf16: bool = False) -> np.ndarra
     return np.asarray(x, dtype=np.float64) + h[0]
 
 
+def denoise_l21(x: np.ndarray, lam: float) -> np.ndarray:
+    """Prior agent of the l2,1-regularised comparison method (Sec. IV: l2 across cross-range,
+    l1 across range): the proximal map of lam * sum_z ||r_z||_2, where r_z is the (y, x)
+    cross-range plane of range bin z.  Each plane's group is shrunk in l2 norm by lam:
+    r_z = max(0, 1 - lam / ||x_z||) x_z (reading R13)."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros_like(x)
+    for z in range(x.shape[0]):
+        nrm = math.sqrt(float(np.sum(x[z] * x[z])))
+        if nrm > lam:
+            out[z] = (1.0 - lam / nrm) * x[z]
+    return out
+
+
 def apply_prior(x: np.ndarray, den: dict) -> np.ndarray:
     if den["kind"] == "gauss":
         return denoise_gauss(x, den["sigma"])
+    if den["kind"] == "l21":
+        return denoise_l21(x, den["lam"])
     if den["kind"] == "cnn":
         return denoise_cnn(x, den["weights"], den["biases"], bf16=den.get("dtype") == "bf16")
     if den["kind"] == "identity":

@@ -67,6 +67,8 @@ def test_forward_bf16(C):
     assert rel(got, ref) < 2e-2         # against exact arithmetic
 
 
+# BF16 against exact FP64 gradients: operand rounding alone moves them by up to about
+# 2.4e-2 on this problem (tests/test_bf16_tolerances.py measures it on the CPU)
 @pytest.mark.parametrize("dtype,tol", [("fp32", 1e-4), ("bf16", 3e-2)])
 def test_loss_and_gradients(C, dtype, tol):
     ch = (4, 8, 16)
@@ -152,7 +154,9 @@ def test_normalize_and_warm_map(C):
     assert rel(got, ref) < 1e-5
 
 
-@pytest.mark.parametrize("dtype,oracle_bf16,tol", [("fp32", False, 2e-5), ("bf16", True, 3e-2)])
+# BF16: FP32 against FP64 accumulation with the same rounding points differs by about 8e-3
+# at this size (rounding flips grow through the layers; tests/test_bf16_tolerances.py)
+@pytest.mark.parametrize("dtype,oracle_bf16,tol", [("fp32", False, 2e-5), ("bf16", True, 2e-2)])
 def test_fullsize_forward_crop(C, dtype, oracle_bf16, tol):
     """16/32/64 network at 256x256x128 (the warm start's inference size) on one sample:
     an interior crop of the output against the oracle on the crop plus a 32-voxel halo
@@ -171,4 +175,5 @@ def test_fullsize_forward_crop(C, dtype, oracle_bf16, tol):
     crop = xd[z0 - h:z0 + s + h, y0 - h:y0 + s + h, x0 - h:x0 + s + h].cpu().numpy().astype(np.float64)
     ref = U.forward(p.astype(np.float64), crop[None], ch, bf16=oracle_bf16).numpy()[0][h:-h, h:-h, h:-h]
     g = got[z0:z0 + s, y0:y0 + s, x0:x0 + s].cpu().numpy()
+    print(f"full-size crop {dtype}: rel-L2 {rel(g, ref):.3e}")
     assert rel(g, ref) < tol
