@@ -33,7 +33,7 @@ EXPORTS = [
     "clamp_last_error", "clamp_version", "clamp_supported_length", "clamp_check_params",
     "clamp_workspace_size", "clamp_reconstruct_workspace_size", "clamp_fft3", "clamp_simulate",
     "clamp_init", "clamp_forward_prox", "clamp_denoise", "clamp_mace_step",
-    "clamp_denoiser_create_gauss", "clamp_denoiser_create_cnn", "clamp_denoiser_destroy",
+    "clamp_denoiser_create_gauss", "clamp_denoiser_create_cnn", "clamp_denoiser_destroy", "clamp_denoiser_create_l21",
     "clamp_denoise_workspace_size", "clamp_reconstruct", "clamp_reconstruct_host", "clamp_release_cache",
     "clamp_iterate", "clamp_iterate_workspace_size", "clamp_mace_step_noalloc",
     "clamp_tc_gemm_bf16", "clamp_tc_gemm_tf32x3",
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_denoise": (I, [P, P, P, I, I, I, P, S, P]),
         "clamp_mace_step": (I, [PP, P, P, P, P, P, S, P]),
         "clamp_denoiser_create_gauss": (I, [ctypes.c_float, ctypes.POINTER(P)]),
+        "clamp_denoiser_create_l21": (I, [ctypes.c_float, ctypes.POINTER(P)]),
         "clamp_denoiser_create_cnn": (I, [I, I, I, P, P, ctypes.POINTER(P)]),
         "clamp_denoiser_destroy": (V, [P]),
         "clamp_denoise_workspace_size": (S, [P, I, I, I]),
@@ -189,6 +190,13 @@ class Denoiser:
         return cls(h.value, {"kind": "gauss", "sigma": sigma})
 
     @classmethod
+    def l21(cls, lam: float) -> "Denoiser":
+        """The l2,1 prior agent: each range bin's cross-range plane shrunk in l2 norm by lam."""
+        h = ctypes.c_void_p()
+        _check(load().clamp_denoiser_create_l21(lam, ctypes.byref(h)), "clamp_denoiser_create_l21")
+        return cls(h.value, {"kind": "l21", "lam": lam})
+
+    @classmethod
     def cnn(cls, weights, biases, dtype: str = "fp32") -> "Denoiser":
         layers = len(weights)
         channels = int(weights[0].shape[0])
@@ -214,6 +222,8 @@ class Denoiser:
     def from_desc(cls, desc: dict) -> "Denoiser":
         if desc["kind"] == "gauss":
             return cls.gauss(desc["sigma"])
+        if desc["kind"] == "l21":
+            return cls.l21(desc["lam"])
         if desc["kind"] == "unet":
             net = UNet(*desc["channels"], params=desc["params"], dtype=desc.get("dtype", "bf16"))
             return cls.unet(net, desc.get("floor", 1e-3))

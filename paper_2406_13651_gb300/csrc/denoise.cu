@@ -217,12 +217,88 @@ static cudaError_t run_conv_c1(const float* in, int cin, float* out, const float
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- l2,1 prior agent
+
+// Prox of lam * sum_z ||r_z||_2 over the (y, x) planes r_z of the range bins (the l2,1
+// comparison prior of Sec. IV): r_z = max(0, 1 - lam / ||x_z||) x_z.  Pass 1 writes one
+// FP64 sum of squares per (CTA, plane); pass 2 has every CTA of a plane add its plane's
+// partials in the same fixed order, so all CTAs apply the same factor.  Both passes read
+// the plane as float4 (nx is a multiple of 16, so a plane is a whole number of float4).
+constexpr int L21_PER = 4;   // float4 per thread per CTA
+
+__global__ void __launch_bounds__(NT) k_l21_norm(const float4* __restrict__ x, long long plane4,
+                                                 double* __restrict__ part) {
+  const int z = blockIdx.y;
+  const float4* xz = x + (long long)z * plane4;
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < L21_PER; ++k) {
+    const long long i = ((long long)blockIdx.x * L21_PER + k) * NT + threadIdx.x;
+    if (i < plane4) {
+      const float4 v = xz[i];
+      acc = fmaf(v.x, v.x, fmaf(v.y, v.y, fmaf(v.z, v.z, fmaf(v.w, v.w, acc))));
+    }
+  }
+  __shared__ double red[NT / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < NT / 32; ++w) s += red[w];
+    part[(long long)z * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(NT) k_l21_shrink(const float4* __restrict__ x, long long plane4,
+                                                   const double* __restrict__ part, double lam,
+                                                   float4* __restrict__ out) {
+  const int z = blockIdx.y;
+  __shared__ float s_fac;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += part[(long long)z * gridDim.x + b];
+    const double nrm = sqrt(s);
+    s_fac = nrm > lam ? (float)(1.0 - lam / nrm) : 0.0f;
+  }
+  __syncthreads();
+  const float f = s_fac;
+  const float4* xz = x + (long long)z * plane4;
+  float4* oz = out + (long long)z * plane4;
+#pragma unroll
+  for (int k = 0; k < L21_PER; ++k) {
+    const long long i = ((long long)blockIdx.x * L21_PER + k) * NT + threadIdx.x;
+    if (i < plane4) {
+      const float4 v = xz[i];
+      oz[i] = make_float4(f * v.x, f * v.y, f * v.z, f * v.w);
+    }
+  }
+}
+
+static int l21_blocks_per_plane(int nx, int ny) {
+  const long long plane4 = (long long)nx * ny / 4;
+  return (int)((plane4 + (long long)NT * L21_PER - 1) / ((long long)NT * L21_PER));
+}
+
+static cudaError_t run_l21(const float* in, float* out, double lam, int nx, int ny, int nz, void* ws,
+                           cudaStream_t st) {
+  const long long plane4 = (long long)nx * ny / 4;
+  const dim3 grid(l21_blocks_per_plane(nx, ny), nz);
+  double* part = static_cast<double*>(ws);
+  k_l21_norm<<<grid, NT, 0, st>>>(reinterpret_cast<const float4*>(in), plane4, part);
+  k_l21_shrink<<<grid, NT, 0, st>>>(reinterpret_cast<const float4*>(in), plane4, part, lam,
+                                    reinterpret_cast<float4*>(out));
+  return cudaGetLastError();
+}
+
 }  // namespace clamp
 
 using namespace clamp;
 
 size_t denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz) {
   if (d && d->kind == 2) return clamp_unet_workspace_size(d->unet, 1, nx, ny, nz, 0);
+  if (d && d->kind == 3) return (((size_t)l21_blocks_per_plane(nx, ny) * nz * sizeof(double)) + 255) & ~(size_t)255;
   if (!d || d->kind != 1) return 0;
   if (d->dtype == CLAMP_DENOISER_BF16) return tc_denoise_ws_bytes(d, nx, ny, nz);
   const size_t n = (size_t)nx * ny * nz;
@@ -245,6 +321,7 @@ cudaError_t denoise_apply(const clamp_denoiser* d, const float* in, float* out, 
                                                  denoise_ws_bytes(d, nx, ny, nz), st);
     return s == CLAMP_OK ? cudaSuccess : cudaErrorInvalidValue;
   }
+  if (d->kind == 3) return run_l21(in, out, (double)d->lam, nx, ny, nz, ws, st);
   // tensor-core path (BF16, or FP32 through TF32x3) when the volume fits its tiling
   if (tc_denoiser_supports(d, nx, ny, nz)) return tc_denoise_apply(d, in, out, nx, ny, nz, ws, err, st);
   if (d->dtype == CLAMP_DENOISER_BF16) return cudaErrorInvalidValue;
@@ -281,6 +358,17 @@ extern "C" clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser*
   const double e = exp(-1.0 / (2.0 * (double)sigma * sigma));
   d->g0 = (float)(e / (1.0 + 2.0 * e));
   d->g1 = (float)(1.0 / (1.0 + 2.0 * e));
+  cudaGetDevice(&d->dev);
+  *out = d;
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_denoiser_create_l21(float lam, clamp_denoiser** out) {
+  if (!out) return CLAMP_EINVAL;
+  if (!(lam >= 0.f) || !isfinite(lam)) return CLAMP_EINVAL;
+  clamp_denoiser* d = new clamp_denoiser();
+  d->kind = 3;
+  d->lam = lam;
   cudaGetDevice(&d->dev);
   *out = d;
   return CLAMP_OK;

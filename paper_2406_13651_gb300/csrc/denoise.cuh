@@ -10,7 +10,7 @@
 struct clamp_unet;
 
 struct clamp_denoiser {
-  int kind = 0;              // 0 = Gaussian smoother, 1 = residual CNN, 2 = U-Net prior (borrowed net)
+  int kind = 0;              // 0 = Gaussian smoother, 1 = residual CNN, 2 = U-Net prior (borrowed net), 3 = l2,1 prox
   float g0 = 0.f, g1 = 1.f;  // Gaussian taps [g0, g1, g0]
   int layers = 0, channels = 0, dtype = 0;
   int dev = -1;
@@ -20,6 +20,7 @@ struct clamp_denoiser {
   std::vector<void*> w16;     // per layer, device, tensor-core packed weights (layers >= 1)
   clamp_unet* unet = nullptr; // kind 2: the caller's network (not owned)
   float floor_rel = 1e-3f;    // kind 2: output floor in units of the input's column energy
+  float lam = 0.f;            // kind 3: l2,1 weight
 };
 
 size_t denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz);

@@ -93,3 +93,11 @@ def test_prior_schedule_rule(lib):
     small.flags = clamp.FLAG_PRIOR_SERIAL | clamp.FLAG_PRIOR_CONCURRENT
     assert lib.clamp_prior_concurrent(ctypes.byref(small)) == -1
     assert lib.clamp_check_params(ctypes.byref(small)) == 1
+
+
+def test_l21_weight_validation(lib):
+    """The l2,1 prior agent rejects a negative or non-finite weight before touching the GPU."""
+    h = ctypes.c_void_p()
+    for lam in (-1.0, float("nan"), float("inf")):
+        assert lib.clamp_denoiser_create_l21(lam, ctypes.byref(h)) == 1
+    assert lib.clamp_denoiser_create_l21(1.0, None) == 1
