@@ -174,12 +174,21 @@ clamp_status clamp_mace_step(const clamp_params* p, const float* r, float* w, fl
  * Calls no cudaMalloc/cudaFree.  All calls share the array: calls that overlap on
  * the GPU (other streams, other threads) race and must be serialised by the caller.
  * Returns CLAMP_ENOMEM if the partial sums would not fit the array (never for the
- * volumes clamp_check_params accepts: at most 1216 reduction blocks x 16 bytes). */
+ * volumes clamp_check_params accepts: at most 1216 reduction blocks x 16 bytes).
+ * The array's address is cached per device ordinal: after cudaDeviceReset, call
+ * clamp_release_cache() before the next call so that it is looked up again. */
 clamp_status clamp_mace_step_noalloc(const clamp_params* p, const float* r, float* w, float* wbar,
                                      double* ce_residual, void* stream);
 
 /* Prior agents. */
 clamp_status clamp_denoiser_create_gauss(float sigma, clamp_denoiser** out);
+/* The l2,1 prior agent of the paper's comparison method (Sec. IV: "l2-regularization in
+ * cross-range and l1-regularization in range"): the proximal map of lam * sum_z ||r_z||_2,
+ * r_z the (y, x) plane of range bin z, i.e. each plane shrunk in l2 norm by lam:
+ * H(w)_z = max(0, 1 - lam / ||w_z||) w_z.  The plane norms are FP64 sums.  lam >= 0
+ * (lam = 0 is the identity).  Workspace: clamp_denoise_workspace_size bytes (one FP64
+ * partial sum per CTA and plane); in == out is allowed. */
+clamp_status clamp_denoiser_create_l21(float lam, clamp_denoiser** out);
 /* Residual CNN H(x) = x + CNN(x), 3x3x3 convs, zero padding; layer i maps
  * c_in -> c_out (1 -> C -> ... -> C -> 1), ReLU after every layer but the last.
  * weights_host: all layers' [c_out][c_in][3][3][3] float32 concatenated;
@@ -253,7 +262,8 @@ clamp_status clamp_reconstruct(const clamp_params* p, const float* y, const floa
 
 /* Same on HOST buffers (pageable or pinned): copies y, pupil, window and r_init to
  * the device, reconstructs, copies r_out back and synchronises.  Device scratch is
- * kept in a per-device cache between calls (clamp_release_cache frees it). */
+ * kept in a per-device cache between calls (clamp_release_cache frees it;
+ * clamp_release_cache also forgets the device addresses clamp_mace_step_noalloc caches). */
 clamp_status clamp_reconstruct_host(const clamp_params* p, const float* y_host,
                                     const float* pupil_host, const float* window_host,
                                     const clamp_denoiser* den, const float* r_init_host,
@@ -307,8 +317,8 @@ clamp_status clamp_batch_residuals(clamp_batch* b, void* stream, double* ce);
 void clamp_batch_destroy(clamp_batch* b);
 
 
-/* The initial image of Alg. 2 alone: r0 = (1/L) sum_l |A^H y_l / alpha|^2 (the speckle
- * average; Sec. IV-A), floored at 1e-12 of its maximum as the initialisation floors it.
+/* The initial image of Alg. 2 alone: r0 = (1/L) sum_l |A^H y_l|^2 (the speckle average;
+ * Sec. IV-A), floored at 1e-12 of its maximum as the initialisation floors it.
  * r0: device float [n].  ws: at least clamp_workspace_size(p) bytes. */
 clamp_status clamp_speckle_average(const clamp_params* p, const float* y, const float* pupil, const float* window,
                                    float* r0, void* ws, size_t ws_bytes, void* stream);

@@ -837,6 +837,7 @@ extern "C" void clamp_release_cache(void) {
   }
   g_cache.clear();
   if (cur >= 0) cudaSetDevice(cur);
+  noalloc_forget();
 }
 
 extern "C" clamp_status clamp_reconstruct_host(const clamp_params* p, const float* y_host, const float* pupil_host,

@@ -7,6 +7,8 @@
 clamp_status api_fail(clamp_status s, const char* fmt, ...);
 // Per-device set-up (twiddle tables); idempotent.
 clamp_status api_ensure_device();
+// Forgets the per-device addresses of clamp_mace_step_noalloc's static scratch.
+void noalloc_forget();
 
 // Per-problem constants: geometry, alpha = mean(a^2), noise floor, FFT scales.
 struct ReconPlan {

@@ -14,8 +14,14 @@
 // library reserves its 32 KiB until the process exits.  In host code its name
 // only stands for the device object; the device address is obtained once per
 // device with cudaGetSymbolAddress (with that device current) and passed to
-// the kernels.
+// the kernels.  That lookup can load the library's device code, which a
+// stream being captured must not see: make the first call on each device
+// before any stream capture.  The address is cached per device ordinal; after
+// cudaDeviceReset the module is loaded again (possibly elsewhere), so a caller
+// that resets a device calls clamp_release_cache(), which forgets the cached
+// addresses, before the next call.
 #include "../../include/clamp.h"
+#include "clamp_internal.cuh"
 #include "clamp_kernels.cuh"
 
 #include <math.h>
@@ -53,16 +59,26 @@ cudaError_t noalloc_scratch(double** out) {
 
 }  // namespace
 
+// Forgets the cached device addresses (clamp_release_cache).
+void noalloc_forget() {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  g_noalloc_ptr.clear();
+}
+
 extern "C" clamp_status clamp_mace_step_noalloc(const clamp_params* p, const float* r, float* w, float* wbar,
                                                 double* ce_residual, void* stream) {
   clamp_status s = clamp_check_params(p);
   if (s != CLAMP_OK) return s;
-  if (!r || !w || !wbar) return CLAMP_EINVAL;
+  if (!r || !w || !wbar) return api_fail(CLAMP_EINVAL, "clamp_mace_step_noalloc: NULL array argument");
   const long long n = (long long)p->nx * p->ny * p->nz;
   const int nblk = clamp::passc_blocks(n);
-  if (2 * nblk > kNoAllocDoubles) return CLAMP_ENOMEM;  // the partials would not fit the static array
+  if (2 * nblk > kNoAllocDoubles)   // the partials would not fit the static array
+    return api_fail(CLAMP_ENOMEM, "clamp_mace_step_noalloc: %d reduction blocks exceed the %d-double static scratch",
+                    nblk, kNoAllocDoubles);
   double* scratch = nullptr;
-  if (noalloc_scratch(&scratch) != cudaSuccess) return CLAMP_ECUDA;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess)
+    return api_fail(CLAMP_ECUDA, "clamp_mace_step_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
   cudaStream_t st = (cudaStream_t)stream;
   clamp::Geom g{p->nx, p->ny, p->nz, p->looks, n};
   clamp::PassC c{};
@@ -77,8 +93,8 @@ extern "C" clamp_status clamp_mace_step_noalloc(const clamp_params* p, const flo
   c.part_num = scratch;
   c.part_den = scratch + nblk;
   c.err = nullptr;
-  if (clamp::launch_mace_only(g, c, st) != cudaSuccess) return CLAMP_ECUDA;
-  if (ce_residual && clamp::launch_ce_final(c.part_num, c.part_den, nblk, ce_residual, st) != cudaSuccess)
-    return CLAMP_ECUDA;
+  e = clamp::launch_mace_only(g, c, st);
+  if (e == cudaSuccess && ce_residual) e = clamp::launch_ce_final(c.part_num, c.part_den, nblk, ce_residual, st);
+  if (e != cudaSuccess) return api_fail(CLAMP_ECUDA, "clamp_mace_step_noalloc: launch: %s", cudaGetErrorString(e));
   return CLAMP_OK;
 }

@@ -35,7 +35,10 @@ def test_noalloc_mace_step_matches_allocating_step(lib, order):
     from paper_2406_13651_gb300 import clamp
     dev = torch.device("cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    shapes = [(16, 32, 64, 5), (32, 64, 128, 3)] if order == "first" else [(32, 64, 128, 3), (16, 32, 64, 5)]
+    # the last shape gives the most reduction blocks the step ever uses (1216), filling the array's cap
+    shapes = [(16, 32, 64, 5), (32, 64, 128, 3), (64, 128, 128, 2)]
+    if order == "second":
+        shapes = shapes[::-1]
     for call, (nz, ny, nx, L) in enumerate(shapes):
         rng = np.random.default_rng(100 + call)
         r = torch.from_numpy(rng.uniform(0.01, 1, (L + 1, nz, ny, nx)).astype(np.float32)).to(dev)
@@ -57,3 +60,27 @@ def test_noalloc_mace_step_matches_allocating_step(lib, order):
         assert _rel(w_new.cpu(), w_ref.cpu()) < 1e-6
         assert _rel(wbar_new.cpu(), wbar_ref.cpu()) < 1e-6
         assert ce_new.item() == pytest.approx(ce_ref.item(), rel=1e-6)
+
+
+def test_noalloc_mace_step_allocates_nothing(lib):
+    """After a first call on the device, further calls leave the device's free memory as it was."""
+    from paper_2406_13651_gb300 import clamp
+    dev = torch.device("cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    nz, ny, nx, L = 64, 128, 128, 2
+    rng = np.random.default_rng(7)
+    r = torch.from_numpy(rng.uniform(0.01, 1, (L + 1, nz, ny, nx)).astype(np.float32)).to(dev)
+    w = torch.from_numpy(rng.uniform(0.01, 1, (L + 1, nz, ny, nx)).astype(np.float32)).to(dev)
+    wbar = torch.empty((nz, ny, nx), dtype=torch.float32, device=dev)
+    ce = torch.zeros(1, dtype=torch.float64, device=dev)
+    p = clamp.make_params(nx, ny, nz, L, 1e-3, 1e-4)
+    assert lib.clamp_mace_step_noalloc(ctypes.byref(p), r.data_ptr(), w.data_ptr(), wbar.data_ptr(),
+                                       ce.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        assert lib.clamp_mace_step_noalloc(ctypes.byref(p), r.data_ptr(), w.data_ptr(), wbar.data_ptr(),
+                                           ce.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
