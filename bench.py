@@ -1,14 +1,16 @@
 #!/usr/bin/env python
 """CLAMP throughput benchmark: voxel-looks/s per MACE iteration on one GB300.
 
-Workload (default ``cfg2``): 128x128x64 complex64 volume, L = 16 looks, column-
-surface scene (reflectance U[0.2, 1]) with circular speckle per look, pupil
-radius 0.4 Nyquist, periodic Hann range window, 15 dB SNR, residual CNN prior
-(5 layers, 3x3x3, 32 channels, FP32).  A step is one CLAMP iteration (Alg. 2
-loop body): the forward FFT passes of all looks, the exact line search, the
-prior agent, and the fused prox + Mann pass.
+Workload (default ``cfg3``, the largest single-GPU configuration): 256x256x128
+complex64 volume, L = 32 looks, a scene of 3-6 planar facets with occlusion in front
+of a back plane (reflectance U[0.2, 1]), circular speckle per look, pupil radius 0.35
+Nyquist, periodic Hann range window, 10 dB SNR, residual CNN prior (8 layers, 3x3x3,
+48 channels, BF16 operands, FP32 accumulation).  A step is one CLAMP iteration (Alg. 2
+loop body): the forward agents of all looks (FFT passes, exact line search, prox), the
+prior agent, and the MACE step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl clamp|reference]
+                  [--workload cfg1|cfg2|cfg3|batch|warm]
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 (the only reference there is) on a bounded sample of the same workload.
@@ -33,16 +35,9 @@ UNIT = "voxel-looks/s"
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
-
-# dram__bytes_read.sum + dram__bytes_write.sum over the five kernels of one FP32 prior-agent
-# call (5 layers x 32 channels, 128x128x64), from the ncu capture summarised in
-# profiles/prior_agent_traffic_128x128x64.md
-PRIOR_TRAFFIC_128 = 879_373_824
-# the same for the forward-agent path of one iteration (five FFT passes and the fused prox /
-# Mann pass) at 128x128x64, L = 16, from the capture in
-# profiles/forward_agent_passes_128x128x64_L16.md
-AGENT_TRAFFIC_128 = 2_543_945_728
-
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch set, measured by ncu
+# on the current kernels, keyed by (workload, part); parts without a capture report null.
+TRAFFIC = {}
 
 def phase_times(t01, t02, t03, concurrent: bool):
     """Mean seconds of (forward agents, prior agent, MACE pass) per iteration from the
@@ -60,21 +55,14 @@ def phase_times(t01, t02, t03, concurrent: bool):
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="clamp", choices=["clamp", "reference"])
-    ap.add_argument("--workload", default="cfg2", choices=["cfg1", "cfg2", "cfg3", "batch", "warm"])
+    ap.add_argument("--workload", default="cfg3", choices=["cfg1", "cfg2", "cfg3", "batch", "warm"])
     ap.add_argument("--prior-schedule", choices=["auto", "concurrent", "serial"], default="auto",
                     help="prior agent beside the forward agents or after them (auto: the library's size rule)")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="skip the warm-start comparison (256x256x128, L=32) on the default line")
-    ap.add_argument("--probe", choices=["prior", "agent"], default=None,
-                    help="profiling driver: run only the prior agent (CNN, --probe-shape / --probe-dtype) or "
-                         "--steps iterations of --workload with a Gaussian prior")
-    ap.add_argument("--probe-shape", default="128,128,64", help="nx,ny,nz of the prior probe")
-    ap.add_argument("--probe-dtype", choices=["fp32", "bf16"], default="fp32",
-                    help="prior probe: fp32 = CNN 5 x 32 (TF32x3), bf16 = CNN 8 x 48")
-    ap.add_argument("--probe-variants", default="2,0,2,3,1", help="agent probe: FFT launch variants per pass")
     ap.add_argument("--batch-iters", type=int, default=10)
     ap.add_argument("--e2e-calls", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -377,6 +365,34 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def error_vs_oracle(C, wl, p, y, pupil, window, den) -> dict | None:
+    """Reconstruction error against the FP64 oracle's committed golden for this workload
+    (tests/golden/reconstruction_<workload>.npz, written by the oracle alone): the same
+    number of iterations from the same seeded draws, compared on the golden's region."""
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", f"reconstruction_{wl.name}.npz")
+    if not os.path.exists(path):
+        return None
+    g = np.load(path)
+    iters = int(g["iters"])
+    pe = C.make_params(p.nx, p.ny, p.nz, p.looks, p.noise_var, p.prox_var, max_iters=iters, flags=p.flags)
+    res = C.reconstruct(pe, y, pupil, window, den)
+    got = res.r.cpu().numpy().astype(np.float64)
+    region = "whole volume"
+    if "slab" in g.files:
+        z0, z1 = (int(v) for v in g["slab"])
+        got = got[z0:z1]
+        region = f"range planes {z0}..{z1 - 1} of the volume"
+    ref = g["wbar"].astype(np.float64)
+    return {"rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+            "max_abs_over_max": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+            "iterations": iters, "region": region,
+            "target": 1e-2 if wl.denoiser.get("dtype") == "bf16" else 1e-4,
+            "ce_last": {"gpu": float(res.ce_hist[iters - 1]), "oracle": float(g["ce_hist"][-1])},
+            "note": "the GPU's data are simulated on the device from the same draws as the oracle's "
+                    "(they differ by FP32 rounding of y)"}
+
+
 def warm_start_leg(dev) -> dict:
     """Time to CE residual 1e-3 from the speckle-average init and from the learned warm start
     (speckle average + U-Net inference + mapping included), same data, 256x256x128, L=32."""
@@ -384,65 +400,6 @@ def warm_start_leg(dev) -> dict:
     if not os.path.exists(Wm.WEIGHTS):
         return {"unavailable": "trained warm-start weights are missing"}
     return Wm.warm_workload_report(dev)
-
-
-def run_probe(args, local):
-    """Profiling drivers (one GPU, no timing contract): the prior agent alone on a seeded
-    random volume, or whole iterations (forward agents, a Gaussian prior, the fused
-    prox/Mann pass) on a workload's geometry with fixed FFT launch variants; prints the
-    mean time per repetition."""
-    import numpy as np
-    import torch
-    from paper_2406_13651_gb300 import build as B
-    from paper_2406_13651_gb300 import clamp as C
-    from paper_2406_13651_gb300 import inputs as I
-    torch.cuda.set_device(local)
-    B.build()
-    dev = torch.device("cuda", local)
-    reps = max(1, args.steps)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if args.probe == "prior":
-        nx, ny, nz = (int(v) for v in args.probe_shape.split(","))
-        layers, ch = (8, 48) if args.probe_dtype == "bf16" else (5, 32)
-        ws_, bs_ = I.cnn_weights(layers, ch, seed=1)
-        den = C.Denoiser.cnn(ws_, bs_, args.probe_dtype)
-        x = torch.rand((nz, ny, nx), generator=torch.Generator(device=dev).manual_seed(3), device=dev)
-        out = torch.empty_like(x)
-        wsb = C._ws(den.workspace_size(nx, ny, nz))
-        C.denoise(den, x, out, ws=wsb)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            C.denoise(den, x, out, ws=wsb)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        macs = 27 * (ch + (layers - 2) * ch * ch + ch)
-        print(json.dumps({"probe": "prior", "shape": [nx, ny, nz], "dtype": args.probe_dtype, "ms": ms,
-                          "tflops": 2 * macs * nx * ny * nz / ms / 1e9}), flush=True)
-        return 0
-    wl = I.make_workload(args.workload, seed=1, with_draws=False)
-    L = wl.looks
-    p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var)
-    pu, wi = torch.from_numpy(wl.pupil).to(dev), torch.from_numpy(wl.window).to(dev)
-    g = torch.Generator(device=dev).manual_seed(5)
-    shape = (L, wl.nz, wl.ny, wl.nx)
-    y = torch.complex(torch.randn(shape, generator=g, device=dev), torch.randn(shape, generator=g, device=dev))
-    mu, r, w = C.init(p, y, pu, wi)
-    wbar = torch.empty((wl.nz, wl.ny, wl.nx), device=dev)
-    den = C.Denoiser.gauss(0.8)   # a cheap prior: the iteration's other kernels are the subject
-    ws = C.iterate_workspace(p, den)
-    variants = [int(v) for v in args.probe_variants.split(",")]
-    C.autotune_set(p, variants)
-    torch.cuda.synchronize()
-    e0.record()
-    for k in range(reps):
-        C.iterate(p, k + 1, 1, y, pu, wi, den, mu, r, w, wbar, ws=ws)
-    e1.record()
-    torch.cuda.synchronize()
-    print(json.dumps({"probe": "agent", "workload": args.workload, "variants": variants,
-                      "ms": e0.elapsed_time(e1) / reps}), flush=True)
-    return 0
 
 
 def run_warm(args, rank, world, local):
@@ -481,8 +438,6 @@ def main():
         return run_batch(args, rank, world, local)
     if args.workload == "warm":
         return run_warm(args, rank, world, local)
-    if args.probe:
-        return run_probe(args, local)
 
     import numpy as np
     import torch
@@ -605,6 +560,7 @@ def main():
         e2e_value = job_throughput(n * L * e2e_iters, 1, world, e2e_t)
     h2d = L * n * 8 + wl.nx * wl.ny * 4 + wl.nz * 4
     d2h = n * 4 + 2 * 8 * e2e_iters
+    err_oracle = error_vs_oracle(C, wl, p, y, pupil, window, den) if rank == 0 else None
 
     if rank != 0:
         if world > 1:
@@ -638,12 +594,9 @@ def main():
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
         elif tensor_path:
             tf32x3_peak = bf16_peak * (1.1 / 2.25) / 3.0
-            # DRAM bytes of one prior-agent call (5 x 32 channels at 128x128x64) from one ncu
-            # capture of its five kernels; other sizes or networks have no capture
-            measured = (wl.nx, wl.ny, wl.nz, ch, len(wl.denoiser["weights"])) == (128, 128, 64, 32, 5)
             roofline = {"bound": "tensor", "kernel": "k_conv3_tc_plane<TF32x3> (+ SIMT first and last layers): the prior agent",
                         "achieved": cnn_tflops, "peak": tf32x3_peak, "unit": "TFLOP/s",
-                        "frac": cnn_tflops / tf32x3_peak, "traffic": PRIOR_TRAFFIC_128 if measured else None,
+                        "frac": cnn_tflops / tf32x3_peak, "traffic": TRAFFIC.get((wl.name, "prior")),
                         "peak_source": "measured bf16_tflops_sustained x nominal TF32/BF16 ratio (1.1/2.25), "
                                        "/3 for the three TF32 MMAs per FP32 product",
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
@@ -658,10 +611,9 @@ def main():
     # forward-agent FFT + prox + Mann path: 136 B per voxel-look (two HBM passes per 3D FFT)
     agent_bytes = 136.0 * n * L
     agent_gbs = agent_bytes / (agent + passc) / 1e9
-    agent_measured = (wl.nx, wl.ny, wl.nz, L) == (128, 128, 64, 16)
     roof_agent = {"bound": "hbm", "kernel": "forward-agent FFT passes + line search + fused prox/Mann pass",
                   "achieved": agent_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": agent_gbs / hbm_peak,
-                  "traffic": AGENT_TRAFFIC_128 if agent_measured else None, "peak_source": hbm_src,
+                  "traffic": TRAFFIC.get((wl.name, "agent")), "peak_source": hbm_src,
                   "algorithmic": "136 B per voxel-look per iteration (two HBM passes per 3D FFT)"}
     if roofline is None:
         roofline = roof_agent
@@ -696,6 +648,7 @@ def main():
         "gpu_launches": launches_per_iter * K,
         "clocks": clk.summary(),
         "ce_residual_last": ce_last, "finite": finite,
+        "error_vs_oracle": err_oracle,
         "fft_variants": {"passes": ["x", "y", "z fused", "inverse y", "inverse x"], "chosen": variants},
         "warm_start": warm,
     }
