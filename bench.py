@@ -39,6 +39,33 @@ FP32_LANES_PER_SM = 128
 # on the current kernels, keyed by (workload, part); parts without a capture report null.
 TRAFFIC = {}
 
+def agent_bytes_per_iteration(sched: dict, nx: int, ny: int, nz: int, L: int) -> float:
+    """Algorithmic DRAM bytes of one iteration's forward agents and fused prox/Mann pass:
+    what each kernel must read and write by its definition, for the schedule that ran.
+
+    Full spectrum (five passes per look): x 28, y 32, fused z 32, inverse y 16, inverse x
+    20 B per voxel-look.  Band-limited (S = pupil support, B = its kx band, padded to 16):
+    P1 reads M, F d, y and writes M, Gz on S (40 B per element of S); P2 reads S, writes
+    the band rows; P3 reads mu, r' and writes d (20 B per voxel-look) and reads / writes
+    a band row each; P4 reads the band rows, writes S; P5 reads and writes S.  The prox /
+    Mann pass: mu, d, r', w read and mu, r, w written (40 B per voxel-look), plus the prior
+    agent's r, w and wbar (16 B per voxel)."""
+    n = nx * ny * nz
+    passc = 40.0 * n * L + 16.0 * n
+    if sched["schedule"] != "band-limited":
+        return (28 + 32 + 32 + 16 + 20) * n * L + passc
+    nS, nbx = sched["support_columns"], sched["band_columns"]
+    nbxp = -(-nbx // 16) * 16
+    sup = 8.0 * L * nz * nS
+    rows = L * nz * ny
+    p1 = 5 * sup
+    p2 = sup + 8.0 * rows * nbxp
+    p3 = 20.0 * n * L + 8.0 * rows * (nbx + nbxp)
+    p4 = 8.0 * rows * nbxp + sup
+    p5 = 2 * sup
+    return p1 + p2 + p3 + p4 + p5 + passc
+
+
 def phase_times(t01, t02, t03, concurrent: bool):
     """Mean seconds of (forward agents, prior agent, MACE pass) per iteration from the
     milliseconds from each iteration's first event e0 (before the forward agents and the
@@ -475,7 +502,8 @@ def main():
     del spk, eta
     y_host = None
     den = C.Denoiser.from_desc(wl.denoiser)
-    variants = C.autotune(p, y, pupil, window)   # per-pass FFT launch variants, cached for this geometry
+    variants = C.autotune(p, y, pupil, window)   # launch variants and schedule, cached for this geometry
+    sched = C.agent_schedule(p, pupil, window)
     mu, r, w = C.init(p, y, pupil, window)
     wbar = torch.empty((wl.nz, wl.ny, wl.nx), dtype=torch.float32, device=dev)
     ws = C.iterate_workspace(p, den)
@@ -608,13 +636,19 @@ def main():
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per launch set"}
     else:
         roofline = None
-    # forward-agent FFT + prox + Mann path: 136 B per voxel-look (two HBM passes per 3D FFT)
-    agent_bytes = 136.0 * n * L
+    # forward-agent passes + line search + fused prox/Mann pass, bytes of the schedule that ran
+    agent_bytes = agent_bytes_per_iteration(sched, wl.nx, wl.ny, wl.nz, L)
     agent_gbs = agent_bytes / (agent + passc) / 1e9
-    roof_agent = {"bound": "hbm", "kernel": "forward-agent FFT passes + line search + fused prox/Mann pass",
+    roof_agent = {"bound": "hbm", "kernel": f"forward agents ({sched['schedule']} schedule) + line search + "
+                                            "fused prox/Mann pass",
                   "achieved": agent_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": agent_gbs / hbm_peak,
-                  "traffic": TRAFFIC.get((wl.name, "agent")), "peak_source": hbm_src,
-                  "algorithmic": "136 B per voxel-look per iteration (two HBM passes per 3D FFT)"}
+                  "traffic": TRAFFIC.get((wl.name, "agent", sched["schedule"])), "peak_source": hbm_src,
+                  "algorithmic": f"{agent_bytes / (n * L):.1f} B per voxel-look per iteration "
+                                 f"({agent_bytes / 1e9:.2f} GB), see agent_bytes_per_iteration",
+                  "two_pass_model_equivalent": {
+                      "GB/s": 136.0 * n * L / (agent + passc) / 1e9,
+                      "note": "the rate a schedule moving the 136 B per voxel-look of two HBM passes per 3D FFT "
+                              "would need for the same time"}}
     if roofline is None:
         roofline = roof_agent
 
@@ -649,7 +683,8 @@ def main():
         "clocks": clk.summary(),
         "ce_residual_last": ce_last, "finite": finite,
         "error_vs_oracle": err_oracle,
-        "fft_variants": {"passes": ["x", "y", "z fused", "inverse y", "inverse x"], "chosen": variants},
+        "agent_schedule": dict(sched, full_spectrum_variants={"passes": ["x", "y", "z fused", "inverse y",
+                                                                          "inverse x"], "chosen": variants}),
         "warm_start": warm,
     }
     print(json.dumps(line), flush=True)

@@ -64,6 +64,18 @@ typedef enum clamp_status {
  * GPU and only contend.  These flags force either schedule (at most one may be set). */
 #define CLAMP_FLAG_PRIOR_CONCURRENT 0x8
 #define CLAMP_FLAG_PRIOR_SERIAL 0x10
+/* Forward-agent schedule.  The gradient d = F^H[a (y - a F mu)] / sigma_w^2 - D mu
+ * (Eq. h-gradient) and ||A d|| need the y and z transforms only where the pupil is
+ * nonzero, so by default the forward agents transform whole x rows once and everything
+ * else on the pupil's support (the band-limited schedule); F mu is formed once per call and
+ * then advanced by gamma F d.  The full-spectrum schedule transforms every axis of F mu,
+ * F(D mu) and F^H(F d) over the whole volume (five passes).  Both compute the same
+ * quantities up to FP32 rounding.  The band-limited schedule is used when its arrays fit
+ * the agent scratch (clamp_workspace_size), which holds whenever the pupil covers at most
+ * about half of the (ky, kx) plane; these flags force either (at most one may be set;
+ * CLAMP_FLAG_BAND_SPECTRUM falls back to the full spectrum when the arrays do not fit). */
+#define CLAMP_FLAG_FULL_SPECTRUM 0x20
+#define CLAMP_FLAG_BAND_SPECTRUM 0x40
 
 /* Problem and iteration parameters (Sec. II-B, Sec. III, Sec. IV-A). */
 typedef struct clamp_params {
@@ -281,6 +293,14 @@ clamp_status clamp_autotune(const clamp_params* p, const float* y, const float* 
                             void* ws, size_t ws_bytes, void* stream, int32_t* variants_out);
 /* Sets the cached choice for a geometry by hand (host int32[5]). */
 clamp_status clamp_autotune_set(const clamp_params* p, const int32_t* variants);
+/* Which forward-agent schedule iterations with these parameters and this aperture run
+ * (CLAMP_FLAG_*_SPECTRUM, the autotuner's cached choice, else the band-limited one when its
+ * arrays fit the scratch).  pupil [ny][nx], window [nz]: device.  info (host int32[4]):
+ * schedule (1 band-limited, 0 full spectrum), the support's column count |{(ky, kx):
+ * pupil != 0}|, the band's column count |{kx: some pupil(ky, kx) != 0}|, and 1 if the
+ * band-limited arrays fit.  Reads the pupil back (synchronises `stream`). */
+clamp_status clamp_agent_schedule(const clamp_params* p, const float* pupil, const float* window, void* stream,
+                                  int32_t* info);
 
 /* ---- Batched reconstruction: many scenes of uneven size and look count in one launch. */
 

@@ -26,6 +26,8 @@ FLAG_EXACT_PROX = 0x2
 FLAG_NO_APERTURE = 0x4
 FLAG_PRIOR_CONCURRENT = 0x8
 FLAG_PRIOR_SERIAL = 0x10
+FLAG_FULL_SPECTRUM = 0x20
+FLAG_BAND_SPECTRUM = 0x40
 DENOISER_FP32 = 0
 DENOISER_BF16 = 1
 
@@ -38,7 +40,7 @@ EXPORTS = [
     "clamp_iterate", "clamp_iterate_workspace_size", "clamp_mace_step_noalloc",
     "clamp_tc_gemm_bf16", "clamp_tc_gemm_tf32x3",
     "clamp_batch_workspace_size", "clamp_batch_create", "clamp_batch_launch", "clamp_batch_latencies",
-    "clamp_batch_residuals", "clamp_batch_destroy", "clamp_autotune", "clamp_autotune_set",
+    "clamp_batch_residuals", "clamp_batch_destroy", "clamp_autotune", "clamp_autotune_set", "clamp_agent_schedule",
     "clamp_unet_create", "clamp_unet_destroy", "clamp_unet_param_count", "clamp_unet_get", "clamp_unet_set",
     "clamp_unet_workspace_size", "clamp_unet_forward", "clamp_unet_backward", "clamp_unet_adam",
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
@@ -124,6 +126,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_batch_destroy": (V, [P]),
         "clamp_autotune": (I, [PP, P, P, P, P, S, P, ctypes.POINTER(ctypes.c_int32)]),
         "clamp_autotune_set": (I, [PP, ctypes.POINTER(ctypes.c_int32)]),
+        "clamp_agent_schedule": (I, [PP, P, P, P, ctypes.POINTER(ctypes.c_int32)]),
         "clamp_unet_create": (I, [I, I, I, I, P, ctypes.POINTER(P)]),
         "clamp_unet_destroy": (V, [P]),
         "clamp_unet_param_count": (ctypes.c_int64, [P]),
@@ -272,6 +275,16 @@ def autotune(p: Params, y, pupil, window, ws=None, stream=None) -> list:
 def autotune_set(p: Params, variants) -> None:
     arr = (ctypes.c_int32 * 5)(*variants)
     _check(load().clamp_autotune_set(ctypes.byref(p), arr), "clamp_autotune_set")
+
+
+def agent_schedule(p: Params, pupil, window, stream=None) -> dict:
+    """The forward-agent schedule iterations with these parameters run, and the aperture's
+    support and band column counts."""
+    info = (ctypes.c_int32 * 4)()
+    _check(load().clamp_agent_schedule(ctypes.byref(p), _ptr(pupil), _ptr(window), _stream(stream), info),
+           "clamp_agent_schedule")
+    return {"schedule": "band-limited" if info[0] else "full spectrum", "support_columns": int(info[1]),
+            "band_columns": int(info[2]), "band_fits": bool(info[3])}
 
 
 def fft3(x, inverse: bool = False, out=None, stream=None):

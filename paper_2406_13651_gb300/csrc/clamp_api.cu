@@ -91,6 +91,8 @@ extern "C" clamp_status clamp_check_params(const clamp_params* p) {
   if (p->init_mu_steps < 0 || p->init_mu_steps > 1000) return api_fail(CLAMP_EINVAL, "init_mu_steps must be in [0, 1000]");
   if ((p->flags & CLAMP_FLAG_PRIOR_CONCURRENT) && (p->flags & CLAMP_FLAG_PRIOR_SERIAL))
     return api_fail(CLAMP_EINVAL, "CLAMP_FLAG_PRIOR_CONCURRENT and CLAMP_FLAG_PRIOR_SERIAL are exclusive");
+  if ((p->flags & CLAMP_FLAG_FULL_SPECTRUM) && (p->flags & CLAMP_FLAG_BAND_SPECTRUM))
+    return api_fail(CLAMP_EINVAL, "CLAMP_FLAG_FULL_SPECTRUM and CLAMP_FLAG_BAND_SPECTRUM are exclusive");
   return CLAMP_OK;
 }
 
@@ -149,6 +151,30 @@ AgentLayout agent_layout(const clamp_params* p) {
   return a;
 }
 
+// The band-limited schedule's arrays inside the agent scratch's T region (16 bytes per
+// voxel-look): tables, F mu and F d on the support, band rows.
+struct BandLayout {
+  size_t tables, Ms, Fd, band, bytes;
+};
+
+BandLayout band_layout(const clamp_params* p, const BandShape& b) {
+  BandLayout bl{};
+  const long long L = p->looks;
+  Arena ar;
+  bl.tables = ar.off;
+  ar.off += band_table_bytes(b, p->nx, p->ny);
+  bl.Ms = ar.take<float2>(L * p->nz * (long long)b.nSp);
+  bl.Fd = ar.take<float2>(L * p->nz * (long long)b.nSp);
+  bl.band = ar.take<float2>(L * p->nz * (long long)p->ny * b.nbxp);
+  bl.bytes = ar.off;
+  return bl;
+}
+
+bool band_fits(const clamp_params* p, const BandShape& b) {
+  const long long n = (long long)p->nx * p->ny * p->nz;
+  return band_layout(p, b).bytes <= (size_t)(16 * n * p->looks);
+}
+
 struct ReconLayout {
   size_t mu, r, w, ce_ring, mu_ring, agent, den;
   size_t bytes;
@@ -188,6 +214,8 @@ clamp_status recon_prepare(const clamp_params* p, const float* pupil, const floa
   d->g.nz = p->nz;
   d->g.L = p->looks;
   d->g.n = (long long)p->nx * p->ny * p->nz;
+  d->band = BandShape{};
+  d->band_fits = false;
   if (p->flags & CLAMP_FLAG_NO_APERTURE) {  // a = 1: alpha = 1, nothing to read back
     d->alpha = 1.0;
     d->s.nv = p->noise_var;
@@ -214,6 +242,8 @@ clamp_status recon_prepare(const clamp_params* p, const float* pupil, const floa
   const double alpha = (sp / hp.size()) * (sw / hw.size());
   if (!(alpha > 0)) return api_fail(CLAMP_EINVAL, "aperture is identically zero (alpha = 0)");
   d->alpha = alpha;
+  d->band = band_shape(hp.data(), p->nx, p->ny);
+  d->band_fits = band_fits(p, d->band);
   d->s.nv = p->noise_var;
   d->s.alpha = (float)alpha;
   d->s.floor = (float)((double)p->noise_var / alpha);
@@ -375,8 +405,63 @@ AgentVariants tuned_variants(const Geom& g) {
 }
 }  // namespace
 
-static clamp_status agent_ffts(const Derived& d, const float* y, const float* pupil, const float* window,
-                               const float2* mu, const float* r, const AgentLayout& al, void* ws, cudaStream_t st) {
+// Whether the forward agents run the band-limited schedule (CLAMP_FLAG_*_SPECTRUM, the
+// autotuner's cached choice, else whenever its arrays fit the scratch).
+static bool use_band(const clamp_params* p, const Derived& d) {
+  if (!d.band_fits || (p->flags & CLAMP_FLAG_NO_APERTURE) || (p->flags & CLAMP_FLAG_FULL_SPECTRUM)) return false;
+  if (p->flags & CLAMP_FLAG_BAND_SPECTRUM) return true;
+  return tuned_variants(d.g).schedule != 0;
+}
+
+static BandArgs band_args(const clamp_params* p, const Derived& d, const float* y, const float* window,
+                          const float2* mu, const float* r, const AgentLayout& al, void* ws) {
+  const BandLayout bl = band_layout(p, d.band);
+  void* T = at<char>(ws, al.T);
+  BandArgs a{};
+  a.t = band_tables_at(d.band, p->nx, p->ny, at<char>(T, bl.tables));
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.n = d.g.n;
+  a.plane = (long long)p->nx * p->ny;
+  a.y = reinterpret_cast<const float2*>(y);
+  a.window = window;
+  a.mu = mu;
+  a.rprev = r;
+  a.d = at<float2>(ws, al.U);
+  a.Ms = at<float2>(T, bl.Ms);
+  a.Fd = at<float2>(T, bl.Fd);
+  a.band = at<float2>(T, bl.band);
+  a.inv_nv = 1.0f / p->noise_var;
+  a.floor = d.s.floor;
+  a.sc_x = d.s.sc_x;
+  a.sc_y = d.s.sc_y;
+  a.sc_z = d.s.sc_z;
+  a.s1 = at<double>(ws, al.s1);
+  a.s2 = at<double>(ws, al.s2);
+  a.s3 = at<double>(ws, al.s3);
+  a.s4 = at<double>(ws, al.s4);
+  a.px = band_px(p->nx, p->ny, p->nz);
+  return a;
+}
+
+// Forward-agent gradient, line search and mu-residual of every look into the agent scratch
+// (d in U, gamma, mures).  Band-limited schedule: `fresh` builds the support tables and
+// F mu first; otherwise F mu is the previous call's, advanced here by the previous gamma F d.
+static clamp_status agent_ffts(const clamp_params* p, const Derived& d, const float* y, const float* pupil,
+                               const float* window, const float2* mu, const float* r, const AgentLayout& al,
+                               void* ws, bool fresh, cudaStream_t st) {
+  if (use_band(p, d)) {
+    BandArgs a = band_args(p, d, y, window, mu, r, al, ws);
+    if (fresh) {
+      API_CUDA(launch_band_tables(pupil, p->nx, p->ny, a.t, st), "support tables");
+      API_CUDA(launch_band_spectrum(a, p->looks, st), "F mu on the support");
+    }
+    a.gamma_prev = fresh ? nullptr : at<float>(ws, al.gamma);
+    API_CUDA(launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma), at<double>(ws, al.mures), st),
+             "band-limited forward-agent passes");
+    return CLAMP_OK;
+  }
   Partials pt = partials(al, ws);
   API_CUDA(launch_agent_fft(d.g, d.s, mu, r, reinterpret_cast<const float2*>(y), pupil, window,
                             at<float4>(ws, al.T), at<float2>(ws, al.U), pt, tuned_variants(d.g), st),
@@ -395,7 +480,7 @@ static clamp_status do_init_warm(const clamp_params* p, const Derived& d, const 
   API_TRY(do_init(p, d, y, pupil, window, r_init, mu, r, w, al, ws, st));
   if (!r_init || p->init_mu_steps <= 0 || (p->flags & CLAMP_FLAG_NO_APERTURE)) return CLAMP_OK;
   for (int s = 0; s < p->init_mu_steps; ++s) {
-    API_TRY(agent_ffts(d, y, pupil, window, mu, r, al, ws, st));
+    API_TRY(agent_ffts(p, d, y, pupil, window, mu, r, al, ws, s == 0, st));
     API_CUDA(launch_mu_update(d.g, mu, at<float2>(ws, al.U), at<float>(ws, al.gamma), st), "mu update");
   }
   return CLAMP_OK;
@@ -415,6 +500,7 @@ clamp_status autotune_agent(const clamp_params* p, const ReconPlan& d, const flo
   API_CUDA(cudaEventCreate(&e0), "event");
   API_CUDA(cudaEventCreate(&e1), "event");
   AgentVariants best;
+  float full_ms = 0.f;
   for (int pass = 0; pass < 5; ++pass) {
     float best_ms = 1e30f;
     for (int V = 0; V < kVariants; ++V) {
@@ -440,6 +526,29 @@ clamp_status autotune_agent(const clamp_params* p, const ReconPlan& d, const flo
         best.v[pass] = V;
       }
     }
+    full_ms += best_ms;
+  }
+  // the band-limited schedule as a whole (tables from the real pupil: its indices come from them)
+  best.schedule = 0;
+  if (d.band_fits && !(p->flags & CLAMP_FLAG_NO_APERTURE)) {
+    BandArgs a = band_args(p, d, y, window, mu, rp, al, ws);
+    a.gamma_prev = at<float>(ws, al.gamma);
+    cudaError_t e = launch_band_tables(pupil, p->nx, p->ny, a.t, st);
+    if (e == cudaSuccess) e = launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma),
+                                                at<double>(ws, al.mures), st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+      e = launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma), at<double>(ws, al.mures), st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(e, "autotune (band-limited schedule)");
+    }
+    best.schedule = ms <= full_ms ? 1 : 0;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -464,6 +573,20 @@ extern "C" clamp_status clamp_autotune(const clamp_params* p, const float* y, co
   API_TRY(autotune_agent(p, d, y, pupil, window, ws, st, &v));
   if (variants_out)
     for (int i = 0; i < 5; ++i) variants_out[i] = v.v[i];
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_agent_schedule(const clamp_params* p, const float* pupil, const float* window,
+                                             void* stream, int32_t* info) {
+  API_TRY(clamp_check_params(p));
+  API_TRY(need_ptrs({pupil, window, info}, "clamp_agent_schedule"));
+  API_TRY(api_ensure_device());
+  Derived d;
+  API_TRY(recon_prepare(p, pupil, window, (cudaStream_t)stream, &d));
+  info[0] = use_band(p, d) ? 1 : 0;
+  info[1] = d.band.nS;
+  info[2] = d.band.nbx;
+  info[3] = d.band_fits ? 1 : 0;
   return CLAMP_OK;
 }
 
@@ -531,7 +654,7 @@ extern "C" clamp_status clamp_forward_prox(const clamp_params* p, int32_t k, con
     API_TRY(ablation_prepare(d, y, al, ws, st));
     if (mu_residual) API_CUDA(cudaMemsetAsync(mu_residual, 0, sizeof(double), st), "mu residual");
   } else {
-    API_TRY(agent_ffts(d, y, pupil, window, reinterpret_cast<float2*>(mu), r, al, ws, st));
+    API_TRY(agent_ffts(p, d, y, pupil, window, reinterpret_cast<float2*>(mu), r, al, ws, true, st));
     if (mu_residual) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_residual, st), "mu residual");
   }
   PassC c = passc_args(p, d, al, ws, reinterpret_cast<float2*>(mu), r, const_cast<float*>(w), nullptr, k);
@@ -622,10 +745,12 @@ static SideStream* side_stream(cudaStream_t st) {
 }
 
 // One to many loop bodies of Alg. 2 on the state (mu, r, w); ws = agent scratch then denoiser scratch.
+// `spectrum_ready`: the agent scratch already holds the band-limited schedule's F mu for this
+// mu, one pending step behind (a previous call of the same run); otherwise it is rebuilt.
 static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_first, int iters, const float* y,
                                  const float* pupil, const float* window, const clamp_denoiser* den, float2* mu,
                                  float* r, float* w, float* wbar, double* ce_out, double* mu_out, void* ws,
-                                 void* const* events, cudaStream_t st) {
+                                 void* const* events, bool spectrum_ready, cudaStream_t st) {
   const AgentLayout al = agent_layout(p);
   void* dws = static_cast<char*>(ws) + al.bytes;
   const long long n = d.g.n;
@@ -649,7 +774,7 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
     if (noap) {
       if (mu_out) API_CUDA(cudaMemsetAsync(mu_out + it, 0, sizeof(double), st), "mu residual");
     } else {
-      API_TRY(agent_ffts(d, y, pupil, window, mu, r, al, ws, st));
+      API_TRY(agent_ffts(p, d, y, pupil, window, mu, r, al, ws, it == 0 && !spectrum_ready, st));
       if (mu_out) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_out + it, st), "mu residual");
     }
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 1], st), "event");
@@ -687,7 +812,7 @@ clamp_status recon_enqueue(const clamp_params* p, const ReconPlan& d, const floa
              "copy");
   for (int it = 0; it < p->max_iters; ++it)
     API_TRY(iterate_impl(p, d, p->k0 + it + 1, 1, y, pupil, window, den, mu, r, w, r_out,
-                         at<double>(ws, rl.ce_ring) + it, at<double>(ws, rl.mu_ring) + it, aws, nullptr, st));
+                         at<double>(ws, rl.ce_ring) + it, at<double>(ws, rl.mu_ring) + it, aws, nullptr, it > 0, st));
   return CLAMP_OK;
 }
 
@@ -715,7 +840,7 @@ extern "C" clamp_status clamp_iterate(const clamp_params* p, int32_t k_first, in
   API_TRY(recon_prepare(p, pupil, window, st, &d));
   API_CUDA(cudaMemsetAsync(at<int>(ws, agent_layout(p).err), 0, sizeof(int), st), "memset");
   return iterate_impl(p, d, k_first, iters, y, pupil, window, den, reinterpret_cast<float2*>(mu), r, w, wbar, ce_out,
-                      mu_out, ws, events, st);
+                      mu_out, ws, events, false, st);
 }
 
 static clamp_status reconstruct_impl(const clamp_params* p, const float* y, const float* pupil, const float* window,
@@ -747,7 +872,7 @@ static clamp_status reconstruct_impl(const clamp_params* p, const float* y, cons
   for (int it = 0; it < p->max_iters; ++it) {
     const int k = p->k0 + it + 1;
     API_TRY(iterate_impl(p, d, k, 1, y, pupil, window, den, mu, r, w, r_out, ce_ring + it, mu_ring + it, aws,
-                         nullptr, st));
+                         nullptr, it > 0, st));
     done = it + 1;
     const bool last = (it + 1 == p->max_iters);
     if ((p->tol > 0 && ((it + 1) % check == 0 || last)) || (last && report)) {

@@ -15,6 +15,8 @@ struct ReconPlan {
   clamp::Geom g;
   clamp::AgentScalars s;
   double alpha;
+  clamp::BandShape band;   // the aperture's support and band (counted from the pupil)
+  bool band_fits;          // the band-limited schedule's arrays fit the agent scratch
 };
 
 // Reads the aperture back to compute alpha (synchronises `st`): call before any capture.

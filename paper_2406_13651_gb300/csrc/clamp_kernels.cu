@@ -43,6 +43,8 @@ static const float2* tw_ptr(int N) {
   return reinterpret_cast<const float2*>(p) + tw_offset(N);
 }
 
+const float2* twiddle_table(int N) { return tw_ptr(N); }
+
 extern __shared__ float4 dyn_smem[];
 
 // ---------------------------------------------------------------- reductions

@@ -27,6 +27,7 @@ __host__ __device__ constexpr int pipe_cols(int N) { return N > 128 ? 8 : 16; }
 // Passes of the forward agent: A_x, A_y, fused z, B_y, B_x.
 struct AgentVariants {
   int v[5] = {0, 0, 0, 0, 0};
+  int schedule = -1;   // forward-agent schedule: -1 not timed (band-limited when it fits), 0 full spectrum, 1 band-limited
 };
 // True if variant V of pass `pass` can run on the geometry.
 bool variant_valid(int pass, int V, int nx, int ny, int nz);
@@ -55,6 +56,51 @@ struct Partials {
 
 // Twiddle tables (host-computed, uploaded once per device).
 cudaError_t upload_twiddles();
+// Device address of the length-N twiddle table (N a supported axis length).
+const float2* twiddle_table(int N);
+
+// ---- band-limited forward agent (band_agent.cu): the gradient's transforms on the
+// aperture's support only.  Support S = {(ky, kx): pupil != 0} (row by row), band
+// B = {kx: any pupil(ky, kx) != 0}; counts padded to multiples of 16.
+struct BandShape {
+  int nS, nSp, nbx, nbxp;
+};
+struct BandTables {
+  int nS, nSp, nbx, nbxp;
+  int* sidx;      // [ny][nbxp] support index of (ky, band column b), or -1
+  int* s_kykx;    // [nSp] ky * nx + kx of support column s (padding: 0)
+  float* s_pup;   // [nSp] pupil value of support column s (padding: 0)
+  int* bx;        // [nbxp] kx of band column b (padding: -1)
+  int* bpos;      // [nx] band column of kx, or -1
+};
+struct BandArgs {
+  BandTables t;
+  int nx, ny, nz;
+  long long n, plane;         // nx ny nz, nx ny
+  const float2* y;            // [L][n] data (full spectrum layout)
+  const float* window;        // [nz]
+  const float2* mu;           // [L][n]
+  const float* rprev;         // [L][n] r'
+  float2* d;                  // [L][n] gradient direction out
+  float2* Ms;                 // [L][nz][nSp] F mu on the support (kept across iterations)
+  float2* Fd;                 // [L][nz][nSp] Gz, then F d on the support
+  float2* band;               // [L][nz][ny][nbxp] band rows
+  const float* gamma_prev;    // [L] step of the previous evaluation (spectrum update), or null
+  float inv_nv, floor, sc_x, sc_y, sc_z;
+  double *s1, *s2, *s3, *s4;  // partials: s1, s3 [L][px]; s2, s4 [L][pS]
+  int px;
+};
+BandShape band_shape(const float* pupil_host, int nx, int ny);
+size_t band_table_bytes(const BandShape& b, int nx, int ny);
+BandTables band_tables_at(const BandShape& b, int nx, int ny, void* base);
+int band_pS(const BandShape& b);
+int band_px(int nx, int ny, int nz);
+// Builds the device tables from the device pupil (one CTA).
+cudaError_t launch_band_tables(const float* pupil, int nx, int ny, const BandTables& t, cudaStream_t st);
+// Ms <- F mu on the support (first axis x over whole rows, then y and z on band / support).
+cudaError_t launch_band_spectrum(const BandArgs& a, int L, cudaStream_t st);
+// P1-P5 and the line search: d, F d on the support, gamma_l and the floored mu-residual per look.
+cudaError_t launch_band_agent(const BandArgs& a, int L, float nv, float* gamma, double* mures, cudaStream_t st);
 
 // ---- forward agent (Alg. 2 steps 6-8): pass A (x, y), fused z pass, pass B (y, x)
 // p.pz / p.px receive the partial counts per look the chosen variants produce.

@@ -1,5 +1,6 @@
-"""Autotuner: every launch variant of the forward-agent passes matches the oracle, and the
-tuner returns a valid variant for each pass."""
+"""Autotuner: every launch variant of the full-spectrum schedule's passes matches the
+oracle, and the tuner returns a valid variant for each pass (it also times the
+band-limited schedule against them and caches the faster)."""
 import numpy as np
 import pytest
 
@@ -45,7 +46,8 @@ def _case(nx, ny, nz, L, seed):
 def test_every_variant_matches_oracle(C, shape, variant):
     nx, ny, nz, L = shape
     wl, y32, st, mu_ref, r_ref = _case(nx, ny, nz, L, seed=nx + variant)
-    p = C.make_params(nx, ny, nz, L, wl.noise_var, wl.prox_var)
+    # the variants belong to the full-spectrum schedule's five passes
+    p = C.make_params(nx, ny, nz, L, wl.noise_var, wl.prox_var, flags=C.FLAG_FULL_SPECTRUM)
     dev = torch.device("cuda")
     C.autotune_set(p, [variant] * 5)
     try:
