@@ -666,6 +666,19 @@ int passc_blocks(long long n) {
   return (int)(b < 152 * 8 ? b : 152 * 8);
 }
 
+// The fused pass reads every look's r and w of a voxel twice (the look sum, then the Mann
+// step), so the second read hits L2 only while the rows all resident threads hold fit in
+// it: the grid keeps them near 48 MB (16 bytes per voxel pair and row), in whole waves of
+// 152 SMs, between 1 and 8 CTAs per SM.
+int passc_fused_blocks(long long n, int L) {
+  const long long threads = (48LL << 20) / (16LL * (L + 1));
+  long long b = (threads + NT - 1) / NT;
+  b = (b + 151) / 152 * 152;
+  if (b < 152) b = 152;
+  const int cap = passc_blocks(n);
+  return (int)(b < cap ? b : cap);
+}
+
 // Each thread walks the L looks of one voxel at a time.  The look loops are software-
 // pipelined: look l + 1's loads are issued before look l's arithmetic and stores (the
 // arrays do not alias), so two looks' loads are in flight per thread.
@@ -876,9 +889,10 @@ cudaError_t launch_mu_update(const Geom& g, float2* mu, const float2* d, const f
 cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st) {
   const bool pair = g.n % 2 == 0 && aligned(c.w, 8) && aligned(c.r, 8) && aligned(c.wbar, 8) &&
                     aligned(c.mu, 16) && aligned(c.d, 16);
-  if (c.exact_prox) k_pass_c<true, true, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
-  else if (pair) k_pass_c_pair<<<passc_blocks(g.n), NT, 0, st>>>(g, c);
-  else k_pass_c<true, true><<<passc_blocks(g.n), NT, 0, st>>>(g, c);
+  const int nb = passc_fused_blocks(g.n, g.L);
+  if (c.exact_prox) k_pass_c<true, true, true><<<nb, NT, 0, st>>>(g, c);
+  else if (pair) k_pass_c_pair<<<nb, NT, 0, st>>>(g, c);
+  else k_pass_c<true, true><<<nb, NT, 0, st>>>(g, c);
   return cudaGetLastError();
 }
 cudaError_t launch_prox_only(const Geom& g, const PassC& c, cudaStream_t st) {

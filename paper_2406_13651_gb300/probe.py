@@ -1,0 +1,93 @@
+"""Profiling driver for the CLAMP kernels (one GPU; no timing contract, for ncu captures).
+
+  python -m paper_2406_13651_gb300.probe agent --shape 256,256,128 --looks 4 --iters 3 \\
+      [--schedule auto|band|full] [--prior gauss|cnn-bf16|cnn-fp32]
+  python -m paper_2406_13651_gb300.probe prior --shape 256,256,64 --dtype bf16 --reps 3
+
+``agent`` runs ``--iters`` CLAMP iterations (after one untimed iteration) on seeded random
+data with a circular pupil of radius 0.35 Nyquist and a Hann range window; ``prior`` runs
+the residual CNN prior agent (8 x 48 BF16 or 5 x 32 FP32) on a seeded random volume.  Each
+prints one JSON line with the mean milliseconds per repetition (CUDA events).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+
+def main(argv=None) -> int:
+    import numpy as np
+    import torch
+
+    from . import build as B
+    from . import clamp as C
+    from . import inputs as I
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["agent", "prior"])
+    ap.add_argument("--shape", default="256,256,128", help="nx,ny,nz")
+    ap.add_argument("--looks", type=int, default=4)
+    ap.add_argument("--iters", type=int, default=3)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--schedule", choices=["auto", "band", "full"], default="auto")
+    ap.add_argument("--prior", choices=["gauss", "cnn-bf16", "cnn-fp32"], default="gauss")
+    ap.add_argument("--dtype", choices=["fp32", "bf16"], default="bf16")
+    a = ap.parse_args(argv)
+    B.build()
+    C.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    nx, ny, nz = (int(v) for v in a.shape.split(","))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.what == "prior":
+        layers, ch = (8, 48) if a.dtype == "bf16" else (5, 32)
+        ws_, bs_ = I.cnn_weights(layers, ch, seed=1)
+        den = C.Denoiser.cnn(ws_, bs_, a.dtype)
+        x = torch.rand((nz, ny, nx), generator=torch.Generator(device=dev).manual_seed(3), device=dev)
+        out = torch.empty_like(x)
+        wsb = C._ws(den.workspace_size(nx, ny, nz))
+        C.denoise(den, x, out, ws=wsb)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(a.reps):
+            C.denoise(den, x, out, ws=wsb)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / a.reps
+        macs = 27 * (ch + (layers - 2) * ch * ch + ch)
+        print(json.dumps({"probe": "prior", "shape": [nx, ny, nz], "dtype": a.dtype, "ms": ms,
+                          "tflops": 2 * macs * nx * ny * nz / ms / 1e9}), flush=True)
+        return 0
+    L = a.looks
+    pupil = torch.from_numpy(I.circular_pupil(nx, ny, 0.35)).to(dev)
+    window = torch.from_numpy(I.hann_window(nz)).to(dev)
+    flags = {"auto": 0, "band": C.FLAG_BAND_SPECTRUM, "full": C.FLAG_FULL_SPECTRUM}[a.schedule]
+    p = C.make_params(nx, ny, nz, L, 1e-3, 1e-4, flags=flags)
+    g = torch.Generator(device=dev).manual_seed(5)
+    shape = (L, nz, ny, nx)
+    y = torch.complex(torch.randn(shape, generator=g, device=dev), torch.randn(shape, generator=g, device=dev))
+    y *= (pupil[None, None] * window[None, :, None, None])
+    if a.prior == "gauss":
+        den = C.Denoiser.gauss(0.8)
+    else:
+        dt = a.prior.split("-")[1]
+        layers, ch = (8, 48) if dt == "bf16" else (5, 32)
+        w_, b_ = I.cnn_weights(layers, ch, seed=1)
+        den = C.Denoiser.cnn(w_, b_, dt)
+    mu, r, w = C.init(p, y, pupil, window)
+    wbar = torch.empty((nz, ny, nx), device=dev)
+    ws = C.iterate_workspace(p, den)
+    C.iterate(p, 1, 1, y, pupil, window, den, mu, r, w, wbar, ws=ws)
+    torch.cuda.synchronize()
+    e0.record()
+    C.iterate(p, 2, a.iters, y, pupil, window, den, mu, r, w, wbar, ws=ws)
+    e1.record()
+    torch.cuda.synchronize()
+    sched = C.agent_schedule(p, pupil, window)
+    print(json.dumps({"probe": "agent", "shape": [nx, ny, nz], "looks": L, "schedule": sched, "prior": a.prior,
+                      "ms_per_iteration": e0.elapsed_time(e1) / a.iters}), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())
