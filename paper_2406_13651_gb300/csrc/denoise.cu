@@ -393,6 +393,7 @@ extern "C" void clamp_denoiser_destroy(clamp_denoiser* d) {
     if (p) cudaFree(p);
   for (void* p : d->w16)
     if (p) cudaFree(p);
+  if (d->w_last) cudaFree(d->w_last);
   delete d;
 }
 
@@ -436,6 +437,13 @@ extern "C" clamp_status clamp_denoiser_create_cnn(int32_t layers, int32_t channe
     if (i > 0 && (!last || bf) && ci % chunk == 0) {   // layers on the tensor cores
       const std::vector<uint8_t> pk = clamp::pack_tc_weights(wp, ci, co, co == 1 ? 16 : co, bf);
       ok = ok && upload(&w16, pk.data(), pk.size());
+    } else if (i == 0 && bf && co % 16 == 0 && co <= 64) {   // first BF16 layer: im2col on the tensor cores
+      const std::vector<uint8_t> pk = clamp::pack_first_tc_weights(wp, co);
+      ok = ok && upload(&w16, pk.data(), pk.size());
+    }
+    if (last && bf && ci % 16 == 0 && ci <= 64) {   // last BF16 layer: tap sums on the tensor cores
+      const std::vector<uint8_t> pk = clamp::pack_last_tc_weights(wp, ci);
+      ok = ok && upload(&d->w_last, pk.data(), pk.size());
     }
     d->w.push_back(static_cast<float*>(wd));
     d->b.push_back(static_cast<float*>(bd));

@@ -36,6 +36,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -798,23 +799,283 @@ static cudaError_t run_first(const float* in, const float* w, const float* b, ui
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- first BF16 layer (1 -> C) on tensor cores
+
+// With one input channel the 27 taps are the GEMM's K: a CTA builds, per 128-voxel output
+// row, the im2col tile A[v][k] = x[v + tap k] (k = 9 dz + 3 dy + dx < 27, zero for
+// 27 <= k < 32) in BF16 from its input halo, and two K = 16 MMAs against the packed weights
+// B[co][k] give all C outputs in TMEM; the epilogue is the hidden layers'.  Tiles of 2 rows
+// x 2 planes, as k_conv3_tc<BF16>.  Layouts (no-swizzle K-major): element (row, k) of A at
+// (row / 8) * 512 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2, the same for B with co.
+constexpr int CF1_TY = 2, CF1_TZ = 2, CF1_MT = CF1_TY * CF1_TZ;
+constexpr int CF1_HY = CF1_TY + 2, CF1_HZ = CF1_TZ + 2;
+constexpr int CF1_A_BYTES = 128 * 64;                               // one im2col tile (K = 32)
+__host__ __device__ constexpr size_t cf1_smem(int C) {
+  return 1024 + (size_t)CF1_MT * CF1_A_BYTES + (size_t)C * 64 + 2 * CF1_HZ * CF1_HY * TC_HX + 64;
+}
+
+template <int C>
+__global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict__ in, const uint4* __restrict__ wpk,
+                                                         const float* __restrict__ bias, uint4* __restrict__ out,
+                                                         int nx, int ny, int nz, int* err) {
+  static_assert(C % 16 == 0 && C <= 64, "channels");
+  constexpr int TMEM_COLS = pow2_cols(CF1_MT * C);
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* s_a = base;                                            // [MT][8 KB]
+  uint4* s_w = reinterpret_cast<uint4*>(s_a + CF1_MT * CF1_A_BYTES);    // C * 64 bytes
+  uint16_t* s_x = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(s_w) + C * 64);  // [HZ][HY][HX]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_x + CF1_HZ * CF1_HY * TC_HX + 8);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int x0 = blockIdx.x * TCX, y0 = blockIdx.y * CF1_TY, z0 = blockIdx.z * CF1_TZ;
+  const long long plane = (long long)nx * ny, n = plane * nz;
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  for (int e = tid; e < C * 4; e += TC_NT) cp_async16(&s_w[e], &wpk[e], true);
+  for (int e = tid; e < CF1_HZ * CF1_HY * TC_HX; e += TC_NT) {   // input halo, BF16, zeros outside
+    const int xr = e % TC_HX, t = e / TC_HX;
+    const int yr = t % CF1_HY, zr = t / CF1_HY;
+    const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z0 + zr - 1;
+    float v = 0.f;
+    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
+      v = __ldg(&in[(long long)gz * plane + (long long)gy * nx + gx]);
+    s_x[e] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  // im2col: one 16-byte chunk (8 consecutive k of one row) per step
+  for (int e = tid; e < CF1_MT * 128 * 4; e += TC_NT) {
+    const int row = e % 128, g = (e / 128) % 4, mt = e / 512;
+    const int ty = mt % CF1_TY, tz = mt / CF1_TY;
+    uint32_t w4[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      uint32_t pair = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 8 * g + 2 * j + h;
+        uint32_t v = 0;
+        if (k < 27) {
+          const int dz = k / 9, dy = (k / 3) % 3, dx = k % 3;
+          v = s_x[((tz + dz) * CF1_HY + ty + dy) * TC_HX + row + dx];
+        }
+        pair |= v << (16 * h);
+      }
+      w4[j] = pair;
+    }
+    *reinterpret_cast<uint4*>(s_a + mt * CF1_A_BYTES + (row / 8) * 512 + g * 128 + (row % 8) * 16) =
+        make_uint4(w4[0], w4[1], w4[2], w4[3]);
+  }
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  if (tid == 0) {
+    const uint32_t a_s = tc::smem_addr(s_a), w_s = tc::smem_addr(s_w);
+#pragma unroll
+    for (int mt = 0; mt < CF1_MT; ++mt)
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        tc::mma_bf16(tbase + (uint32_t)(mt * C), tc::make_desc(a_s + mt * CF1_A_BYTES + h * 256, 128, 512),
+                     tc::make_desc(w_s + h * 256, 128, 512), TcKind<TC_BF16>::idesc(128, C), h ? 1u : 0u);
+    tc::mma_commit(mbar);
+  }
+  const bool done = tc::mbar_wait_bounded(mbar, 0u, kWaitLimit);
+  tc::fence_after_sync();
+  if (done) {
+    const int q = warp & 3, hh = warp >> 2;
+#pragma unroll 1
+    for (int mt = 0; mt < CF1_MT; ++mt) {
+      const int gy = y0 + mt % CF1_TY, gz = z0 + mt / CF1_TY, gx = x0 + 32 * q + lane;
+      const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
+      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * C);
+      constexpr int HALF = C / 2;
+#pragma unroll
+      for (int j = 0; j < HALF / 8; ++j) {
+        const int col = hh * HALF + 8 * j;
+        float v[8];
+        tc::tmem_ld_x8(trow + (uint32_t)col, v);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
+        uint4 o;
+        o.x = pack_bf16x2(v[0], v[1]);
+        o.y = pack_bf16x2(v[2], v[3]);
+        o.z = pack_bf16x2(v[4], v[5]);
+        o.w = pack_bf16x2(v[6], v[7]);
+        out[(long long)(col / 8) * n + vox] = o;
+      }
+    }
+  } else if (tid == 0) {
+    if (err) atomicOr(err, 2);
+    tc::mbar_wait_bounded(mbar, 0u, kWaitLimit);   // give the MMAs a bounded wait before TMEM is freed
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, TMEM_COLS);
+}
+
+template <int C>
+static cudaError_t run_first_tc(const float* in, const uint4* wpk, const float* b, uint4* out, int nx, int ny, int nz,
+                                int* err, cudaStream_t st) {
+  const size_t smem = cf1_smem(C);
+  cudaError_t e = cudaFuncSetAttribute(k_conv_first_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(nx / TCX, ny / CF1_TY, nz / CF1_TZ);
+  k_conv_first_tc<C><<<grid, TC_NT, smem, st>>>(in, wpk, b, out, nx, ny, nz, err);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- last BF16 layer (C -> 1)
+
+// out[v] = x[v] + b + sum_tap sum_c W[tap][c] h[v + tap][c] is split into a pointwise GEMM,
+// P_tap[u] = sum_c W[tap][c] h[u][c] for the 27 taps of every voxel u (tensor cores: M = 128
+// voxels, K = C channels, N = 27 taps padded to 32, FP32 accumulators), and a gather
+// out[v] = x[v] + b + sum_tap P_tap[v + tap] (zero outside the volume).  The GEMM reads each
+// activation once with no halo: in the [C/8][n][8] BF16 layout 128 consecutive voxels of one
+// channel group are 16 no-swizzle K-major core matrices back to back, so a tile is copied
+// as is.  B (the weights, BF16) is [C/8][32 taps][8]: element (tap, c) at (c / 8) * 512 +
+// tap * 16 + (c % 8) * 2.  P is FP32 [27][n] (tap-major).
+constexpr int CL2_MT = 4;   // 128-voxel tiles per CTA
+
+// Bytes of each of the prior's two activation buffers: C channels per voxel, and for BF16 at
+// least the last layer's tap sums P (27 FP32 values per voxel), which go to whichever
+// buffer the last hidden layer did not write.
+static size_t tc_buffer_bytes(bool bf16, int C, size_t n) {
+  const size_t act = ((size_t)C * n * (bf16 ? 2 : 4) + 255) & ~(size_t)255;
+  return bf16 ? std::max(act, (27 * n * 4 + 255) & ~(size_t)255) : act;
+}
+
+template <int C>
+__global__ void __launch_bounds__(TC_NT) k_last_taps_tc(const uint4* __restrict__ act, const uint4* __restrict__ wpk,
+                                                        float* __restrict__ P, long long n, int* err) {
+  constexpr int G = C / 8, KSTEPS = C / 16, TMEM_COLS = pow2_cols(CL2_MT * 32);
+  extern __shared__ unsigned char tc_smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+  uint4* s_a = reinterpret_cast<uint4*>(base);                  // [MT][G][128 voxels] x 16 B
+  uint4* s_w = s_a + CL2_MT * G * 128;                          // [G][32 taps] x 16 B
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_w + G * 32);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const long long v0 = (long long)blockIdx.x * (CL2_MT * 128);
+  if (tid == 0) tc::mbar_init(mbar, 1);
+  if (warp == 0) {
+    tc::tmem_alloc(tslot, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  for (int e = tid; e < CL2_MT * G * 128; e += TC_NT) {
+    const int vv = e % 128, g = (e / 128) % G, mt = e / (128 * G);
+    cp_async16(&s_a[e], &act[(long long)g * n + v0 + mt * 128 + vv], true);
+  }
+  for (int e = tid; e < G * 32; e += TC_NT) cp_async16(&s_w[e], &wpk[e], true);
+  cp_async_wait_all();
+  tc::fence_proxy_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = *tslot;
+  if (tid == 0) {
+    const uint32_t a_s = tc::smem_addr(s_a), w_s = tc::smem_addr(s_w);
+#pragma unroll
+    for (int mt = 0; mt < CL2_MT; ++mt)
+#pragma unroll
+      for (int ks = 0; ks < KSTEPS; ++ks)
+        tc::mma_bf16(tbase + (uint32_t)(mt * 32),
+                     tc::make_desc(a_s + (uint32_t)((mt * G + 2 * ks) * 128 * 16), 128 * 16, 128),
+                     tc::make_desc(w_s + (uint32_t)(2 * ks * 32 * 16), 32 * 16, 128), TcKind<TC_BF16>::idesc(128, 32),
+                     ks ? 1u : 0u);
+    tc::mma_commit(mbar);
+  }
+  const bool done = tc::mbar_wait_bounded(mbar, 0u, kWaitLimit);
+  tc::fence_after_sync();
+  if (done) {
+    const int q = warp & 3, hh = warp >> 2;
+#pragma unroll 1
+    for (int mt = 0; mt < CL2_MT; ++mt) {
+      const long long v = v0 + mt * 128 + 32 * q + lane;
+      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * 32);
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const int col = hh * 16 + 8 * j;
+        float t[8];
+        tc::tmem_ld_x8(trow + (uint32_t)col, t);
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+          if (col + i < 27) P[(long long)(col + i) * n + v] = t[i];
+      }
+    }
+  } else if (tid == 0) {
+    if (err) atomicOr(err, 2);
+    tc::mbar_wait_bounded(mbar, 0u, kWaitLimit);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, TMEM_COLS);
+}
+
+// out[v] = resid[v] + bias + sum over the 27 taps of P_tap[v + tap] inside the volume.
+__global__ void __launch_bounds__(NT) k_last_gather(const float* __restrict__ P, const float* __restrict__ bias,
+                                                    const float* __restrict__ resid, float* __restrict__ out, int nx,
+                                                    int ny, int nz) {
+  const long long plane = (long long)nx * ny, n = plane * nz;
+  const long long v = (long long)blockIdx.x * NT + threadIdx.x;
+  if (v >= n) return;
+  const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / plane);
+  float acc = __ldg(&bias[0]) + resid[v];
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz) {
+    const int zz = z + dz - 1;
+    if (zz < 0 || zz >= nz) continue;
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      const int yy = y + dy - 1;
+      if (yy < 0 || yy >= ny) continue;
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int xx = x + dx - 1;
+        if (xx < 0 || xx >= nx) continue;
+        const int tap = 9 * dz + 3 * dy + dx;
+        acc += __ldg(&P[(long long)tap * n + (long long)zz * plane + (long long)yy * nx + xx]);
+      }
+    }
+  }
+  out[v] = acc;
+}
+
+template <int C>
+static cudaError_t run_last_tc(const uint4* act, const uint4* wpk, const float* b, const float* resid, float* out,
+                               float* P, int nx, int ny, int nz, int* err, cudaStream_t st) {
+  const long long n = (long long)nx * ny * nz;
+  const size_t smem = 1024 + (size_t)16 * (CL2_MT * (C / 8) * 128 + (C / 8) * 32) + 64;
+  cudaError_t e = cudaFuncSetAttribute(k_last_taps_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_last_taps_tc<C><<<(unsigned)(n / (CL2_MT * 128)), TC_NT, smem, st>>>(act, wpk, P, n, err);
+  k_last_gather<<<(unsigned)((n + NT - 1) / NT), NT, 0, st>>>(P, b, resid, out, nx, ny, nz);
+  return cudaGetLastError();
+}
+
 template <int KIND, int C>
 static cudaError_t apply_tc_c(const clamp_denoiser* d, const float* in, float* out, int nx, int ny, int nz, void* ws,
                               int* err, cudaStream_t st) {
   const size_t n = (size_t)nx * ny * nz;
-  const size_t esz = KIND == TC_BF16 ? 2 : 4;
-  const size_t act = ((size_t)C * n * esz + 255) & ~(size_t)255;
   uint4* A = static_cast<uint4*>(ws);
-  uint4* B = reinterpret_cast<uint4*>(static_cast<char*>(ws) + act);
-  cudaError_t e = run_first<C, KIND == TC_BF16>(in, d->w[0], d->b[0], A, nx, ny, nz, st);
+  uint4* B = reinterpret_cast<uint4*>(static_cast<char*>(ws) + tc_buffer_bytes(KIND == TC_BF16, C, n));
+  cudaError_t e = (KIND == TC_BF16 && d->w16[0])
+                      ? run_first_tc<C>(in, static_cast<const uint4*>(d->w16[0]), d->b[0], A, nx, ny, nz, err, st)
+                      : run_first<C, KIND == TC_BF16>(in, d->w[0], d->b[0], A, nx, ny, nz, st);
   if (e != cudaSuccess) return e;
   uint4* cur = A;
   for (int i = 1; i < d->layers; ++i) {
     const uint4* wp = static_cast<const uint4*>(d->w16[i]);
     if (i == d->layers - 1) {
       if constexpr (KIND == TC_BF16) {
-        // BF16: the padded MMA tile is cheaper than unpacking BF16 on the CUDA cores
-        e = run_tc<KIND, C, 16, true>(cur, wp, d->b[i], nullptr, out, in, nx, ny, nz, err, st);
+        // BF16: per-voxel tap sums on the tensor cores, then a gather (no halo staging)
+        float* P = reinterpret_cast<float*>(cur == A ? B : A);
+        e = run_last_tc<C>(cur, static_cast<const uint4*>(d->w_last), d->b[i], in, out, P, nx, ny, nz, err, st);
       } else {
         // TF32x3: the padded tile costs as much as a hidden layer; CUDA cores instead
         e = cudaFuncSetAttribute(k_conv_last<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CL_SMEM);
@@ -848,9 +1109,7 @@ bool tc_denoiser_supports(const clamp_denoiser* d, int nx, int ny, int nz) {
 }
 
 size_t tc_denoise_ws_bytes(const clamp_denoiser* d, int nx, int ny, int nz) {
-  const size_t n = (size_t)nx * ny * nz;
-  const size_t esz = d->dtype == CLAMP_DENOISER_BF16 ? 2 : 4;
-  return 2 * ((((size_t)d->channels * n * esz) + 255) & ~(size_t)255);
+  return 2 * tc_buffer_bytes(d->dtype == CLAMP_DENOISER_BF16, d->channels, (size_t)nx * ny * nz);
 }
 
 cudaError_t tc_denoise_apply(const clamp_denoiser* d, const float* in, float* out, int nx, int ny, int nz, void* ws,
@@ -876,6 +1135,23 @@ cudaError_t tc_denoise_apply(const clamp_denoiser* d, const float* in, float* ou
 // tensor-core kernels: per chunk of input channels [dz][dx][2 channel groups]
 // [dy = 2, 1, 0][npad][epv].  BF16: BF16 (RNE), epv = 8.  TF32x3: hi copy then lo copy,
 // FP32, epv = 4.  Output channels >= cout are zero.
+std::vector<uint8_t> pack_last_tc_weights(const float* W, int cin) {
+  std::vector<uint8_t> p((size_t)cin * 64, 0);
+  uint16_t* h = reinterpret_cast<uint16_t*>(p.data());
+  for (int c = 0; c < cin; ++c)
+    for (int tap = 0; tap < 27; ++tap) h[((c / 8) * 512 + tap * 16 + (c % 8) * 2) / 2] = bf16_bits(W[c * 27 + tap]);
+  return p;
+}
+
+std::vector<uint8_t> pack_first_tc_weights(const float* W, int cout) {
+  std::vector<uint8_t> p((size_t)cout * 64, 0);
+  uint16_t* h = reinterpret_cast<uint16_t*>(p.data());
+  for (int co = 0; co < cout; ++co)
+    for (int k = 0; k < 27; ++k)
+      h[((co / 8) * 512 + (k / 8) * 128 + (co % 8) * 16 + (k % 8) * 2) / 2] = bf16_bits(W[co * 27 + k]);
+  return p;
+}
+
 std::vector<uint8_t> pack_tc_weights(const float* W, int cin, int cout, int npad, bool bf16) {
   const int epv = bf16 ? 8 : 4, ch = 2 * epv, chunks = cin / ch;
   const size_t per = (size_t)chunks * 27 * 2 * npad * epv;  // elements per copy
