@@ -40,7 +40,7 @@ EXPORTS = [
     "clamp_iterate", "clamp_iterate_workspace_size", "clamp_mace_step_noalloc",
     "clamp_tc_gemm_bf16", "clamp_tc_gemm_tf32x3",
     "clamp_batch_workspace_size", "clamp_batch_create", "clamp_batch_launch", "clamp_batch_latencies",
-    "clamp_batch_residuals", "clamp_batch_destroy", "clamp_autotune", "clamp_autotune_set", "clamp_agent_schedule",
+    "clamp_batch_residuals", "clamp_batch_destroy", "clamp_autotune", "clamp_autotune_set", "clamp_agent_schedule", "clamp_autotune_set_band",
     "clamp_unet_create", "clamp_unet_destroy", "clamp_unet_param_count", "clamp_unet_get", "clamp_unet_set",
     "clamp_unet_workspace_size", "clamp_unet_forward", "clamp_unet_backward", "clamp_unet_adam",
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_autotune": (I, [PP, P, P, P, P, S, P, ctypes.POINTER(ctypes.c_int32)]),
         "clamp_autotune_set": (I, [PP, ctypes.POINTER(ctypes.c_int32)]),
         "clamp_agent_schedule": (I, [PP, P, P, P, ctypes.POINTER(ctypes.c_int32)]),
+        "clamp_autotune_set_band": (I, [PP, I]),
         "clamp_unet_create": (I, [I, I, I, I, P, ctypes.POINTER(P)]),
         "clamp_unet_destroy": (V, [P]),
         "clamp_unet_param_count": (ctypes.c_int64, [P]),
@@ -277,6 +278,11 @@ def autotune_set(p: Params, variants) -> None:
     _check(load().clamp_autotune_set(ctypes.byref(p), arr), "clamp_autotune_set")
 
 
+def autotune_set_band(p: Params, row_variant: int) -> None:
+    """Band-limited schedule's row pass for this geometry: 0 one tile per CTA, 1 persistent, pipelined."""
+    _check(load().clamp_autotune_set_band(ctypes.byref(p), row_variant), "clamp_autotune_set_band")
+
+
 def agent_schedule(p: Params, pupil, window, stream=None) -> dict:
     """The forward-agent schedule iterations with these parameters run, and the aperture's
     support and band column counts."""
@@ -321,7 +327,7 @@ def init(p: Params, y, pupil, window, r_init=None, ws=None, stream=None):
 
 
 def speckle_average(p: Params, y, pupil, window, out=None, ws=None, stream=None):
-    """r0 = (1/L) sum_l |A^H y_l / alpha|^2 (floored), device float32 [nz, ny, nx]."""
+    """r0 = (1/L) sum_l |A^H y_l|^2 (floored), device float32 [nz, ny, nx]."""
     import torch
     out = torch.empty((p.nz, p.ny, p.nx), dtype=torch.float32, device=y.device) if out is None else out
     ws = workspace(p) if ws is None else ws

@@ -441,7 +441,7 @@ static BandArgs band_args(const clamp_params* p, const Derived& d, const float* 
   a.s2 = at<double>(ws, al.s2);
   a.s3 = at<double>(ws, al.s3);
   a.s4 = at<double>(ws, al.s4);
-  a.px = band_px(p->nx, p->ny, p->nz);
+  a.px = band_px(p->nx, p->ny, p->nz, 0);
   return a;
 }
 
@@ -458,7 +458,8 @@ static clamp_status agent_ffts(const clamp_params* p, const Derived& d, const fl
       API_CUDA(launch_band_spectrum(a, p->looks, st), "F mu on the support");
     }
     a.gamma_prev = fresh ? nullptr : at<float>(ws, al.gamma);
-    API_CUDA(launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma), at<double>(ws, al.mures), st),
+    API_CUDA(launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma), at<double>(ws, al.mures),
+                               tuned_variants(d.g).band_x, st),
              "band-limited forward-agent passes");
     return CLAMP_OK;
   }
@@ -528,27 +529,35 @@ clamp_status autotune_agent(const clamp_params* p, const ReconPlan& d, const flo
     }
     full_ms += best_ms;
   }
-  // the band-limited schedule as a whole (tables from the real pupil: its indices come from them)
+  // the band-limited schedule as a whole, with each row-pass variant (tables from the real
+  // pupil: its indices come from them)
   best.schedule = 0;
   if (d.band_fits && !(p->flags & CLAMP_FLAG_NO_APERTURE)) {
     BandArgs a = band_args(p, d, y, window, mu, rp, al, ws);
     a.gamma_prev = at<float>(ws, al.gamma);
+    float band_ms = 1e30f;
     cudaError_t e = launch_band_tables(pupil, p->nx, p->ny, a.t, st);
-    if (e == cudaSuccess) e = launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma),
-                                                at<double>(ws, al.mures), st);
-    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
-      e = launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma), at<double>(ws, al.mures), st);
-    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    for (int xv = 0; xv < 2 && e == cudaSuccess; ++xv) {
+      e = launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma), at<double>(ws, al.mures), xv, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
+        e = launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma), at<double>(ws, al.mures), xv,
+                              st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < band_ms) {
+        band_ms = ms;
+        best.band_x = xv;
+      }
+    }
     if (e != cudaSuccess) {
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       return cuda_fail(e, "autotune (band-limited schedule)");
     }
-    best.schedule = ms <= full_ms ? 1 : 0;
+    best.schedule = band_ms <= full_ms ? 1 : 0;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -587,6 +596,16 @@ extern "C" clamp_status clamp_agent_schedule(const clamp_params* p, const float*
   info[1] = d.band.nS;
   info[2] = d.band.nbx;
   info[3] = d.band_fits ? 1 : 0;
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_autotune_set_band(const clamp_params* p, int32_t row_variant) {
+  API_TRY(clamp_check_params(p));
+  if (row_variant != 0 && row_variant != 1)
+    return api_fail(CLAMP_EINVAL, "clamp_autotune_set_band: row_variant=%d must be 0 or 1", row_variant);
+  Geom g{p->nx, p->ny, p->nz, p->looks, (long long)p->nx * p->ny * p->nz};
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[tune_key(g)].band_x = row_variant;
   return CLAMP_OK;
 }
 
@@ -788,7 +807,9 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
     }
     PassC c = passc_args(p, d, al, ws, mu, r, w, wbar, k);
     API_CUDA(launch_pass_c_fused(d.g, c, st), "fused prox + MACE pass");
-    if (ce_out) API_CUDA(launch_ce_final(c.part_num, c.part_den, al.nbc, ce_out + it, st), "CE residual");
+    if (ce_out)
+      API_CUDA(launch_ce_final(c.part_num, c.part_den, passc_fused_blocks(n, p->looks), ce_out + it, st),
+               "CE residual");
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 3], st), "event");
   }
   return CLAMP_OK;

@@ -28,6 +28,7 @@ __host__ __device__ constexpr int pipe_cols(int N) { return N > 128 ? 8 : 16; }
 struct AgentVariants {
   int v[5] = {0, 0, 0, 0, 0};
   int schedule = -1;   // forward-agent schedule: -1 not timed (band-limited when it fits), 0 full spectrum, 1 band-limited
+  int band_x = 0;      // band-limited row pass: 0 one tile per CTA, 1 persistent and pipelined
 };
 // True if variant V of pass `pass` can run on the geometry.
 bool variant_valid(int pass, int V, int nx, int ny, int nz);
@@ -94,13 +95,16 @@ BandShape band_shape(const float* pupil_host, int nx, int ny);
 size_t band_table_bytes(const BandShape& b, int nx, int ny);
 BandTables band_tables_at(const BandShape& b, int nx, int ny, void* base);
 int band_pS(const BandShape& b);
-int band_px(int nx, int ny, int nz);
+// S1 / S3 partial sums per look of the row pass (x_variant 0: one tile per CTA; 1: persistent, pipelined).
+int band_px(int nx, int ny, int nz, int x_variant);
 // Builds the device tables from the device pupil (one CTA).
 cudaError_t launch_band_tables(const float* pupil, int nx, int ny, const BandTables& t, cudaStream_t st);
 // Ms <- F mu on the support (first axis x over whole rows, then y and z on band / support).
 cudaError_t launch_band_spectrum(const BandArgs& a, int L, cudaStream_t st);
 // P1-P5 and the line search: d, F d on the support, gamma_l and the floored mu-residual per look.
-cudaError_t launch_band_agent(const BandArgs& a, int L, float nv, float* gamma, double* mures, cudaStream_t st);
+// x_variant: 0 the one-tile row pass, 1 the persistent cp.async-pipelined row pass.
+cudaError_t launch_band_agent(const BandArgs& a, int L, float nv, float* gamma, double* mures, int x_variant,
+                              cudaStream_t st);
 
 // ---- forward agent (Alg. 2 steps 6-8): pass A (x, y), fused z pass, pass B (y, x)
 // p.pz / p.px receive the partial counts per look the chosen variants produce.
@@ -142,6 +146,8 @@ struct PassC {
   int closed_mu;     // 1: mu = d / (1 + sigma_w^2 / (r' + sigma_w^2)) with d holding F^H y (no aperture)
 };
 int passc_blocks(long long n);
+// CTAs (and CE partial sums) of launch_pass_c_fused; at most passc_blocks(n).
+int passc_fused_blocks(long long n, int L);
 // mu <- mu + gamma_l d for all looks (the mu half of pass C: Eq. mu-update).
 cudaError_t launch_mu_update(const Geom& g, float2* mu, const float2* d, const float* gamma, cudaStream_t st);
 cudaError_t launch_pass_c_fused(const Geom& g, const PassC& c, cudaStream_t st);

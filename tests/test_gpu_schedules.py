@@ -59,10 +59,10 @@ def _problem(shape, L, pupil_kind, seed):
     return wl, a, y32
 
 
-@pytest.mark.parametrize("flag", ["full", "band"])
+@pytest.mark.parametrize("flag", ["full", "band", "band_pipelined"])
 @pytest.mark.parametrize("shape,L,pupil_kind", [((64, 32, 16), 2, "circle"), ((96, 96, 32), 1, "circle"),
                                                  ((16, 8, 8), 1, "one_column"), ((96, 32, 16), 3, "ragged"),
-                                                 ((32, 32, 16), 2, "wide")])
+                                                 ((32, 32, 16), 2, "wide"), ((256, 16, 8), 2, "circle")])
 def test_forward_prox_both_schedules(C, flag, shape, L, pupil_kind):
     wl, a, y32 = _problem(shape, L, pupil_kind, seed=sum(shape) + L)
     alpha = O.alpha_of(a)
@@ -77,10 +77,14 @@ def test_forward_prox_both_schedules(C, flag, shape, L, pupil_kind):
             for l in range(L)]
     f = C.FLAG_FULL_SPECTRUM if flag == "full" else C.FLAG_BAND_SPECTRUM
     p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var, flags=f)
+    C.autotune_set_band(p, 1 if flag == "band_pipelined" else 0)
     mu, r, wd = to_dev(mu0), to_dev(r0), to_dev(w0)
     mres = torch.zeros((), dtype=torch.float64, device="cuda")
-    C.forward_prox(p, 3, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), mu, r, wd, mu_residual=mres)
-    torch.cuda.synchronize()
+    try:
+        C.forward_prox(p, 3, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), mu, r, wd, mu_residual=mres)
+        torch.cuda.synchronize()
+    finally:
+        C.autotune_set_band(p, 0)
     for l in range(L):
         assert rel(mu[l].cpu().numpy(), refs[l][0]) < 1e-5, l
         assert rel(r[l].cpu().numpy(), refs[l][1]) < 1e-5, l
@@ -97,15 +101,20 @@ def test_reconstruct_both_schedules(C, shape, L, pupil_kind):
     ref, st = O.reconstruct(y32.astype(np.complex128), wl.pupil, wl.window, wl.denoiser, wl.noise_var,
                             wl.prox_var, 6)
     out = {}
-    for flag in ("full", "band"):
+    for flag in ("full", "band", "band_pipelined"):
         f = C.FLAG_FULL_SPECTRUM if flag == "full" else C.FLAG_BAND_SPECTRUM
         p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var, max_iters=6, flags=f)
-        res = C.reconstruct(p, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), C.Denoiser.gauss(0.8))
+        C.autotune_set_band(p, 1 if flag == "band_pipelined" else 0)
+        try:
+            res = C.reconstruct(p, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), C.Denoiser.gauss(0.8))
+        finally:
+            C.autotune_set_band(p, 0)
         out[flag] = res.r.cpu().numpy()
         assert rel(out[flag], ref) < 1e-4, flag
         np.testing.assert_allclose(res.ce_hist, st.ce_hist, rtol=1e-3)
         np.testing.assert_allclose(res.mu_hist, st.mu_res_hist, rtol=1e-3)
     assert rel(out["band"], out["full"]) < 2e-5
+    assert rel(out["band_pipelined"], out["band"]) < 2e-5
 
 
 def test_band_schedule_long_run_tracks_oracle(C):
