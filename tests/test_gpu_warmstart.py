@@ -1,9 +1,10 @@
 """The learned warm start against plain CLAMP: the U-Net trained by the library's own
 kernels (weights in paper_2406_13651_gb300/weights/) must reach the convergence error
-1e-3 in fewer iterations and less wall time than the speckle-average initialisation,
-on held-out scenes and at 256x256x128, with the same reflectance (relative distance to
-the plain solution run twice as long); and a short training run from scratch must
-learn (validation loss far below that of the identity map)."""
+1e-3 at the same reflectance error as the speckle-average initialisation (distance to
+the long plain solution no larger than the plain run's at its own CE 1e-3 stop) in fewer
+iterations and less wall time, on held-out scenes and at 256x256x128; and a short
+training run from scratch must learn (validation loss far below that of the identity
+map)."""
 import os
 
 import numpy as np
@@ -56,9 +57,10 @@ def test_warm_start_gain_heldout_64(env):
         sp["snr"] = 7.5
         p, y, pu, wi = W.scene_data(sp, dev)
         c = W.compare(net, p, y, pu, wi, den, tol=1e-3, max_iters=400)
-        assert c["plain"]["converged"] and c["warm"]["converged"], c
+        assert c["plain"]["reached"] and c["warm"]["reached"], c
         assert c["warm"]["iters"] < c["plain"]["iters"], c
-        assert c["warm"]["rel_err_vs_ref"] < 2e-2, c
+        assert c["warm"]["rel_err_vs_ref"] <= c["plain"]["rel_err_vs_ref"], c
+        assert c["warm"]["ce_final"] <= 1e-3, c
         gains.append(1 - c["warm"]["iters"] / c["plain"]["iters"])
     assert np.mean(gains) > 0.15, gains
 
@@ -75,8 +77,10 @@ def test_warm_start_gain_256(env):
     y = C.simulate(p, torch.from_numpy(wl.r_true.astype(np.float32)).to(dev), spk, eta, pu, wi)
     del spk, eta
     c = W.compare(net, p, y, pu, wi, den, tol=1e-3, max_iters=wl.iters, r_true=wl.r_true)
-    assert c["plain"]["converged"] and c["warm"]["converged"], c
+    print({k: c[k] for k in ("plain", "warm", "warm_ce_only", "error_target")})
+    assert c["plain"]["reached"] and c["warm"]["reached"], c
     assert c["warm"]["iters"] < c["plain"]["iters"], c
     assert c["warm"]["seconds"] < c["plain"]["seconds"], c
-    assert c["warm"]["rel_err_vs_ref"] < 2e-2, c
+    assert c["warm"]["rel_err_vs_ref"] <= c["plain"]["rel_err_vs_ref"], c
+    assert c["warm"]["ce_final"] <= 1e-3, c
     assert c["warm"]["psnr"] > c["plain"]["psnr"] - 0.5, c
