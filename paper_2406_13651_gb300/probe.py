@@ -31,6 +31,8 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--schedule", choices=["auto", "band", "full"], default="auto")
     ap.add_argument("--prior", choices=["gauss", "cnn-bf16", "cnn-fp32"], default="gauss")
+    ap.add_argument("--band-row", type=int, choices=[-1, 0, 1], default=-1,
+                    help="band-limited row pass variant (0 one tile per CTA, 1 pipelined; -1 autotune)")
     ap.add_argument("--dtype", choices=["fp32", "bf16"], default="bf16")
     a = ap.parse_args(argv)
     B.build()
@@ -74,6 +76,10 @@ def main(argv=None) -> int:
         layers, ch = (8, 48) if dt == "bf16" else (5, 32)
         w_, b_ = I.cnn_weights(layers, ch, seed=1)
         den = C.Denoiser.cnn(w_, b_, dt)
+    if a.band_row < 0:
+        C.autotune(p, y, pupil, window)
+    else:
+        C.autotune_set_band(p, a.band_row)
     mu, r, w = C.init(p, y, pupil, window)
     wbar = torch.empty((nz, ny, nx), device=dev)
     ws = C.iterate_workspace(p, den)
@@ -85,6 +91,7 @@ def main(argv=None) -> int:
     torch.cuda.synchronize()
     sched = C.agent_schedule(p, pupil, window)
     print(json.dumps({"probe": "agent", "shape": [nx, ny, nz], "looks": L, "schedule": sched, "prior": a.prior,
+                      "band_row": a.band_row,
                       "ms_per_iteration": e0.elapsed_time(e1) / a.iters}), flush=True)
     return 0
 
