@@ -293,17 +293,17 @@ clamp_status clamp_autotune(const clamp_params* p, const float* y, const float* 
                             void* ws, size_t ws_bytes, void* stream, int32_t* variants_out);
 /* Sets the cached choice for a geometry by hand (host int32[5]). */
 clamp_status clamp_autotune_set(const clamp_params* p, const int32_t* variants);
-/* Sets the band-limited schedule's row-pass variant for a geometry (0: one tile of rows per
- * CTA; 1: persistent CTAs that prefetch the next tile's mu, r' and band rows with cp.async
- * while the current tile's transforms run), keeping the other cached choices.  clamp_autotune
- * times both and keeps the faster. */
+/* Sets the band-limited schedule's row-pass variant for a geometry (0: the default tile of
+ * rows per CTA; 1: tiles of half as many rows, three CTAs per SM), keeping the other cached
+ * choices.  clamp_autotune times both and keeps the faster. */
 clamp_status clamp_autotune_set_band(const clamp_params* p, int32_t row_variant);
 /* Which forward-agent schedule iterations with these parameters and this aperture run
  * (CLAMP_FLAG_*_SPECTRUM, the autotuner's cached choice, else the band-limited one when its
- * arrays fit the scratch).  pupil [ny][nx], window [nz]: device.  info (host int32[4]):
+ * arrays fit the scratch).  pupil [ny][nx], window [nz]: device.  info (host int32[5]):
  * schedule (1 band-limited, 0 full spectrum), the support's column count |{(ky, kx):
- * pupil != 0}|, the band's column count |{kx: some pupil(ky, kx) != 0}|, and 1 if the
- * band-limited arrays fit.  Reads the pupil back (synchronises `stream`). */
+ * pupil != 0}|, the band's column count |{kx: some pupil(ky, kx) != 0}|, 1 if the
+ * band-limited arrays fit, and the band-limited row-pass variant (clamp_autotune_set_band).
+ * Reads the pupil back (synchronises `stream`). */
 clamp_status clamp_agent_schedule(const clamp_params* p, const float* pupil, const float* window, void* stream,
                                   int32_t* info);
 

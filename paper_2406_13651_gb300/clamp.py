@@ -279,18 +279,18 @@ def autotune_set(p: Params, variants) -> None:
 
 
 def autotune_set_band(p: Params, row_variant: int) -> None:
-    """Band-limited schedule's row pass for this geometry: 0 one tile per CTA, 1 persistent, pipelined."""
+    """Band-limited schedule's row pass for this geometry: 0 the default row tile, 1 half-height tiles."""
     _check(load().clamp_autotune_set_band(ctypes.byref(p), row_variant), "clamp_autotune_set_band")
 
 
 def agent_schedule(p: Params, pupil, window, stream=None) -> dict:
     """The forward-agent schedule iterations with these parameters run, and the aperture's
     support and band column counts."""
-    info = (ctypes.c_int32 * 4)()
+    info = (ctypes.c_int32 * 5)()
     _check(load().clamp_agent_schedule(ctypes.byref(p), _ptr(pupil), _ptr(window), _stream(stream), info),
            "clamp_agent_schedule")
     return {"schedule": "band-limited" if info[0] else "full spectrum", "support_columns": int(info[1]),
-            "band_columns": int(info[2]), "band_fits": bool(info[3])}
+            "band_columns": int(info[2]), "band_fits": bool(info[3]), "row_pass_variant": int(info[4])}
 
 
 def fft3(x, inverse: bool = False, out=None, stream=None):

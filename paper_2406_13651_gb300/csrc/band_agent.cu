@@ -230,9 +230,14 @@ enum BandRowMode { BAND_GRAD = 0, BAND_SPEC = 1 };
 
 // BAND_GRAD: e = inverse x-FFT of the band row, d = e - D mu (written), S1/S3, forward x-FFT
 // of d kept on the band.  BAND_SPEC: forward x-FFT of mu kept on the band (F mu's first axis).
-template <int N, int MODE>
-__global__ void __launch_bounds__(NT) k_band_x(BandArgs a, const float2* __restrict__ tw) {
-  constexpr int LX = rows_per_cta(N), LD = N + 1, CNT = LX * N, PER = (CNT + NT - 1) / NT;
+// Launch variant V = 0: rows_per_cta(N) rows per CTA; V = 1: half as many rows, so a thread
+// holds half the prefetched values and three CTAs share an SM (at N = 256 with the
+// 8 x 8 x 4 radix plan, whose stages keep all threads of an 8-row tile busy).
+template <int N, int MODE, int V>
+__global__ void __launch_bounds__(NT, V == 1 ? 3 : 1) k_band_x(BandArgs a, const float2* __restrict__ tw) {
+  constexpr int LX = V == 1 ? variant_rows(N, 2) : rows_per_cta(N), LD = N + 1, CNT = LX * N,
+                PER = (CNT + NT - 1) / NT;
+  using PL = std::conditional_t<V == 1 && N == 256, PlanB<N>, Plan<N>>;
   float2* sm = reinterpret_cast<float2*>(band_smem);
   const long long row0 = (long long)blockIdx.x * LX;   // rows over [L][nz][ny]
   const long long e0 = row0 * N;
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(NT) k_band_x(BandArgs a, const float2* __restr
   __syncthreads();
   float acc[2] = {0.f, 0.f};
   if constexpr (MODE == BAND_GRAD) {
-    fft_tile<N, LX, NT, true>(sm, tw);
+    fft_tile<N, LX, NT, true, PL>(sm, tw);
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
       const int e = threadIdx.x + p * NT;
@@ -280,7 +285,7 @@ __global__ void __launch_bounds__(NT) k_band_x(BandArgs a, const float2* __restr
     }
     __syncthreads();
   }
-  fft_tile<N, LX, NT, false>(sm, tw);
+  fft_tile<N, LX, NT, false, PL>(sm, tw);
   // band of the forward transform: LX rows x nbxp columns (padding columns get zeros)
   const int nbxp = a.t.nbxp;
   for (int e = threadIdx.x; e < LX * nbxp; e += NT) {
@@ -293,101 +298,6 @@ __global__ void __launch_bounds__(NT) k_band_x(BandArgs a, const float2* __restr
     const long long rows_per_look = (long long)a.nz * a.ny;
     const long long look = row0 / rows_per_look;
     block_sums<2>(acc, outs, look * a.px + (row0 - look * rows_per_look) / LX);
-  }
-}
-
-// Persistent, pipelined BAND_GRAD row pass (launch variant 1): CTAs walk tiles of LXP rows
-// t = blockIdx.x, blockIdx.x + G, ...; while a tile's two FFTs run, cp.async copies of the
-// next tile's mu, r' and band rows are in flight into the other of two input buffers.
-// Dynamic shared memory: one FFT tile [LXP][N + 1] float2, then two input stages of
-// mu [LXP][N] float2, r' [LXP][N] float, band rows [LXP][nbxp] float2.
-__device__ __forceinline__ uint32_t band_sptr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-template <int N>
-__global__ void __launch_bounds__(NT, 2) k_band_x_pipe(BandArgs a, const float2* __restrict__ tw, int ntiles) {
-  constexpr int LXP = variant_rows(N, 3), LD = N + 1, CNT = LXP * N, PER = (CNT + NT - 1) / NT;
-  // radix-16 stages keep 16 points per thread live at N = 256: the 8 x 8 x 4 plan stays in registers
-  using PL = std::conditional_t<N == 256, PlanB<N>, Plan<N>>;
-  const int nbxp = a.t.nbxp, nbx = a.t.nbx;
-  float2* sm = reinterpret_cast<float2*>(band_smem);
-  float* stage0 = reinterpret_cast<float*>(sm + LXP * LD);
-  const int STAGE = 3 * CNT + 2 * LXP * nbxp;   // floats
-  auto issue = [&](int t, float* st) {
-    float2* mb = reinterpret_cast<float2*>(st);
-    float* rb = st + 2 * CNT;
-    float2* eb = reinterpret_cast<float2*>(st + 3 * CNT);
-    const long long e0 = (long long)t * CNT, row0 = (long long)t * LXP;
-#pragma unroll 1
-    for (int p = 0; p < PER; ++p) {
-      const int e = threadIdx.x + p * NT;
-      if (CNT % NT == 0 || e < CNT) {
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(band_sptr(&mb[e])), "l"(&a.mu[e0 + e]) : "memory");
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(band_sptr(&rb[e])), "l"(&a.rprev[e0 + e])
-                     : "memory");
-      }
-    }
-    for (int e = threadIdx.x; e < LXP * nbx; e += NT) {
-      const int line = e / nbx, b = e - line * nbx;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(band_sptr(&eb[line * nbxp + b])),
-                   "l"(&a.band[(row0 + line) * nbxp + b])
-                   : "memory");
-    }
-  };
-  const long long rows_per_look = (long long)a.nz * a.ny;
-  int stage = 0, t = blockIdx.x;
-  if (t < ntiles) issue(t, stage0);
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  for (; t < ntiles; t += gridDim.x) {
-    if (t + (int)gridDim.x < ntiles) issue(t + gridDim.x, stage0 + (stage ^ 1) * STAGE);
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
-    __syncthreads();
-    const float* st = stage0 + stage * STAGE;
-    const float2* mb = reinterpret_cast<const float2*>(st);
-    const float* rb = st + 2 * CNT;
-    const float2* eb = reinterpret_cast<const float2*>(st + 3 * CNT);
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int e = threadIdx.x + p * NT;
-      if (CNT % NT == 0 || e < CNT) {
-        const int line = e / N, i = e - line * N;
-        const int b = __ldg(&a.t.bpos[i]);
-        sm[line * LD + i] = b >= 0 ? eb[line * nbxp + b] : make_float2(0.f, 0.f);
-      }
-    }
-    __syncthreads();
-    fft_tile<N, LXP, NT, true, PL>(sm, tw);
-    const long long e0 = (long long)t * CNT;
-    float acc[2] = {0.f, 0.f};
-#pragma unroll
-    for (int p = 0; p < PER; ++p) {
-      const int e = threadIdx.x + p * NT;
-      if (CNT % NT == 0 || e < CNT) {
-        const int line = e / N, i = e - line * N;
-        const float2 ee = cscale(sm[line * LD + i], a.sc_x);
-        const float D = 1.0f / (rb[e] + a.floor);
-        const float2 mv = mb[e];
-        const float2 dv = make_float2(fmaf(-D, mv.x, ee.x), fmaf(-D, mv.y, ee.y));
-        a.d[e0 + e] = dv;
-        const float d2 = cabs2(dv);
-        acc[0] += d2;
-        acc[1] += D * d2;
-        sm[line * LD + i] = dv;
-      }
-    }
-    __syncthreads();
-    fft_tile<N, LXP, NT, false, PL>(sm, tw);
-    const long long row0 = (long long)t * LXP;
-    for (int e = threadIdx.x; e < LXP * nbxp; e += NT) {
-      const int line = e / nbxp, b = e - line * nbxp;
-      const int kx = __ldg(&a.t.bx[b]);
-      a.band[(row0 + line) * nbxp + b] = kx >= 0 ? cscale(sm[line * LD + kx], a.sc_x) : make_float2(0.f, 0.f);
-    }
-    const long long look = row0 / rows_per_look;
-    double* const outs[2] = {a.s1, a.s3};
-    block_sums<2>(acc, outs, look * a.px + (row0 - look * rows_per_look) / LXP);
-    __syncthreads();
-    stage ^= 1;
   }
 }
 
@@ -529,34 +439,25 @@ cudaError_t run_y(const BandArgs& a, int L, bool inverse, cudaStream_t st) {
   });
 }
 
-int g_sm_count = 0;
-
 cudaError_t run_x(const BandArgs& a, int L, int mode, int variant, cudaStream_t st) {
   return dispatch_n(a.nx, [&](auto NC) -> cudaError_t {
     constexpr int N = decltype(NC)::value;
+    if (mode == BAND_GRAD && variant == 1) {
+      constexpr int LX = variant_rows(N, 2);
+      const size_t smem = (size_t)LX * (N + 1) * sizeof(float2);
+      BAND_TRY(smem_attr(k_band_x<N, BAND_GRAD, 1>, smem));
+      k_band_x<N, BAND_GRAD, 1><<<(unsigned)((long long)L * a.nz * a.ny / LX), NT, smem, st>>>(a, twiddle_table(N));
+      return cudaGetLastError();
+    }
     constexpr int LX = rows_per_cta(N);
     const size_t smem = (size_t)LX * (N + 1) * sizeof(float2);
     const unsigned grid = (unsigned)((long long)L * a.nz * a.ny / LX);
-    if (mode == BAND_GRAD && variant == 1) {
-      constexpr int LXP = variant_rows(N, 3);
-      const int ntiles = (int)((long long)L * a.nz * a.ny / LXP);
-      const size_t sm_p = sizeof(float2) * LXP * (N + 1) + 2 * sizeof(float) * (3 * LXP * N + 2 * LXP * a.t.nbxp);
-      BAND_TRY(smem_attr(k_band_x_pipe<N>, sm_p));
-      if (g_sm_count == 0) {
-        int dev = 0;
-        BAND_TRY(cudaGetDevice(&dev));
-        BAND_TRY(cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev));
-      }
-      const int gridp = ntiles < 2 * g_sm_count ? ntiles : 2 * g_sm_count;
-      k_band_x_pipe<N><<<gridp, NT, sm_p, st>>>(a, twiddle_table(N), ntiles);
-      return cudaGetLastError();
-    }
     if (mode == BAND_GRAD) {
-      BAND_TRY(smem_attr(k_band_x<N, BAND_GRAD>, smem));
-      k_band_x<N, BAND_GRAD><<<grid, NT, smem, st>>>(a, twiddle_table(N));
+      BAND_TRY(smem_attr(k_band_x<N, BAND_GRAD, 0>, smem));
+      k_band_x<N, BAND_GRAD, 0><<<grid, NT, smem, st>>>(a, twiddle_table(N));
     } else {
-      BAND_TRY(smem_attr(k_band_x<N, BAND_SPEC>, smem));
-      k_band_x<N, BAND_SPEC><<<grid, NT, smem, st>>>(a, twiddle_table(N));
+      BAND_TRY(smem_attr(k_band_x<N, BAND_SPEC, 0>, smem));
+      k_band_x<N, BAND_SPEC, 0><<<grid, NT, smem, st>>>(a, twiddle_table(N));
     }
     return cudaGetLastError();
   });
@@ -611,7 +512,7 @@ BandTables band_tables_at(const BandShape& b, int nx, int ny, void* base) {
 
 int band_pS(const BandShape& b) { return b.nSp / BC; }
 int band_px(int nx, int ny, int nz, int x_variant) {
-  return (int)((long long)nz * ny / (x_variant == 1 ? variant_rows(nx, 3) : rows_per_cta(nx)));
+  return (int)((long long)nz * ny / (x_variant == 1 ? variant_rows(nx, 2) : rows_per_cta(nx)));
 }
 
 cudaError_t launch_band_tables(const float* pupil, int nx, int ny, const BandTables& t, cudaStream_t st) {

@@ -10,6 +10,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <map>
 #include <mutex>
 #include <set>
@@ -596,6 +598,7 @@ extern "C" clamp_status clamp_agent_schedule(const clamp_params* p, const float*
   info[1] = d.band.nS;
   info[2] = d.band.nbx;
   info[3] = d.band_fits ? 1 : 0;
+  info[4] = tuned_variants(d.g).band_x;
   return CLAMP_OK;
 }
 
@@ -763,6 +766,13 @@ static SideStream* side_stream(cudaStream_t st) {
   return &ss;
 }
 
+// Named NVTX range around the host-side enqueue of a phase (shows each iteration's forward
+// agents, prior agent and MACE step on a profiler's timeline; no cost without a tool).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 // One to many loop bodies of Alg. 2 on the state (mu, r, w); ws = agent scratch then denoiser scratch.
 // `spectrum_ready`: the agent scratch already holds the band-limited schedule's F mu for this
 // mu, one pending step behind (a previous call of the same run); otherwise it is rebuilt.
@@ -780,8 +790,10 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
   SideStream* ss = prior_concurrent(p) ? side_stream(st) : nullptr;
   for (int it = 0; it < iters; ++it) {
     const int k = k_first + it;
+    NvtxRange r_it("clamp iteration");
     if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 0], st), "event");
     if (ss) {
+      NvtxRange r_prior("prior agent (side stream)");
       API_CUDA(cudaEventRecord(ss->fork, st), "event");
       API_CUDA(cudaStreamWaitEvent(ss->s, ss->fork, 0), "event");
       API_CUDA(denoise_apply(den, w + (long long)p->looks * n, r + (long long)p->looks * n, p->nx, p->ny, p->nz,
@@ -793,6 +805,7 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
     if (noap) {
       if (mu_out) API_CUDA(cudaMemsetAsync(mu_out + it, 0, sizeof(double), st), "mu residual");
     } else {
+      NvtxRange r_agents("forward agents");
       API_TRY(agent_ffts(p, d, y, pupil, window, mu, r, al, ws, it == 0 && !spectrum_ready, st));
       if (mu_out) API_CUDA(launch_mean(at<double>(ws, al.mures), p->looks, mu_out + it, st), "mu residual");
     }
@@ -800,11 +813,13 @@ static clamp_status iterate_impl(const clamp_params* p, const Derived& d, int k_
     if (ss) {
       API_CUDA(cudaStreamWaitEvent(st, ss->join, 0), "event");
     } else {
+      NvtxRange r_prior("prior agent");
       API_CUDA(denoise_apply(den, w + (long long)p->looks * n, r + (long long)p->looks * n, p->nx, p->ny, p->nz,
                              dws, at<int>(ws, al.err), st),
                "denoiser");
       if (events) API_CUDA(cudaEventRecord((cudaEvent_t)events[4 * it + 2], st), "event");
     }
+    NvtxRange r_mace("prox + MACE step");
     PassC c = passc_args(p, d, al, ws, mu, r, w, wbar, k);
     API_CUDA(launch_pass_c_fused(d.g, c, st), "fused prox + MACE pass");
     if (ce_out)

@@ -669,7 +669,8 @@ int passc_blocks(long long n) {
 // The fused pass reads every look's r and w of a voxel twice (the look sum, then the Mann
 // step), so the second read hits L2 only while the rows all resident threads hold fit in
 // it: the grid keeps them near 48 MB (16 bytes per voxel pair and row), in whole waves of
-// 152 SMs, between 1 and 8 CTAs per SM.
+// 152 SMs, between 1 and 8 CTAs per SM.  (A 64 MB grid with 64 registers per thread ran the
+// pass faster but left more dirty lines in L2 for the next iteration's passes: slower overall.)
 int passc_fused_blocks(long long n, int L) {
   const long long threads = (48LL << 20) / (16LL * (L + 1));
   long long b = (threads + NT - 1) / NT;

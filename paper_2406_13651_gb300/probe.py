@@ -32,7 +32,7 @@ def main(argv=None) -> int:
     ap.add_argument("--schedule", choices=["auto", "band", "full"], default="auto")
     ap.add_argument("--prior", choices=["gauss", "cnn-bf16", "cnn-fp32"], default="gauss")
     ap.add_argument("--band-row", type=int, choices=[-1, 0, 1], default=-1,
-                    help="band-limited row pass variant (0 one tile per CTA, 1 pipelined; -1 autotune)")
+                    help="band-limited row pass variant (0 default row tile, 1 half-height tiles; -1 autotune)")
     ap.add_argument("--dtype", choices=["fp32", "bf16"], default="bf16")
     a = ap.parse_args(argv)
     B.build()
