@@ -230,11 +230,13 @@ enum BandRowMode { BAND_GRAD = 0, BAND_SPEC = 1 };
 
 // BAND_GRAD: e = inverse x-FFT of the band row, d = e - D mu (written), S1/S3, forward x-FFT
 // of d kept on the band.  BAND_SPEC: forward x-FFT of mu kept on the band (F mu's first axis).
-// Launch variant V = 0: rows_per_cta(N) rows per CTA; V = 1: half as many rows, so a thread
-// holds half the prefetched values and three CTAs share an SM (at N = 256 with the
+// Launch variant V = 0: rows_per_cta(N) rows per CTA, two CTAs per SM (at most 128
+// registers: with no occupancy bound the compiler takes about 180 and one CTA runs per SM,
+// 0.5 ms slower per iteration at 256x256x128, L = 32); V = 1: half as many rows, so a
+// thread holds half the prefetched values and three CTAs share an SM (at N = 256 with the
 // 8 x 8 x 4 radix plan, whose stages keep all threads of an 8-row tile busy).
 template <int N, int MODE, int V>
-__global__ void __launch_bounds__(NT, V == 1 ? 3 : 1) k_band_x(BandArgs a, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(NT, V == 1 ? 3 : 2) k_band_x(BandArgs a, const float2* __restrict__ tw) {
   constexpr int LX = V == 1 ? variant_rows(N, 2) : rows_per_cta(N), LD = N + 1, CNT = LX * N,
                 PER = (CNT + NT - 1) / NT;
   using PL = std::conditional_t<V == 1 && N == 256, PlanB<N>, Plan<N>>;
@@ -243,6 +245,9 @@ __global__ void __launch_bounds__(NT, V == 1 ? 3 : 1) k_band_x(BandArgs a, const
   const long long e0 = row0 * N;
   float2 mv[PER], ev[PER];
   float rv[PER];
+  // with NT a multiple of N every element a thread touches is in the same column
+  constexpr bool FIXED_COL = NT % N == 0;
+  const int b_fixed = FIXED_COL && MODE == BAND_GRAD ? __ldg(&a.t.bpos[threadIdx.x % N]) : -1;
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
@@ -251,7 +256,7 @@ __global__ void __launch_bounds__(NT, V == 1 ? 3 : 1) k_band_x(BandArgs a, const
       if constexpr (MODE == BAND_GRAD) {
         rv[p] = a.rprev[e0 + e];
         const int line = e / N, i = e - line * N;
-        const int b = __ldg(&a.t.bpos[i]);
+        const int b = FIXED_COL ? b_fixed : __ldg(&a.t.bpos[i]);
         ev[p] = b >= 0 ? a.band[(row0 + line) * a.t.nbxp + b] : make_float2(0.f, 0.f);
       }
     }
@@ -274,7 +279,7 @@ __global__ void __launch_bounds__(NT, V == 1 ? 3 : 1) k_band_x(BandArgs a, const
       if (CNT % NT == 0 || e < CNT) {
         const int line = e / N, i = e - line * N;
         const float2 ee = cscale(sm[line * LD + i], a.sc_x);
-        const float D = 1.0f / (rv[p] + a.floor);
+        const float D = __frcp_rn(rv[p] + a.floor);
         const float2 dv = make_float2(fmaf(-D, mv[p].x, ee.x), fmaf(-D, mv[p].y, ee.y));
         a.d[e0 + e] = dv;
         const float d2 = cabs2(dv);
@@ -287,11 +292,14 @@ __global__ void __launch_bounds__(NT, V == 1 ? 3 : 1) k_band_x(BandArgs a, const
   }
   fft_tile<N, LX, NT, false, PL>(sm, tw);
   // band of the forward transform: LX rows x nbxp columns (padding columns get zeros)
+  // (a warp per row at a time, lanes over the band columns: no division by nbxp)
   const int nbxp = a.t.nbxp;
-  for (int e = threadIdx.x; e < LX * nbxp; e += NT) {
-    const int line = e / nbxp, b = e - line * nbxp;
-    const int kx = __ldg(&a.t.bx[b]);
-    a.band[(row0 + line) * nbxp + b] = kx >= 0 ? cscale(sm[line * LD + kx], a.sc_x) : make_float2(0.f, 0.f);
+  for (int line = threadIdx.x >> 5; line < LX; line += NT / 32) {
+    float2* brow = a.band + (row0 + line) * nbxp;
+    for (int b = threadIdx.x & 31; b < nbxp; b += 32) {
+      const int kx = __ldg(&a.t.bx[b]);
+      brow[b] = kx >= 0 ? cscale(sm[line * LD + kx], a.sc_x) : make_float2(0.f, 0.f);
+    }
   }
   if constexpr (MODE == BAND_GRAD) {
     double* const outs[2] = {a.s1, a.s3};

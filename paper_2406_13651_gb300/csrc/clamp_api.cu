@@ -640,6 +640,8 @@ static PassC passc_args(const clamp_params* p, const Derived& d, const AgentLayo
   c.alpha = d.s.alpha;
   c.prox_var = p->prox_var;
   c.beta = k > 0 ? beta_of(k) : 1.0f;
+  c.inv_prox_var = (float)(1.0 / (double)p->prox_var);
+  c.inv_beta = (float)(1.0 / (double)c.beta);
   c.ups_look = (float)((1.0 - (double)p->prior_weight) / p->looks);
   c.ups_prior = p->prior_weight;
   c.rho = p->rho;

@@ -597,15 +597,19 @@ cudaError_t launch_mean(const double* v, int L, double* out, cudaStream_t st) {
 // App. A reflectance update for one voxel of one look: quadratic fit of the
 // derivative of Q (Eq. convex-surrogate) between r' and xi, closed-form prox,
 // clip to the validity interval.
-__device__ __forceinline__ float prox_quad(float v, float rp, float K, float s2, float beta) {
-  const float inv = 1.0f / rp;
+// Divisions are reciprocals: 1/xi follows from 1/r' (xi = r' / beta or beta r'), and
+// 1/sigma^2, 1/beta come from the host, so a voxel takes two correctly rounded reciprocals.
+__device__ __forceinline__ float prox_quad(float v, float rp, float K, float s2, float inv_s2, float beta,
+                                           float inv_beta) {
+  const float inv = __frcp_rn(rp);
   const float qr = fmaf(-K * inv, inv, inv);           // 1/r' - K/r'^2
-  const float drho = qr + (rp - v) / s2;
-  const float xi = drho > 0.0f ? rp / beta : beta * rp;
-  const float ixi = 1.0f / xi;
+  const float drho = fmaf(rp - v, inv_s2, qr);
+  const bool down = drho > 0.0f;                        // the minimiser lies below r'
+  const float xi = down ? rp * inv_beta : beta * rp;
+  const float ixi = down ? beta * inv : inv * inv_beta;
   const float aq = K * (xi + rp) * (inv * inv) * (ixi * ixi);
   const float bq = fmaf(-aq, rp, qr);
-  const float rn = (v - s2 * bq) / fmaf(s2, aq, 1.0f);
+  const float rn = (v - s2 * bq) * __frcp_rn(fmaf(s2, aq, 1.0f));
   const float lo = fminf(rp, xi), hi = fmaxf(rp, xi);
   return fminf(fmaxf(rn, lo), hi);
 }
@@ -732,10 +736,10 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
           m.y = fmaf(gm, dd.y, m.y);
         }
         MUo[i] = m;
-        const float cc = c.nv * rp / fmaf(c.alpha, rp, c.nv);
+        const float cc = c.nv * rp * __frcp_rn(fmaf(c.alpha, rp, c.nv));
         const float K = cc + cabs2(m);
         if constexpr (EXACT) rn = (float)prox_exact((double)wl, (double)K, (double)c.prox_var);
-        else rn = prox_quad(wl, rp, K, c.prox_var, c.beta);
+        else rn = prox_quad(wl, rp, K, c.prox_var, c.inv_prox_var, c.beta, c.inv_beta);
         Ro[i] = rn;
         bad |= !isfinite(rn) || !isfinite(K);   // K covers mu: the prox's clip would hide a NaN there
       } else {
@@ -785,7 +789,9 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
 // Fused pass C on pairs of adjacent voxels: the same arithmetic as k_pass_c<true, true,
 // false> per voxel, with 16-byte loads of mu and d and 8-byte loads of r and w, so each
 // memory request carries two voxels (n even; the launcher checks the pointers'
-// alignment and otherwise uses the one-voxel kernel).
+// alignment and otherwise uses the one-voxel kernel).  The look-sum loop keeps the loads
+// of the next two looks in flight (the grid is small, to keep the Mann loop's re-reads in
+// L2, so each thread needs more bytes in flight).
 __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
   const long long n2 = g.n / 2;
   const int L = g.L;
@@ -800,18 +806,31 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
   for (long long vp = (long long)blockIdx.x * NT + threadIdx.x; vp < n2; vp += (long long)gridDim.x * NT) {
     CSum wb0, xb0, wb1, xb1;
     bool bad = false;
+    // two looks ahead in flight: slot a holds look l + 1, slot b look l + 2
     float2 w_n = Wi[vp], r_n = Ri[vp];
     float4 m_n = MUi[vp], d_n = Di[vp];
+    float2 w_a = w_n, r_a = r_n;
+    float4 m_a = m_n, d_a = d_n;
+    if (L > 1) {
+      w_a = Wi[n2 + vp];
+      r_a = Ri[n2 + vp];
+      m_a = MUi[n2 + vp];
+      d_a = Di[n2 + vp];
+    }
     for (int l = 0; l < L; ++l) {
       const long long i = (long long)l * n2 + vp;
       const float2 wl = w_n, rp = r_n;
       float4 m = m_n;
       const float4 dd = d_n;
-      if (l + 1 < L) {
-        w_n = Wi[i + n2];
-        r_n = Ri[i + n2];
-        m_n = MUi[i + n2];
-        d_n = Di[i + n2];
+      w_n = w_a;
+      r_n = r_a;
+      m_n = m_a;
+      d_n = d_a;
+      if (l + 2 < L) {
+        w_a = Wi[i + 2 * n2];
+        r_a = Ri[i + 2 * n2];
+        m_a = MUi[i + 2 * n2];
+        d_a = Di[i + 2 * n2];
       }
       if (c.closed_mu) {  // no-aperture ablation: d holds F^H y
         const float f0 = 1.0f / (1.0f + c.nv / (rp.x + c.nv)), f1 = 1.0f / (1.0f + c.nv / (rp.y + c.nv));
@@ -821,10 +840,11 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
         m = make_float4(fmaf(gm, dd.x, m.x), fmaf(gm, dd.y, m.y), fmaf(gm, dd.z, m.z), fmaf(gm, dd.w, m.w));
       }
       MUo[i] = m;
-      const float c0 = c.nv * rp.x / fmaf(c.alpha, rp.x, c.nv), c1 = c.nv * rp.y / fmaf(c.alpha, rp.y, c.nv);
+      const float c0 = c.nv * rp.x * __frcp_rn(fmaf(c.alpha, rp.x, c.nv));
+      const float c1 = c.nv * rp.y * __frcp_rn(fmaf(c.alpha, rp.y, c.nv));
       const float K0 = c0 + fmaf(m.x, m.x, m.y * m.y), K1 = c1 + fmaf(m.z, m.z, m.w * m.w);
-      const float2 rn = make_float2(prox_quad(wl.x, rp.x, K0, c.prox_var, c.beta),
-                                    prox_quad(wl.y, rp.y, K1, c.prox_var, c.beta));
+      const float2 rn = make_float2(prox_quad(wl.x, rp.x, K0, c.prox_var, c.inv_prox_var, c.beta, c.inv_beta),
+                                    prox_quad(wl.y, rp.y, K1, c.prox_var, c.inv_prox_var, c.beta, c.inv_beta));
       Ro[i] = rn;
       bad |= !isfinite(rn.x) || !isfinite(rn.y) || !isfinite(K0) || !isfinite(K1);   // K covers mu
       wb0.add(c.ups_look * wl.x);
@@ -842,12 +862,15 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
     float num = 0.f;
     CSum wn0, wn1;
     float2 rj_n = Ri[vp], wj_n = Wi[vp];
+    float2 rj_a = Ri[n2 + vp], wj_a = Wi[n2 + vp];   // rows 0..L: L + 1 >= 2
     for (int j = 0; j <= L; ++j) {
       const long long i = (long long)j * n2 + vp;
       const float2 rj = rj_n, wj = wj_n;
-      if (j < L) {
-        rj_n = Ri[i + n2];
-        wj_n = Wi[i + n2];
+      rj_n = rj_a;
+      wj_n = wj_a;
+      if (j + 2 <= L) {
+        rj_a = Ri[i + 2 * n2];
+        wj_a = Wi[i + 2 * n2];
       }
       const float dv0 = rj.x - w0, dv1 = rj.y - w1;
       num = fmaf(dv0, dv0, fmaf(dv1, dv1, num));

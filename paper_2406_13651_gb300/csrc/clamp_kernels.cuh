@@ -138,6 +138,7 @@ struct PassC {
   float* wbar;       // [n] (MACE variants)
   const float* gamma;
   float nv, alpha, prox_var, beta;
+  float inv_prox_var, inv_beta;   // 1 / prox_var, 1 / beta (host, rounded once)
   float ups_look, ups_prior, rho;
   double* part_num;  // CE partials (MACE variants)
   double* part_den;
