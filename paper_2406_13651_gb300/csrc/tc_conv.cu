@@ -172,19 +172,23 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   uint32_t fail_parity = 0;
 
   // Chunk staging: cp.async 16-byte copies (zero-fill outside the volume), all in flight
-  // at once.  TF32x3 lands the raw FP32 halo in the lo copy and splits it in place.
+  // at once.  TF32x3 lands the raw FP32 halo in the lo copy and splits it in place.  Each
+  // warp takes whole halo rows (channel group, z, y: row-uniform bounds and base address)
+  // with its lanes along x, so a copy costs a few instructions to issue.
   uint4* s_raw = s_halo + (Kd::SPLIT - 1) * Cfg::HALO_VEC;
+  constexpr int HROWS = 2 * HZ * HY;
   for (int c = 0; c < Cfg::CHUNKS; ++c) {
-    for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
-      const int xr = e % TC_HX;
-      int t = e / TC_HX;
-      const int yr = t % HY;
-      t /= HY;
-      const int zr = t % HZ, cg = t / HZ;
-      const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z0 + zr - 1;
-      const bool inb = gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz;
-      const uint4* src = inb ? &in[(long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx + gx] : in;
-      cp_async16(&s_raw[e], src, inb);
+    for (int row = warp; row < HROWS; row += TC_NT / 32) {
+      const int yr = row % HY, zr = (row / HY) % HZ, cg = row / (HY * HZ);
+      const int gy = y0 + yr - 1, gz = z0 + zr - 1;
+      const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+      const long long rbase = (long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx;
+      uint4* drow = s_raw + row * TC_HX;
+      for (int xr = lane; xr < TC_HX; xr += 32) {
+        const int gx = x0 + xr - 1;
+        const bool inb = rin && gx >= 0 && gx < nx;
+        cp_async16(&drow[xr], inb ? &in[rbase + gx] : in, inb);
+      }
     }
     for (int s = 0; s < Kd::SPLIT; ++s) {
       const uint4* wsrc = wpk + ((long long)s * Cfg::CHUNKS + c) * Cfg::W_VEC;
@@ -245,8 +249,10 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
       }
       tc::mma_commit(mbar);
     }
-    // every thread waits for the chunk's MMAs: they read the buffers the next chunk overwrites
-    if (!tc::mbar_wait_bounded(mbar, (uint32_t)(c & 1), kWaitLimit)) atomicOr(abort_flag, 1);
+    // the chunk's MMAs read the buffers the next chunk overwrites: one thread waits for
+    // their commit, the others at the barrier (which takes no issue slots from the CTA
+    // staging beside this one)
+    if (tid == 0 && !tc::mbar_wait_bounded(mbar, (uint32_t)(c & 1), kWaitLimit)) *abort_flag = 1;
     __syncthreads();
     if (*abort_flag) {
       aborted = true;
