@@ -172,30 +172,97 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   uint32_t fail_parity = 0;
 
   // Chunk staging: cp.async 16-byte copies (zero-fill outside the volume), all in flight
-  // at once.  TF32x3 lands the raw FP32 halo in the lo copy and splits it in place.  Each
-  // warp takes whole halo rows (channel group, z, y: row-uniform bounds and base address)
-  // with its lanes along x, so a copy costs a few instructions to issue.
+  // at once, in one commit group per halo plane: group p holds halo plane p and the
+  // weights of dz = p, the first taps that reach it.  Each warp takes whole halo rows
+  // (channel group, y: row-uniform bounds and base address) with its lanes along x, so a
+  // copy costs a few instructions to issue.  BF16 waits for the groups one plane at a time
+  // and issues the MMAs that read a plane as soon as it has landed, while the later planes
+  // are still in flight; TF32x3 lands the raw FP32 halo in the lo copy, waits for all of it
+  // and splits it in place.
   uint4* s_raw = s_halo + (Kd::SPLIT - 1) * Cfg::HALO_VEC;
-  constexpr int HROWS = 2 * HZ * HY;
-  for (int c = 0; c < Cfg::CHUNKS; ++c) {
-    for (int row = warp; row < HROWS; row += TC_NT / 32) {
-      const int yr = row % HY, zr = (row / HY) % HZ, cg = row / (HY * HZ);
-      const int gy = y0 + yr - 1, gz = z0 + zr - 1;
-      const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
-      const long long rbase = (long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx;
-      uint4* drow = s_raw + row * TC_HX;
-      for (int xr = lane; xr < TC_HX; xr += 32) {
-        const int gx = x0 + xr - 1;
-        const bool inb = rin && gx >= 0 && gx < nx;
-        cp_async16(&drow[xr], inb ? &in[rbase + gx] : in, inb);
+  constexpr int WDZ = Cfg::W_VEC / 3;   // weights of one dz
+  const uint64_t a0 = tc::make_desc(halo_s, LBO_A, 128);
+  const uint64_t b0 = tc::make_desc(w_s, LBO_B, 128);
+  // MMAs of one chunk that read halo plane hz: tiles tz with tap dz = hz - tz.  Descriptors
+  // differ only in the start-address field (bits 0-13, 16-byte units), so each MMA adds a
+  // compile-time offset to a base descriptor.
+  auto issue_plane = [&](int hz) {
+#pragma unroll
+    for (int tz = 0; tz < Cfg::TZ; ++tz) {
+      const int dz = hz - tz;
+      if (dz < 0 || dz > 2) continue;
+#pragma unroll
+      for (int hy = 0; hy < HY; ++hy) {
+        // tiles ty_lo..ty_hi of z-row tz read halo row hy with taps dy = hy - ty
+        const int ty_lo = hy - 2 > 0 ? hy - 2 : 0, ty_hi = hy < TY - 1 ? hy : TY - 1;
+        const int ntile = ty_hi - ty_lo + 1;
+        const uint32_t idesc = Kd::idesc(128, ntile * NPAD);
+        const uint32_t dcol = tbase + (uint32_t)((tz * TY + ty_lo) * NPAD);
+        const int dyp = 2 - (hy - ty_lo);   // block index of the first tile's tap (dy = hy - ty_lo)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const uint64_t aoff = (uint64_t)((hz * HY + hy) * TC_HX + dx);
+          const uint64_t boff = (uint64_t)((dz * 3 + dx) * 6 * NPAD + dyp * NPAD);
+#pragma unroll
+          for (int sp = 0; sp < (KIND == TC_BF16 ? 1 : 3); ++sp) {
+            // TF32x3 terms: (a_lo, b_hi), (a_hi, b_lo), (a_hi, b_hi)
+            const uint64_t a_sp = (KIND == TC_BF16 || sp > 0) ? 0 : (uint64_t)(SPLIT_A >> 4);
+            const uint64_t b_sp = (KIND != TC_BF16 && sp == 1) ? (uint64_t)(SPLIT_B >> 4) : 0;
+            mma_kind(KIND, dcol, a0 + a_sp + aoff, b0 + b_sp + boff, idesc, 1u);
+          }
+        }
       }
     }
-    for (int s = 0; s < Kd::SPLIT; ++s) {
-      const uint4* wsrc = wpk + ((long long)s * Cfg::CHUNKS + c) * Cfg::W_VEC;
-      for (int e = tid; e < Cfg::W_VEC; e += TC_NT) cp_async16(&s_w[s * Cfg::W_VEC + e], &wsrc[e], true);
+  };
+  auto clear_acc = [&]() {   // D = A x 0 for every accumulator (first chunk)
+    const uint64_t bz = tc::make_desc(z_s, NPAD * 16, 128);
+#pragma unroll
+    for (int mt = 0; mt < MT; ++mt) mma_kind(KIND, tbase + (uint32_t)(mt * NPAD), a0, bz, Kd::idesc(128, NPAD), 0u);
+  };
+  static_assert(HZ == 4, "one commit group per halo plane: the waits below name groups 3..0");
+  for (int c = 0; c < Cfg::CHUNKS; ++c) {
+#pragma unroll
+    for (int hz = 0; hz < HZ; ++hz) {
+      if (hz < 3) {
+        for (int sp = 0; sp < Kd::SPLIT; ++sp) {
+          const uint4* wsrc = wpk + ((long long)sp * Cfg::CHUNKS + c) * Cfg::W_VEC + hz * WDZ;
+          uint4* wdst = s_w + sp * Cfg::W_VEC + hz * WDZ;
+          for (int e = tid; e < WDZ; e += TC_NT) cp_async16(&wdst[e], &wsrc[e], true);
+        }
+      }
+      const int gz = z0 + hz - 1;
+      for (int r = warp; r < 2 * HY; r += TC_NT / 32) {
+        const int cg = r / HY, yr = r % HY;
+        const int gy = y0 + yr - 1;
+        const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+        const long long rbase = (long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx;
+        uint4* drow = s_raw + ((cg * HZ + hz) * HY + yr) * TC_HX;
+        for (int xr = lane; xr < TC_HX; xr += 32) {
+          const int gx = x0 + xr - 1;
+          const bool inb = rin && gx >= 0 && gx < nx;
+          cp_async16(&drow[xr], inb ? &in[rbase + gx] : in, inb);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    cp_async_wait_all();
-    if constexpr (KIND == TC_TF32X3) {
+    if constexpr (KIND == TC_BF16) {
+#pragma unroll
+      for (int hz = 0; hz < HZ; ++hz) {
+        if (hz == 0) asm volatile("cp.async.wait_group 3;" ::: "memory");
+        else if (hz == 1) asm volatile("cp.async.wait_group 2;" ::: "memory");
+        else if (hz == 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else asm volatile("cp.async.wait_group 0;" ::: "memory");
+        tc::fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+          tc::fence_after_sync();
+          if (c == 0 && hz == 0) clear_acc();
+          issue_plane(hz);
+          if (hz == HZ - 1) tc::mma_commit(mbar);
+        }
+      }
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncthreads();
       float4* hi = reinterpret_cast<float4*>(s_halo);
       float4* lo = reinterpret_cast<float4*>(s_raw);
@@ -205,49 +272,15 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
         hi[e] = h;
         lo[e] = make_float4(tf32_rn(f.x - h.x), tf32_rn(f.y - h.y), tf32_rn(f.z - h.z), tf32_rn(f.w - h.w));
       }
-    }
-    tc::fence_proxy_async();
-    __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-      // Descriptors differ only in the start-address field (bits 0-13, 16-byte units), so
-      // each MMA adds a compile-time offset to a base descriptor.
-      const uint64_t a0 = tc::make_desc(halo_s, LBO_A, 128);
-      const uint64_t b0 = tc::make_desc(w_s, LBO_B, 128);
-      if (c == 0) {  // clear every accumulator: D = A x 0
-        const uint64_t bz = tc::make_desc(z_s, NPAD * 16, 128);
+      tc::fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+        if (c == 0) clear_acc();
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt)
-          mma_kind(KIND, tbase + (uint32_t)(mt * NPAD), a0, bz, Kd::idesc(128, NPAD), 0u);
+        for (int hz = 0; hz < HZ; ++hz) issue_plane(hz);
+        tc::mma_commit(mbar);
       }
-#pragma unroll
-      for (int dz = 0; dz < 3; ++dz) {
-#pragma unroll
-        for (int tz = 0; tz < Cfg::TZ; ++tz) {
-#pragma unroll
-          for (int hy = 0; hy < HY; ++hy) {
-            // tiles ty_lo..ty_hi of z-row tz read halo row hy with taps dy = hy - ty
-            const int ty_lo = hy - 2 > 0 ? hy - 2 : 0, ty_hi = hy < TY - 1 ? hy : TY - 1;
-            const int ntile = ty_hi - ty_lo + 1;
-            const uint32_t idesc = Kd::idesc(128, ntile * NPAD);
-            const uint32_t dcol = tbase + (uint32_t)((tz * TY + ty_lo) * NPAD);
-            const int dyp = 2 - (hy - ty_lo);   // block index of the first tile's tap (dy = hy - ty_lo)
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) {
-              const uint64_t aoff = (uint64_t)(((tz + dz) * HY + hy) * TC_HX + dx);
-              const uint64_t boff = (uint64_t)((dz * 3 + dx) * 6 * NPAD + dyp * NPAD);
-#pragma unroll
-              for (int sp = 0; sp < (KIND == TC_BF16 ? 1 : 3); ++sp) {
-                // TF32x3 terms: (a_lo, b_hi), (a_hi, b_lo), (a_hi, b_hi)
-                const uint64_t a_sp = (KIND == TC_BF16 || sp > 0) ? 0 : (uint64_t)(SPLIT_A >> 4);
-                const uint64_t b_sp = (KIND != TC_BF16 && sp == 1) ? (uint64_t)(SPLIT_B >> 4) : 0;
-                mma_kind(KIND, dcol, a0 + a_sp + aoff, b0 + b_sp + boff, idesc, 1u);
-              }
-            }
-          }
-        }
-      }
-      tc::mma_commit(mbar);
     }
     // the chunk's MMAs read the buffers the next chunk overwrites: one thread waits for
     // their commit, the others at the barrier (which takes no issue slots from the CTA
