@@ -875,39 +875,42 @@ __global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict
     tc::tmem_relinquish();
   }
   for (int e = tid; e < C * 4; e += TC_NT) cp_async16(&s_w[e], &wpk[e], true);
-  for (int e = tid; e < CF1_HZ * CF1_HY * TC_HX; e += TC_NT) {   // input halo, BF16, zeros outside
-    const int xr = e % TC_HX, t = e / TC_HX;
-    const int yr = t % CF1_HY, zr = t / CF1_HY;
-    const int gx = x0 + xr - 1, gy = y0 + yr - 1, gz = z0 + zr - 1;
-    float v = 0.f;
-    if (gx >= 0 && gx < nx && gy >= 0 && gy < ny && gz >= 0 && gz < nz)
-      v = __ldg(&in[(long long)gz * plane + (long long)gy * nx + gx]);
-    s_x[e] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+  // input halo, BF16, zeros outside: a warp per halo row, lanes along x
+  for (int r = warp; r < CF1_HZ * CF1_HY; r += TC_NT / 32) {
+    const int yr = r % CF1_HY, zr = r / CF1_HY;
+    const int gy = y0 + yr - 1, gz = z0 + zr - 1;
+    const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+    const float* src = in + (long long)gz * plane + (long long)gy * nx;
+    for (int xr = lane; xr < TC_HX; xr += 32) {
+      const int gx = x0 + xr - 1;
+      const float v = rin && gx >= 0 && gx < nx ? __ldg(&src[gx]) : 0.f;
+      s_x[r * TC_HX + xr] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    }
   }
   cp_async_wait_all();
   __syncthreads();
-  // im2col: one 16-byte chunk (8 consecutive k of one row) per step
-  for (int e = tid; e < CF1_MT * 128 * 4; e += TC_NT) {
-    const int row = e % 128, g = (e / 128) % 4, mt = e / 512;
+  // im2col: a thread builds whole rows (128-voxel tile row, all four 8-tap groups), so
+  // every tap offset is a compile-time constant
+  for (int e = tid; e < CF1_MT * 128; e += TC_NT) {
+    const int row = e % 128, mt = e / 128;
     const int ty = mt % CF1_TY, tz = mt / CF1_TY;
-    uint32_t w4[4];
+    const uint16_t* xs = s_x + (tz * CF1_HY + ty) * TC_HX + row;
+    unsigned char* arow = s_a + mt * CF1_A_BYTES + (row / 8) * 512 + (row % 8) * 16;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      uint32_t pair = 0;
+    for (int g = 0; g < 4; ++g) {
+      uint32_t w4[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int k = 8 * g + 2 * j + h;
-        uint32_t v = 0;
-        if (k < 27) {
-          const int dz = k / 9, dy = (k / 3) % 3, dx = k % 3;
-          v = s_x[((tz + dz) * CF1_HY + ty + dy) * TC_HX + row + dx];
+      for (int j = 0; j < 4; ++j) {
+        uint32_t pair = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = 8 * g + 2 * j + h;
+          if (k < 27) pair |= (uint32_t)xs[((k / 9) * CF1_HY + (k / 3) % 3) * TC_HX + k % 3] << (16 * h);
         }
-        pair |= v << (16 * h);
+        w4[j] = pair;
       }
-      w4[j] = pair;
+      *reinterpret_cast<uint4*>(arow + g * 128) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
     }
-    *reinterpret_cast<uint4*>(s_a + mt * CF1_A_BYTES + (row / 8) * 512 + g * 128 + (row % 8) * 16) =
-        make_uint4(w4[0], w4[1], w4[2], w4[3]);
   }
   tc::fence_proxy_async();
   tc::fence_before_sync();

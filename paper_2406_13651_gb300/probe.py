@@ -3,11 +3,15 @@
   python -m paper_2406_13651_gb300.probe agent --shape 256,256,128 --looks 4 --iters 3 \\
       [--schedule auto|band|full] [--prior gauss|cnn-bf16|cnn-fp32]
   python -m paper_2406_13651_gb300.probe prior --shape 256,256,64 --dtype bf16 --reps 3
+  python -m paper_2406_13651_gb300.probe e2e --shape 256,256,128 --looks 32 --iters 20 --prior cnn-bf16
 
 ``agent`` runs ``--iters`` CLAMP iterations (after one untimed iteration) on seeded random
 data with a circular pupil of radius 0.35 Nyquist and a Hann range window; ``prior`` runs
-the residual CNN prior agent (8 x 48 BF16 or 5 x 32 FP32) on a seeded random volume.  Each
-prints one JSON line with the mean milliseconds per repetition (CUDA events).
+the residual CNN prior agent (8 x 48 BF16 or 5 x 32 FP32) on a seeded random volume;
+``e2e`` splits one clamp_reconstruct_host call on pinned host buffers into its parts: a
+plain upload of y, a call with no iterations (upload, initialisation, download) and a call
+with ``--iters`` iterations (wall clock).  Each prints one JSON line with the mean
+milliseconds per repetition.
 """
 from __future__ import annotations
 
@@ -24,7 +28,7 @@ def main(argv=None) -> int:
     from . import inputs as I
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["agent", "prior"])
+    ap.add_argument("what", choices=["agent", "prior", "e2e"])
     ap.add_argument("--shape", default="256,256,128", help="nx,ny,nz")
     ap.add_argument("--looks", type=int, default=4)
     ap.add_argument("--iters", type=int, default=3)
@@ -61,6 +65,45 @@ def main(argv=None) -> int:
                           "tflops": 2 * macs * nx * ny * nz / ms / 1e9}), flush=True)
         return 0
     L = a.looks
+    if a.what == "e2e":
+        import ctypes
+        import time
+        lib = C.load()
+        pupil_pin = torch.from_numpy(I.circular_pupil(nx, ny, 0.35)).pin_memory()
+        window_pin = torch.from_numpy(I.hann_window(nz)).pin_memory()
+        y_pin = torch.empty((L, nz, ny, nx), dtype=torch.complex64, pin_memory=True)
+        y_pin.copy_(torch.complex(torch.randn(y_pin.shape), torch.randn(y_pin.shape)) *
+                    (pupil_pin[None, None] * window_pin[None, :, None, None]))
+        rout_pin = torch.empty((nz, ny, nx), dtype=torch.float32, pin_memory=True)
+        if a.prior == "gauss":
+            den = C.Denoiser.gauss(0.8)
+        else:
+            dt = a.prior.split("-")[1]
+            layers, ch = (8, 48) if dt == "bf16" else (5, 32)
+            w_, b_ = I.cnn_weights(layers, ch, seed=1)
+            den = C.Denoiser.cnn(w_, b_, dt)
+        st = torch.cuda.current_stream()
+        out = {"probe": "e2e", "shape": [nx, ny, nz], "looks": L, "prior": a.prior, "iters": a.iters}
+        yd = torch.empty(y_pin.shape, dtype=y_pin.dtype, device=dev)
+        for name, iters in (("upload_only", None), ("zero_iterations", 0), ("with_iterations", a.iters)):
+            def call():
+                if iters is None:
+                    yd.copy_(y_pin, non_blocking=True)
+                    return
+                p = C.make_params(nx, ny, nz, L, 1e-3, 1e-4, max_iters=iters)
+                rep = C.Report(0, 0, 0.0, 0.0, None, None)
+                C._check(lib.clamp_reconstruct_host(ctypes.byref(p), y_pin.data_ptr(), pupil_pin.data_ptr(),
+                                                    window_pin.data_ptr(), den.handle, None, rout_pin.data_ptr(),
+                                                    ctypes.byref(rep), st.cuda_stream), "clamp_reconstruct_host")
+            call()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(a.reps):
+                call()
+            torch.cuda.synchronize()
+            out[name + "_ms"] = (time.perf_counter() - t0) / a.reps * 1e3
+        print(json.dumps(out), flush=True)
+        return 0
     pupil = torch.from_numpy(I.circular_pupil(nx, ny, 0.35)).to(dev)
     window = torch.from_numpy(I.hann_window(nz)).to(dev)
     flags = {"auto": 0, "band": C.FLAG_BAND_SPECTRUM, "full": C.FLAG_FULL_SPECTRUM}[a.schedule]
