@@ -37,7 +37,13 @@ FP32_LANES_PER_SM = 128
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch set, measured by ncu
 # on the current kernels, keyed by (workload, part); parts without a capture report null.
-TRAFFIC = {}
+#  * cfg3 prior: one BF16 prior call (first layer, six hidden layers, tap sums, gather)
+#    captured at 256x256x64 (6.24 GB) and doubled: every kernel streams its volume once, so
+#    the traffic grows with the voxel count.
+#  * cfg3 agent: one band-limited iteration's passes, line search and prox/Mann pass
+#    captured at 256x256x128 with L = 4 looks (2.54 GB) and scaled to L = 32: all but the
+#    prox/Mann pass's 16 B per voxel (the prior agent's r, w and wbar) grows with the looks.
+TRAFFIC = {("cfg3", "prior"): 12.479e9, ("cfg3", "agent", "band-limited"): 19.344e9}
 
 def agent_bytes_per_iteration(sched: dict, nx: int, ny: int, nz: int, L: int) -> float:
     """Algorithmic DRAM bytes of one iteration's forward agents and fused prox/Mann pass:
@@ -615,9 +621,11 @@ def main():
         bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
         tensor_path = wl.nx % 128 == 0 and ch in (16, 32, 48) and wl.ny % 2 == 0 and wl.nz % 2 == 0
         if wl.denoiser.get("dtype", "fp32") == "bf16":
-            roofline = {"bound": "tensor", "kernel": "k_conv3_tc<BF16> (+ SIMT first layer): the prior agent",
+            roofline = {"bound": "tensor",
+                        "kernel": "the prior agent: k_conv3_tc<BF16> hidden layers, k_conv_first_tc, "
+                                  "k_last_taps_tc + k_last_gather",
                         "achieved": cnn_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
-                        "frac": cnn_tflops / bf16_peak, "traffic": None,
+                        "frac": cnn_tflops / bf16_peak, "traffic": TRAFFIC.get((wl.name, "prior")),
                         "peak_source": "measured bf16_tflops_sustained",
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
         elif tensor_path:
@@ -657,7 +665,13 @@ def main():
         t_it, desc = oracle_sample(wl, 2, max(4, wl.nz // 16), seed=seed)
         cpu = {"value": n * L / t_it, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": desc}
 
-    launches_per_iter = 5 + 1 + (len(wl.denoiser.get("weights", [])) if wl.denoiser["kind"] == "cnn" else 1) + 1 + 1
+    # kernels per iteration: the five agent passes and the line search, the prior (one per CNN
+    # layer; the BF16 last layer is a tap-sum GEMM plus a gather), the prox/Mann pass and the
+    # CE reduction (17 at 256x256x128 with the 8-layer BF16 CNN)
+    prior_k = 1
+    if wl.denoiser["kind"] == "cnn":
+        prior_k = len(wl.denoiser["weights"]) + (1 if wl.denoiser.get("dtype", "fp32") == "bf16" else 0)
+    launches_per_iter = 5 + 1 + prior_k + 1 + 1
     warm = None
     if world == 1 and not args.no_warm_start:
         del mu, r, w, ws, y

@@ -382,7 +382,8 @@ clamp_status clamp_point_cloud_metrics(const float* r_hat, const float* r_true, 
  *   conv 2c2->c2, c2->c2, tconv c2->c1, conv 2c1->c1, c1->c1, 1x1 c1->1.
  * Tensors are float32 [batch][channels][nz][ny][nx] on the device; nx, ny, nz must be
  * multiples of 4.  dtype CLAMP_DENOISER_BF16: every conv rounds its weights and inputs
- * (forward) or its two operands (gradients) to bfloat16 and accumulates in FP32;
+ * (forward) or its two operands (gradients) to bfloat16 and accumulates in FP32 (the 3x3x3
+ * convs on the tensor cores where clamp_unet_set_tensor_cores allows);
  * CLAMP_DENOISER_FP32: all FP32.  Master weights, gradients and Adam moments are FP32. */
 typedef struct clamp_unet clamp_unet;
 
@@ -428,6 +429,17 @@ clamp_status clamp_unet_warm_start(clamp_unet* u, int32_t nx, int32_t ny, int32_
  * after clamp_denoiser_destroy.  Volumes need nx, ny, nz multiples of 4 (else
  * CLAMP_EUNSUPPORTED at use); workspace: clamp_unet_workspace_size(net, 1, nx, ny, nz, 0). */
 clamp_status clamp_denoiser_create_unet(clamp_unet* net, float floor_rel, clamp_denoiser** out);
+/* BF16 networks: on = 1 (the default) runs every 3x3x3 conv with 16k input channels and 16,
+ * 32 or 64 output channels, forward and data gradient, on the tensor cores (tcgen05, BF16
+ * operands, FP32 accumulation) wherever the level's shape allows it (nx = 16 with ny a
+ * multiple of 8, or nx a multiple of 32 with ny a multiple of 4); on = 0 keeps them on the CUDA
+ * cores.  Both round the same operands to bfloat16; only the order of the FP32 sums
+ * differs.  The first conv (one input channel), the transposed convs, the 1x1 conv and the
+ * weight gradients stay on the CUDA cores.  FP32 networks ignore the setting. */
+clamp_status clamp_unet_set_tensor_cores(clamp_unet* u, int32_t on);
+/* Synchronous check of the network's tensor-core waits since the last check: CLAMP_ETIMEOUT
+ * (and the flag cleared) if a bounded wait gave up, else CLAMP_OK. */
+clamp_status clamp_unet_check(clamp_unet* u);
 /* One Adam step (Kingma and Ba, 2015, with bias correction; t >= 1 is the step number)
  * on the parameters from the current gradients. */
 clamp_status clamp_unet_adam(clamp_unet* u, float lr, float beta1, float beta2, float eps, int32_t t,

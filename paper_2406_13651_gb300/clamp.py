@@ -45,7 +45,7 @@ EXPORTS = [
     "clamp_unet_workspace_size", "clamp_unet_forward", "clamp_unet_backward", "clamp_unet_adam",
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
     "clamp_point_cloud_workspace_size", "clamp_point_cloud_metrics", "clamp_denoiser_create_unet",
-    "clamp_selftest_bounded_wait", "clamp_prior_concurrent",
+    "clamp_selftest_bounded_wait", "clamp_prior_concurrent", "clamp_unet_set_tensor_cores", "clamp_unet_check",
 ]
 
 
@@ -139,6 +139,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_unet_adam": (I, [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, I, P]),
         "clamp_speckle_average": (I, [PP, P, P, P, P, P, S, P]),
         "clamp_unet_normalize": (I, [I, ctypes.c_int64, ctypes.c_int64, P, P, P, P, P]),
+        "clamp_unet_set_tensor_cores": (I, [P, I]),
+        "clamp_unet_check": (I, [P]),
         "clamp_unet_warm_start": (I, [P, I, I, I, P, ctypes.c_float, P, P, S, P]),
         "clamp_unet_loss": (I, [P, P, P, I, I, I, I, P, P, S, P]),
         "clamp_point_cloud_workspace_size": (S, []),
@@ -577,6 +579,14 @@ class UNet:
         self.step += 1
         _check(load().clamp_unet_adam(self.handle, lr, beta1, beta2, eps, self.step, _stream(stream)),
                "clamp_unet_adam")
+
+    def set_tensor_cores(self, on: bool) -> None:
+        """BF16 networks: 3x3x3 convs on the tensor cores (default) or on the CUDA cores."""
+        _check(load().clamp_unet_set_tensor_cores(self.handle, int(bool(on))), "clamp_unet_set_tensor_cores")
+
+    def check(self) -> None:
+        """Raises if a bounded tensor-core wait gave up since the last check (synchronous)."""
+        _check(load().clamp_unet_check(self.handle), "clamp_unet_check")
 
     def close(self):
         if getattr(self, "handle", None):

@@ -35,3 +35,15 @@ clamp_status autotune_agent(const clamp_params* p, const ReconPlan& plan, const 
                             const float* window, void* ws, cudaStream_t st, clamp::AgentVariants* out);
 // Byte offset of the forward-agent scratch inside a clamp_reconstruct workspace.
 size_t recon_agent_offset(const clamp_params* p, const clamp_denoiser* den);
+
+// The U-Net's 3x3x3 conv on the tensor cores (BF16 operands, FP32 accumulation), FP32
+// channel-planar tensors in and out; W is FP32 [co][ci][27] (packed to BF16 into wpk,
+// unet_conv3_tc_wpk_bytes(ci, co) bytes, on the stream).  err: device word, bit 2 set when a
+// bounded wait gave up.
+namespace clamp {
+bool unet_conv3_tc_supported(int ci, int co, int nx, int ny);
+size_t unet_conv3_tc_wpk_bytes(int ci, int co);
+cudaError_t unet_conv3_tc(const float* in, long long in_bs, int ci, float* out, long long out_bs, int co,
+                          const float* W, const float* bias, bool relu, int B, int nx, int ny, int nz, uint4* wpk,
+                          int* err, cudaStream_t st);
+}  // namespace clamp

@@ -148,8 +148,18 @@ static void conv3_launch(const float* in, long long in_bs, int ci, float* out, l
       k_conv3<CO, CG, 4, BF><<<grid, UT, 0, st>>>(in, in_bs, ci, out, out_bs, co, W, bias, relu, nx, ny, nz);
   }
 }
+// Tensor-core path of a network (BF16 only): packed-weight scratch, error word, switch.
+struct TcCtx {
+  uint4* wpk;
+  int* err;
+  bool on;
+};
+
 static cudaError_t conv3(bool bf, const float* in, long long in_bs, int ci, float* out, long long out_bs, int co,
-                         const float* W, const float* bias, bool relu, int B, int nx, int ny, int nz, cudaStream_t st) {
+                         const float* W, const float* bias, bool relu, int B, int nx, int ny, int nz, cudaStream_t st,
+                         const TcCtx& tc) {
+  if (bf && tc.on && unet_conv3_tc_supported(ci, co, nx, ny))
+    return unet_conv3_tc(in, in_bs, ci, out, out_bs, co, W, bias, relu, B, nx, ny, nz, tc.wpk, tc.err, st);
   // grid.z = samples * nz * channel blocks must stay <= 65535: launch sample chunks
   const int per = std::max(1, 65535 / (nz * ((co + 15) / 16)));
   for (int b0 = 0; b0 < B; b0 += per) {
@@ -526,6 +536,10 @@ struct clamp_unet {
   size_t count = 0;
   float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr, *flip = nullptr;
   size_t flip_count = 0;
+  uint4* wpk = nullptr;   // BF16 packed weights of the conv on the tensor cores
+  int* err = nullptr;     // device word: bit 2 = a tensor-core wait gave up
+  int tc = 1;             // BF16 convs on the tensor cores where supported
+  TcCtx ctx() const { return TcCtx{wpk, err, bf != 0 && tc != 0}; }
 };
 
 // Workspace: activations and their gradients for batch B at (nx, ny, nz).
@@ -598,15 +612,22 @@ extern "C" clamp_status clamp_unet_create(int32_t c1, int32_t c2, int32_t c3, in
   }
   u->count = off;
   const size_t bytes = off * sizeof(float);
+  size_t wpk_bytes = 16;
+  for (const Layer& L : u->layers)
+    if (L.kind == CONV3 && L.ci >= 16)   // forward (ci -> co) and data gradient (co -> ci)
+      wpk_bytes = std::max({wpk_bytes, clamp::unet_conv3_tc_wpk_bytes(L.ci, L.co),
+                            clamp::unet_conv3_tc_wpk_bytes(L.co, L.ci)});
   if (cudaMalloc(&u->p, bytes) != cudaSuccess || cudaMalloc(&u->g, bytes) != cudaSuccess ||
       cudaMalloc(&u->m, bytes) != cudaSuccess || cudaMalloc(&u->v, bytes) != cudaSuccess ||
-      cudaMalloc(&u->flip, u->flip_count * sizeof(float)) != cudaSuccess) {
+      cudaMalloc(&u->flip, u->flip_count * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&u->wpk, wpk_bytes) != cudaSuccess || cudaMalloc(&u->err, sizeof(int)) != cudaSuccess) {
     clamp_unet_destroy(u);
     return api_fail(CLAMP_ENOMEM, "clamp_unet_create: device allocation failed");
   }
   cudaError_t e = cudaSuccess;
   for (float* q : {u->g, u->m, u->v})
     if (e == cudaSuccess) e = cudaMemset(q, 0, bytes);
+  if (e == cudaSuccess) e = cudaMemset(u->err, 0, sizeof(int));
   if (e == cudaSuccess)
     e = params_host ? cudaMemcpy(u->p, params_host, bytes, cudaMemcpyHostToDevice) : cudaMemset(u->p, 0, bytes);
   if (e != cudaSuccess) {
@@ -621,6 +642,8 @@ extern "C" void clamp_unet_destroy(clamp_unet* u) {
   if (!u) return;
   for (float* q : {u->p, u->g, u->m, u->v, u->flip})
     if (q) cudaFree(q);
+  if (u->wpk) cudaFree(u->wpk);
+  if (u->err) cudaFree(u->err);
   delete u;
 }
 
@@ -678,24 +701,24 @@ static clamp_status unet_forward(clamp_unet* u, const float* x, int B, int nx, i
   const int hx = nx / 2, hy = ny / 2, hz = nz / 2, qx = nx / 4, qy = ny / 4, qz = nz / 4;
   auto W = [&](int i) { return u->p + u->layers[i].w; };
   auto Bi = [&](int i) { return u->p + u->layers[i].b; };
-  U_TRY(conv3(bf, x, n1, 1, a.e1a, c1 * n1, c1, W(0), Bi(0), true, B, nx, ny, nz, st));
-  U_TRY(conv3(bf, a.e1a, c1 * n1, c1, a.cat1 + c1 * n1, 2 * c1 * n1, c1, W(1), Bi(1), true, B, nx, ny, nz, st));  // s1
+  U_TRY(conv3(bf, x, n1, 1, a.e1a, c1 * n1, c1, W(0), Bi(0), true, B, nx, ny, nz, st, u->ctx()));
+  U_TRY(conv3(bf, a.e1a, c1 * n1, c1, a.cat1 + c1 * n1, 2 * c1 * n1, c1, W(1), Bi(1), true, B, nx, ny, nz, st, u->ctx()));  // s1
   k_pool_fwd<<<grid_for(B * c1 * n2), UT, 0, st>>>(a.cat1 + c1 * n1, 2 * c1 * n1, a.p1, a.arg1, c1, B, nx, ny, nz);
   U_TRY(cudaGetLastError());
-  U_TRY(conv3(bf, a.p1, c1 * n2, c1, a.e2a, c2 * n2, c2, W(2), Bi(2), true, B, hx, hy, hz, st));
-  U_TRY(conv3(bf, a.e2a, c2 * n2, c2, a.cat2 + c2 * n2, 2 * c2 * n2, c2, W(3), Bi(3), true, B, hx, hy, hz, st));  // s2
+  U_TRY(conv3(bf, a.p1, c1 * n2, c1, a.e2a, c2 * n2, c2, W(2), Bi(2), true, B, hx, hy, hz, st, u->ctx()));
+  U_TRY(conv3(bf, a.e2a, c2 * n2, c2, a.cat2 + c2 * n2, 2 * c2 * n2, c2, W(3), Bi(3), true, B, hx, hy, hz, st, u->ctx()));  // s2
   k_pool_fwd<<<grid_for(B * c2 * n3), UT, 0, st>>>(a.cat2 + c2 * n2, 2 * c2 * n2, a.p2, a.arg2, c2, B, hx, hy, hz);
   U_TRY(cudaGetLastError());
-  U_TRY(conv3(bf, a.p2, c2 * n3, c2, a.bta, c3 * n3, c3, W(4), Bi(4), true, B, qx, qy, qz, st));
-  U_TRY(conv3(bf, a.bta, c3 * n3, c3, a.btb, c3 * n3, c3, W(5), Bi(5), true, B, qx, qy, qz, st));
+  U_TRY(conv3(bf, a.p2, c2 * n3, c2, a.bta, c3 * n3, c3, W(4), Bi(4), true, B, qx, qy, qz, st, u->ctx()));
+  U_TRY(conv3(bf, a.bta, c3 * n3, c3, a.btb, c3 * n3, c3, W(5), Bi(5), true, B, qx, qy, qz, st, u->ctx()));
   k_tconv_fwd<<<grid_for(B * c2 * n2), UT, 0, st>>>(a.btb, c3, a.cat2, 2 * c2 * n2, c2, W(6), Bi(6), B, hx, hy, hz, bf);
   U_TRY(cudaGetLastError());
-  U_TRY(conv3(bf, a.cat2, 2 * c2 * n2, 2 * c2, a.d2a, c2 * n2, c2, W(7), Bi(7), true, B, hx, hy, hz, st));
-  U_TRY(conv3(bf, a.d2a, c2 * n2, c2, a.d2b, c2 * n2, c2, W(8), Bi(8), true, B, hx, hy, hz, st));
+  U_TRY(conv3(bf, a.cat2, 2 * c2 * n2, 2 * c2, a.d2a, c2 * n2, c2, W(7), Bi(7), true, B, hx, hy, hz, st, u->ctx()));
+  U_TRY(conv3(bf, a.d2a, c2 * n2, c2, a.d2b, c2 * n2, c2, W(8), Bi(8), true, B, hx, hy, hz, st, u->ctx()));
   k_tconv_fwd<<<grid_for(B * c1 * n1), UT, 0, st>>>(a.d2b, c2, a.cat1, 2 * c1 * n1, c1, W(9), Bi(9), B, nx, ny, nz, bf);
   U_TRY(cudaGetLastError());
-  U_TRY(conv3(bf, a.cat1, 2 * c1 * n1, 2 * c1, a.d1a, c1 * n1, c1, W(10), Bi(10), true, B, nx, ny, nz, st));
-  U_TRY(conv3(bf, a.d1a, c1 * n1, c1, a.d1b, c1 * n1, c1, W(11), Bi(11), true, B, nx, ny, nz, st));
+  U_TRY(conv3(bf, a.cat1, 2 * c1 * n1, 2 * c1, a.d1a, c1 * n1, c1, W(10), Bi(10), true, B, nx, ny, nz, st, u->ctx()));
+  U_TRY(conv3(bf, a.d1a, c1 * n1, c1, a.d1b, c1 * n1, c1, W(11), Bi(11), true, B, nx, ny, nz, st, u->ctx()));
   k_conv1_fwd<<<grid_for(B * n1), UT, 0, st>>>(a.d1b, c1, W(12), Bi(12), a.out, B, n1, bf);
   U_TRY(cudaGetLastError());
   return CLAMP_OK;
@@ -727,7 +750,7 @@ static clamp_status conv3_bwd(clamp_unet* u, int li, const float* in, long long 
   if (din) {
     k_flip<<<grid_for((long long)L.nw), UT, 0, st>>>(u->p + L.w, u->flip, L.ci, L.co);
     U_TRY(cudaGetLastError());
-    U_TRY(conv3(bf, g, g_bs, L.co, din, din_bs, L.ci, u->flip, nullptr, false, B, nx, ny, nz, st));
+    U_TRY(conv3(bf, g, g_bs, L.co, din, din_bs, L.ci, u->flip, nullptr, false, B, nx, ny, nz, st, u->ctx()));
   }
   const size_t smem = sizeof(float) * (3 * (WG_ROWS + 2) * (nx + 2) + WG_CO * WG_ROWS * nx);
   U_TRY(cudaFuncSetAttribute(k_wgrad3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -836,6 +859,22 @@ extern "C" clamp_status clamp_unet_adam(clamp_unet* u, float lr, float beta1, fl
                                                                           lr_t, beta1, beta2, eps_t);
   U_TRY(cudaGetLastError());
   return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_unet_set_tensor_cores(clamp_unet* u, int32_t on) {
+  if (!u || (on != 0 && on != 1)) return api_fail(CLAMP_EINVAL, "clamp_unet_set_tensor_cores: bad arguments");
+  u->tc = on;
+  return CLAMP_OK;
+}
+
+extern "C" clamp_status clamp_unet_check(clamp_unet* u) {
+  if (!u) return api_fail(CLAMP_EINVAL, "clamp_unet_check: NULL network");
+  if (!on_unet_device(u, "clamp_unet_check")) return CLAMP_EINVAL;
+  int h = 0;
+  U_TRY(cudaMemcpy(&h, u->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (!h) return CLAMP_OK;
+  U_TRY(cudaMemset(u->err, 0, sizeof(int)));
+  return api_fail(CLAMP_ETIMEOUT, "clamp_unet_check: a bounded tensor-core wait gave up");
 }
 
 extern "C" clamp_status clamp_unet_normalize(int32_t batch, int64_t n, int64_t norm_count, const float* x,

@@ -4,14 +4,17 @@
       [--schedule auto|band|full] [--prior gauss|cnn-bf16|cnn-fp32]
   python -m paper_2406_13651_gb300.probe prior --shape 256,256,64 --dtype bf16 --reps 3
   python -m paper_2406_13651_gb300.probe e2e --shape 256,256,128 --looks 32 --iters 20 --prior cnn-bf16
+  python -m paper_2406_13651_gb300.probe unet --shape 64,64,32 --batch 24 --reps 3 [--cuda-cores]
 
 ``agent`` runs ``--iters`` CLAMP iterations (after one untimed iteration) on seeded random
 data with a circular pupil of radius 0.35 Nyquist and a Hann range window; ``prior`` runs
 the residual CNN prior agent (8 x 48 BF16 or 5 x 32 FP32) on a seeded random volume;
 ``e2e`` splits one clamp_reconstruct_host call on pinned host buffers into its parts: a
 plain upload of y, a call with no iterations (upload, initialisation, download) and a call
-with ``--iters`` iterations (wall clock).  Each prints one JSON line with the mean
-milliseconds per repetition.
+with ``--iters`` iterations (wall clock); ``unet`` times the BF16 16/32/64 U-Net's forward
+pass and training step (forward, backward, Adam) on a seeded batch, with its 3x3x3 convs
+on the tensor cores or (``--cuda-cores``) on the CUDA cores.  Each prints one JSON line
+with the mean milliseconds per repetition.
 """
 from __future__ import annotations
 
@@ -28,7 +31,7 @@ def main(argv=None) -> int:
     from . import inputs as I
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["agent", "prior", "e2e"])
+    ap.add_argument("what", choices=["agent", "prior", "e2e", "unet"])
     ap.add_argument("--shape", default="256,256,128", help="nx,ny,nz")
     ap.add_argument("--looks", type=int, default=4)
     ap.add_argument("--iters", type=int, default=3)
@@ -38,6 +41,8 @@ def main(argv=None) -> int:
     ap.add_argument("--band-row", type=int, choices=[-1, 0, 1], default=-1,
                     help="band-limited row pass variant (0 default row tile, 1 half-height tiles; -1 autotune)")
     ap.add_argument("--dtype", choices=["fp32", "bf16"], default="bf16")
+    ap.add_argument("--batch", type=int, default=24)
+    ap.add_argument("--cuda-cores", action="store_true", help="unet: 3x3x3 convs on the CUDA cores")
     a = ap.parse_args(argv)
     B.build()
     C.load()
@@ -45,6 +50,28 @@ def main(argv=None) -> int:
     torch.cuda.set_device(dev)
     nx, ny, nz = (int(v) for v in a.shape.split(","))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if a.what == "unet":
+        ch = (16, 32, 64)
+        net = C.UNet(*ch, params=I.unet_params(ch, seed=1), dtype="bf16")
+        net.set_tensor_cores(not a.cuda_cores)
+        g = torch.Generator(device=dev).manual_seed(3)
+        x = torch.rand((a.batch, nz, ny, nx), generator=g, device=dev) * 2
+        t = torch.rand((a.batch, nz, ny, nx), generator=g, device=dev)
+        loss = torch.zeros((), dtype=torch.float64, device=dev)
+        out = {"probe": "unet", "shape": [nx, ny, nz], "batch": a.batch, "tensor_cores": not a.cuda_cores}
+        for name, fn in (("forward", lambda: net.forward(x)),
+                         ("train_step", lambda: (net.backward(x, t, loss), net.adam(1e-3)))):
+            fn()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(a.reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            out[name + "_ms"] = e0.elapsed_time(e1) / a.reps
+        net.check()
+        print(json.dumps(out), flush=True)
+        return 0
     if a.what == "prior":
         layers, ch = (8, 48) if a.dtype == "bf16" else (5, 32)
         ws_, bs_ = I.cnn_weights(layers, ch, seed=1)
@@ -97,11 +124,14 @@ def main(argv=None) -> int:
                                                     ctypes.byref(rep), st.cuda_stream), "clamp_reconstruct_host")
             call()
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
+            ts = []
             for _ in range(a.reps):
+                t0 = time.perf_counter()
                 call()
-            torch.cuda.synchronize()
-            out[name + "_ms"] = (time.perf_counter() - t0) / a.reps * 1e3
+                torch.cuda.synchronize()
+                ts.append((time.perf_counter() - t0) * 1e3)
+            out[name + "_ms"] = sum(ts) / len(ts)
+            out[name + "_ms_each"] = [round(t, 2) for t in ts]
         print(json.dumps(out), flush=True)
         return 0
     pupil = torch.from_numpy(I.circular_pupil(nx, ny, 0.35)).to(dev)
