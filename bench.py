@@ -582,6 +582,7 @@ def main():
 
     e2e_value = None
     e2e_calls_ms = []
+    e2e_clocks = None
     if args.e2e_calls > 0:
         e2e_call()  # warm-up (allocates the device cache)
         if world > 1:
@@ -589,12 +590,13 @@ def main():
         torch.cuda.synchronize()
         # each call is timed on its own (the call synchronises); the median is reported, so
         # one call that the host delays does not set the figure
-        e2e_calls_ms = []
-        for _ in range(args.e2e_calls):
-            t0 = time.perf_counter()
-            e2e_call()
-            torch.cuda.synchronize()
-            e2e_calls_ms.append((time.perf_counter() - t0) * 1e3)
+        with ClockSampler(torch.cuda.current_device()) as e2e_clk:
+            for _ in range(args.e2e_calls):
+                t0 = time.perf_counter()
+                e2e_call()
+                torch.cuda.synchronize()
+                e2e_calls_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e_clocks = e2e_clk.summary()
         e2e_t = max_over_ranks(float(np.median(e2e_calls_ms)) / 1e3, world, dev)
         e2e_value = job_throughput(n * L * e2e_iters, 1, world, e2e_t)
     h2d = L * n * 8 + wl.nx * wl.ny * 4 + wl.nz * 4
@@ -698,7 +700,8 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "step": f"one clamp_reconstruct_host call: upload y, init, {e2e_iters} iterations, download r*",
-                "calls_ms": [round(t, 2) for t in e2e_calls_ms], "statistic": "median over calls"},
+                "calls_ms": [round(t, 2) for t in e2e_calls_ms], "statistic": "median over calls",
+                "clocks": e2e_clocks},
         "gpu_launches": launches_per_iter * K,
         "clocks": clk.summary(),
         "ce_residual_last": ce_last, "finite": finite,
