@@ -130,6 +130,10 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
+// Persistent: a CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ... (tile t = x
+// tile fastest, then y pairs, then z pairs).  TMEM, the mbarrier and the zero block are set
+// up once; the first chunk of the next tile is staged while the current tile's epilogue
+// drains TMEM.
 template <int KIND, int CIN, int NPAD, bool LAST>
 __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
     k_conv3_tc(const uint4* __restrict__ in, const uint4* __restrict__ wpk, const float* __restrict__ bias,
@@ -148,8 +152,8 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   int* abort_flag = reinterpret_cast<int*>(tslot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * TCX, y0 = blockIdx.y * TY, z0 = blockIdx.z * Cfg::TZ;
   const long long plane = (long long)nx * ny, n = plane * nz;
+  const int tiles_x = nx / TCX, tiles_y = ny / TY, ntiles = tiles_x * tiles_y * (nz / Cfg::TZ);
 
   if (tid == 0) {
     tc::mbar_init(mbar, 1);
@@ -169,7 +173,7 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   constexpr uint32_t LBO_B = 3 * NPAD * 16;         // channel group 0 -> 1 within a (dz, dx) block
   constexpr uint32_t SPLIT_A = 16u * Cfg::HALO_VEC, SPLIT_B = 16u * Cfg::W_VEC;  // hi -> lo copies
   bool aborted = false;
-  uint32_t fail_parity = 0;
+  uint32_t phase = 0;   // MMA commits completed so far (the mbarrier's phase parity)
 
   // Chunk staging: cp.async 16-byte copies (zero-fill outside the volume), all in flight
   // at once, in one commit group per halo plane: group p holds halo plane p and the
@@ -183,6 +187,32 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   constexpr int WDZ = Cfg::W_VEC / 3;   // weights of one dz
   const uint64_t a0 = tc::make_desc(halo_s, LBO_A, 128);
   const uint64_t b0 = tc::make_desc(w_s, LBO_B, 128);
+  auto stage = [&](int c, int x0, int y0, int z0) {
+#pragma unroll
+    for (int hz = 0; hz < HZ; ++hz) {
+      if (hz < 3) {
+        for (int sp = 0; sp < Kd::SPLIT; ++sp) {
+          const uint4* wsrc = wpk + ((long long)sp * Cfg::CHUNKS + c) * Cfg::W_VEC + hz * WDZ;
+          uint4* wdst = s_w + sp * Cfg::W_VEC + hz * WDZ;
+          for (int e = tid; e < WDZ; e += TC_NT) cp_async16(&wdst[e], &wsrc[e], true);
+        }
+      }
+      const int gz = z0 + hz - 1;
+      for (int r = warp; r < 2 * HY; r += TC_NT / 32) {
+        const int cg = r / HY, yr = r % HY;
+        const int gy = y0 + yr - 1;
+        const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+        const long long rbase = (long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx;
+        uint4* drow = s_raw + ((cg * HZ + hz) * HY + yr) * TC_HX;
+        for (int xr = lane; xr < TC_HX; xr += 32) {
+          const int gx = x0 + xr - 1;
+          const bool inb = rin && gx >= 0 && gx < nx;
+          cp_async16(&drow[xr], inb ? &in[rbase + gx] : in, inb);
+        }
+      }
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+  };
   // MMAs of one chunk that read halo plane hz: tiles tz with tap dz = hz - tz.  Descriptors
   // differ only in the start-address field (bits 0-13, 16-byte units), so each MMA adds a
   // compile-time offset to a base descriptor.
@@ -214,87 +244,86 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
       }
     }
   };
-  auto clear_acc = [&]() {   // D = A x 0 for every accumulator (first chunk)
+  auto clear_acc = [&]() {   // D = A x 0 for every accumulator (first chunk of a tile)
     const uint64_t bz = tc::make_desc(z_s, NPAD * 16, 128);
 #pragma unroll
     for (int mt = 0; mt < MT; ++mt) mma_kind(KIND, tbase + (uint32_t)(mt * NPAD), a0, bz, Kd::idesc(128, NPAD), 0u);
   };
   static_assert(HZ == 4, "one commit group per halo plane: the waits below name groups 3..0");
-  for (int c = 0; c < Cfg::CHUNKS; ++c) {
+
+  int tile = blockIdx.x;
+  auto origin = [&](int t, int& x0, int& y0, int& z0) {
+    x0 = (t % tiles_x) * TCX;
+    t /= tiles_x;
+    y0 = (t % tiles_y) * TY;
+    z0 = (t / tiles_y) * Cfg::TZ;
+  };
+  if (tile < ntiles) {
+    int x0, y0, z0;
+    origin(tile, x0, y0, z0);
+    stage(0, x0, y0, z0);
+  }
+  while (tile < ntiles && !aborted) {
+    int x0, y0, z0;
+    origin(tile, x0, y0, z0);
+    for (int c = 0; c < Cfg::CHUNKS; ++c) {
+      if (c > 0) stage(c, x0, y0, z0);   // the buffers are free: the previous chunk's MMAs completed
+      if constexpr (KIND == TC_BF16) {
 #pragma unroll
-    for (int hz = 0; hz < HZ; ++hz) {
-      if (hz < 3) {
-        for (int sp = 0; sp < Kd::SPLIT; ++sp) {
-          const uint4* wsrc = wpk + ((long long)sp * Cfg::CHUNKS + c) * Cfg::W_VEC + hz * WDZ;
-          uint4* wdst = s_w + sp * Cfg::W_VEC + hz * WDZ;
-          for (int e = tid; e < WDZ; e += TC_NT) cp_async16(&wdst[e], &wsrc[e], true);
+        for (int hz = 0; hz < HZ; ++hz) {
+          if (hz == 0) asm volatile("cp.async.wait_group 3;" ::: "memory");
+          else if (hz == 1) asm volatile("cp.async.wait_group 2;" ::: "memory");
+          else if (hz == 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
+          else asm volatile("cp.async.wait_group 0;" ::: "memory");
+          tc::fence_proxy_async();
+          __syncthreads();
+          if (tid == 0) {
+            tc::fence_after_sync();
+            if (c == 0 && hz == 0) clear_acc();
+            issue_plane(hz);
+            if (hz == HZ - 1) tc::mma_commit(mbar);
+          }
         }
-      }
-      const int gz = z0 + hz - 1;
-      for (int r = warp; r < 2 * HY; r += TC_NT / 32) {
-        const int cg = r / HY, yr = r % HY;
-        const int gy = y0 + yr - 1;
-        const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
-        const long long rbase = (long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx;
-        uint4* drow = s_raw + ((cg * HZ + hz) * HY + yr) * TC_HX;
-        for (int xr = lane; xr < TC_HX; xr += 32) {
-          const int gx = x0 + xr - 1;
-          const bool inb = rin && gx >= 0 && gx < nx;
-          cp_async16(&drow[xr], inb ? &in[rbase + gx] : in, inb);
+      } else {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
+        __syncthreads();
+        float4* hi = reinterpret_cast<float4*>(s_halo);
+        float4* lo = reinterpret_cast<float4*>(s_raw);
+        for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
+          const float4 f = lo[e];
+          const float4 h = make_float4(tf32_rn(f.x), tf32_rn(f.y), tf32_rn(f.z), tf32_rn(f.w));
+          hi[e] = h;
+          lo[e] = make_float4(tf32_rn(f.x - h.x), tf32_rn(f.y - h.y), tf32_rn(f.z - h.z), tf32_rn(f.w - h.w));
         }
-      }
-      asm volatile("cp.async.commit_group;" ::: "memory");
-    }
-    if constexpr (KIND == TC_BF16) {
-#pragma unroll
-      for (int hz = 0; hz < HZ; ++hz) {
-        if (hz == 0) asm volatile("cp.async.wait_group 3;" ::: "memory");
-        else if (hz == 1) asm volatile("cp.async.wait_group 2;" ::: "memory");
-        else if (hz == 2) asm volatile("cp.async.wait_group 1;" ::: "memory");
-        else asm volatile("cp.async.wait_group 0;" ::: "memory");
         tc::fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
           tc::fence_after_sync();
-          if (c == 0 && hz == 0) clear_acc();
-          issue_plane(hz);
-          if (hz == HZ - 1) tc::mma_commit(mbar);
+          if (c == 0) clear_acc();
+#pragma unroll
+          for (int hz = 0; hz < HZ; ++hz) issue_plane(hz);
+          tc::mma_commit(mbar);
         }
       }
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      // the chunk's MMAs read the buffers the next chunk overwrites: one thread waits for
+      // their commit, the others at the barrier (which takes no issue slots from the CTA
+      // staging beside this one)
+      if (tid == 0 && !tc::mbar_wait_bounded(mbar, phase & 1u, kWaitLimit)) *abort_flag = 1;
       __syncthreads();
-      float4* hi = reinterpret_cast<float4*>(s_halo);
-      float4* lo = reinterpret_cast<float4*>(s_raw);
-      for (int e = tid; e < Cfg::HALO_VEC; e += TC_NT) {
-        const float4 f = lo[e];
-        const float4 h = make_float4(tf32_rn(f.x), tf32_rn(f.y), tf32_rn(f.z), tf32_rn(f.w));
-        hi[e] = h;
-        lo[e] = make_float4(tf32_rn(f.x - h.x), tf32_rn(f.y - h.y), tf32_rn(f.z - h.z), tf32_rn(f.w - h.w));
+      if (*abort_flag) {
+        aborted = true;
+        break;
       }
-      tc::fence_proxy_async();
-      __syncthreads();
-      if (tid == 0) {
-        tc::fence_after_sync();
-        if (c == 0) clear_acc();
-#pragma unroll
-        for (int hz = 0; hz < HZ; ++hz) issue_plane(hz);
-        tc::mma_commit(mbar);
-      }
+      ++phase;
     }
-    // the chunk's MMAs read the buffers the next chunk overwrites: one thread waits for
-    // their commit, the others at the barrier (which takes no issue slots from the CTA
-    // staging beside this one)
-    if (tid == 0 && !tc::mbar_wait_bounded(mbar, (uint32_t)(c & 1), kWaitLimit)) *abort_flag = 1;
-    __syncthreads();
-    if (*abort_flag) {
-      aborted = true;
-      fail_parity = (uint32_t)(c & 1);
-      break;
+    if (aborted) break;
+    const int next = tile + (int)gridDim.x;
+    if (next < ntiles) {   // the next tile's first chunk lands while this tile's epilogue runs
+      int nx0, ny0, nz0;
+      origin(next, nx0, ny0, nz0);
+      stage(0, nx0, ny0, nz0);
     }
-  }
-  tc::fence_after_sync();
-  if (!aborted) {
+    tc::fence_after_sync();
     const int q = warp & 3, h = warp >> 2;
 #pragma unroll 1
     for (int mt = 0; mt < MT; ++mt) {
@@ -331,11 +360,17 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
         }
       }
     }
-  } else if (tid == 0) {
+    // every TMEM read of this tile completes before the next tile's first MMA overwrites it
+    tc::fence_before_sync();
+    __syncthreads();
+    tile = next;
+  }
+  if (aborted && tid == 0) {
     if (err) atomicOr(err, 2);
     // the chunk's MMAs may still be in flight: give them a bounded wait before TMEM is freed
-    tc::mbar_wait_bounded(mbar, fail_parity, kWaitLimit);
+    tc::mbar_wait_bounded(mbar, phase & 1u, kWaitLimit);
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");   // no copy may land after the CTA exits
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, Cfg::TMEM_COLS);
@@ -615,7 +650,7 @@ template <int C>
 __global__ void __launch_bounds__(CL_NT, 4) k_conv_last(const float4* __restrict__ act, const float* __restrict__ w,
                                                      const float* __restrict__ bias, const float* __restrict__ resid,
                                                      float* __restrict__ out, int nx, int ny, int nz) {
-  constexpr int G = C / 4, HV = CL_HZ * CL_HY * CL_HX;
+  constexpr int G = C / 4;
   extern __shared__ float4 s_h[];     // [CL_HZ][CL_HY][CL_HX]
   __shared__ float4 s_w[27 * G];      // [tap][channel group]: 4 channels' weights
   const int tid = threadIdx.x, tx = tid % 32, ty = tid / 32;
@@ -813,7 +848,13 @@ static cudaError_t run_tc(const uint4* in, const uint4* wpk, const float* bias, 
   auto kern = k_conv3_tc<KIND, CIN, NPAD, LAST>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   if (e != cudaSuccess) return e;
-  dim3 grid(nx / TCX, ny / Cfg::TY, nz / Cfg::TZ);
+  // persistent: MIN_CTAS CTAs per SM, each walking tiles
+  int dev = 0, sms = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const long long ntiles = (long long)(nx / TCX) * (ny / Cfg::TY) * (nz / Cfg::TZ);
+  const int grid = (int)std::min<long long>(ntiles, (long long)sms * TcKind<KIND>::MIN_CTAS);
   kern<<<grid, TC_NT, Cfg::SMEM, st>>>(in, wpk, bias, out_act, out_f32, resid, nx, ny, nz, err);
   return cudaGetLastError();
 }

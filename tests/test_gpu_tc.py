@@ -94,10 +94,12 @@ def _bf16_cnn(layers, channels, seed, last_scale=0.3):
 
 @pytest.mark.parametrize("shape,layers,channels", [((4, 8, 128), 8, 48), ((2, 4, 256), 4, 48),
                                                    ((4, 8, 128), 4, 16), ((2, 8, 128), 4, 32),
-                                                   ((2, 4, 128), 3, 64), ((4, 12, 256), 3, 48)])
+                                                   ((2, 4, 128), 3, 64), ((4, 12, 256), 3, 48),
+                                                   ((16, 64, 256), 3, 48), ((32, 64, 256), 3, 16)])
 def test_bf16_cnn_matches_oracle(C, shape, layers, channels):
     """Tiles at every volume edge (x0 - 1 < 0, the last rows and planes); 3, 4 and 8 layers
-    (the last layer's tap sums land in either activation buffer)."""
+    (the last layer's tap sums land in either activation buffer); 512 and 1024 tiles, more
+    than the persistent hidden-layer kernel's CTAs, so CTAs walk several tiles."""
     ws, bs = _bf16_cnn(layers, channels, seed=layers * 7 + channels)
     rng = np.random.default_rng(1)
     x = rng.uniform(0, 1, shape).astype(np.float32)
