@@ -294,8 +294,9 @@ clamp_status clamp_autotune(const clamp_params* p, const float* y, const float* 
 /* Sets the cached choice for a geometry by hand (host int32[5]). */
 clamp_status clamp_autotune_set(const clamp_params* p, const int32_t* variants);
 /* Sets the band-limited schedule's row-pass variant for a geometry (0: the default tile of
- * rows per CTA; 1: tiles of half as many rows, three CTAs per SM), keeping the other cached
- * choices.  clamp_autotune times both and keeps the faster. */
+ * rows per CTA; 1: tiles of half as many rows, three CTAs per SM; 2: the default tile with
+ * mu and r' prefetched to L2 and read after the inverse transform, three CTAs per SM),
+ * keeping the other cached choices.  clamp_autotune times all three and keeps the fastest. */
 clamp_status clamp_autotune_set_band(const clamp_params* p, int32_t row_variant);
 /* Which forward-agent schedule iterations with these parameters and this aperture run
  * (CLAMP_FLAG_*_SPECTRUM, the autotuner's cached choice, else the band-limited one when its

@@ -281,7 +281,8 @@ def autotune_set(p: Params, variants) -> None:
 
 
 def autotune_set_band(p: Params, row_variant: int) -> None:
-    """Band-limited schedule's row pass for this geometry: 0 the default row tile, 1 half-height tiles."""
+    """Band-limited schedule's row pass for this geometry: 0 the default row tile, 1 half-height
+    tiles, 2 the default tile with mu and r' read after the inverse transform."""
     _check(load().clamp_autotune_set_band(ctypes.byref(p), row_variant), "clamp_autotune_set_band")
 
 

@@ -234,17 +234,28 @@ enum BandRowMode { BAND_GRAD = 0, BAND_SPEC = 1 };
 // registers: with no occupancy bound the compiler takes about 180 and one CTA runs per SM,
 // 0.5 ms slower per iteration at 256x256x128, L = 32); V = 1: half as many rows, so a
 // thread holds half the prefetched values and three CTAs share an SM (at N = 256 with the
-// 8 x 8 x 4 radix plan, whose stages keep all threads of an 8-row tile busy).
+// 8 x 8 x 4 radix plan, whose stages keep all threads of an 8-row tile busy); V = 2: the
+// tile of V = 0 with mu and r' not held in registers across the inverse transform: the CTA
+// first prefetches their lines into L2 (no registers held) and reads them after the
+// transform, so three CTAs share an SM.
 template <int N, int MODE, int V>
-__global__ void __launch_bounds__(NT, V == 1 ? 3 : 2) k_band_x(BandArgs a, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(NT, V == 0 ? 2 : 3) k_band_x(BandArgs a, const float2* __restrict__ tw) {
   constexpr int LX = V == 1 ? variant_rows(N, 2) : rows_per_cta(N), LD = N + 1, CNT = LX * N,
                 PER = (CNT + NT - 1) / NT;
+  constexpr bool LATE = V == 2 && MODE == BAND_GRAD;   // mu, r' read after the inverse transform
   using PL = std::conditional_t<V == 1 && N == 256, PlanB<N>, Plan<N>>;
   float2* sm = reinterpret_cast<float2*>(band_smem);
   const long long row0 = (long long)blockIdx.x * LX;   // rows over [L][nz][ny]
   const long long e0 = row0 * N;
-  float2 mv[PER], ev[PER];
-  float rv[PER];
+  float2 mv[LATE ? 1 : PER], ev[PER];
+  float rv[LATE ? 1 : PER];
+  if constexpr (LATE) {   // 128-byte lines of the tile's mu (8 B per element) and r' (4 B)
+    static_assert(CNT % 32 == 0, "tile");
+    for (int i = threadIdx.x; i < CNT / 16; i += NT)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.mu + e0 + 16 * i));
+    for (int i = threadIdx.x; i < CNT / 32; i += NT)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a.rprev + e0 + 32 * i));
+  }
   // with NT a multiple of N every element a thread touches is in the same column
   constexpr bool FIXED_COL = NT % N == 0;
   const int b_fixed = FIXED_COL && MODE == BAND_GRAD ? __ldg(&a.t.bpos[threadIdx.x % N]) : -1;
@@ -252,9 +263,9 @@ __global__ void __launch_bounds__(NT, V == 1 ? 3 : 2) k_band_x(BandArgs a, const
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
-      mv[p] = a.mu[e0 + e];
+      if constexpr (!LATE) mv[p] = a.mu[e0 + e];
       if constexpr (MODE == BAND_GRAD) {
-        rv[p] = a.rprev[e0 + e];
+        if constexpr (!LATE) rv[p] = a.rprev[e0 + e];
         const int line = e / N, i = e - line * N;
         const int b = FIXED_COL ? b_fixed : __ldg(&a.t.bpos[i]);
         ev[p] = b >= 0 ? a.band[(row0 + line) * a.t.nbxp + b] : make_float2(0.f, 0.f);
@@ -266,7 +277,7 @@ __global__ void __launch_bounds__(NT, V == 1 ? 3 : 2) k_band_x(BandArgs a, const
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
       const int line = e / N, i = e - line * N;
-      sm[line * LD + i] = MODE == BAND_GRAD ? ev[p] : mv[p];
+      sm[line * LD + i] = MODE == BAND_GRAD ? ev[p] : mv[LATE ? 0 : p];
     }
   }
   __syncthreads();
@@ -279,8 +290,9 @@ __global__ void __launch_bounds__(NT, V == 1 ? 3 : 2) k_band_x(BandArgs a, const
       if (CNT % NT == 0 || e < CNT) {
         const int line = e / N, i = e - line * N;
         const float2 ee = cscale(sm[line * LD + i], a.sc_x);
-        const float D = __frcp_rn(rv[p] + a.floor);
-        const float2 dv = make_float2(fmaf(-D, mv[p].x, ee.x), fmaf(-D, mv[p].y, ee.y));
+        const float2 m = LATE ? a.mu[e0 + e] : mv[LATE ? 0 : p];
+        const float D = __frcp_rn((LATE ? a.rprev[e0 + e] : rv[LATE ? 0 : p]) + a.floor);
+        const float2 dv = make_float2(fmaf(-D, m.x, ee.x), fmaf(-D, m.y, ee.y));
         a.d[e0 + e] = dv;
         const float d2 = cabs2(dv);
         acc[0] += d2;
@@ -455,6 +467,13 @@ cudaError_t run_x(const BandArgs& a, int L, int mode, int variant, cudaStream_t 
       const size_t smem = (size_t)LX * (N + 1) * sizeof(float2);
       BAND_TRY(smem_attr(k_band_x<N, BAND_GRAD, 1>, smem));
       k_band_x<N, BAND_GRAD, 1><<<(unsigned)((long long)L * a.nz * a.ny / LX), NT, smem, st>>>(a, twiddle_table(N));
+      return cudaGetLastError();
+    }
+    if (mode == BAND_GRAD && variant == 2) {
+      constexpr int LX = rows_per_cta(N);
+      const size_t smem = (size_t)LX * (N + 1) * sizeof(float2);
+      BAND_TRY(smem_attr(k_band_x<N, BAND_GRAD, 2>, smem));
+      k_band_x<N, BAND_GRAD, 2><<<(unsigned)((long long)L * a.nz * a.ny / LX), NT, smem, st>>>(a, twiddle_table(N));
       return cudaGetLastError();
     }
     constexpr int LX = rows_per_cta(N);

@@ -539,7 +539,7 @@ clamp_status autotune_agent(const clamp_params* p, const ReconPlan& d, const flo
     a.gamma_prev = at<float>(ws, al.gamma);
     float band_ms = 1e30f;
     cudaError_t e = launch_band_tables(pupil, p->nx, p->ny, a.t, st);
-    for (int xv = 0; xv < 2 && e == cudaSuccess; ++xv) {
+    for (int xv = 0; xv < 3 && e == cudaSuccess; ++xv) {
       e = launch_band_agent(a, p->looks, p->noise_var, at<float>(ws, al.gamma), at<double>(ws, al.mures), xv, st);
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
       for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep)
@@ -604,8 +604,8 @@ extern "C" clamp_status clamp_agent_schedule(const clamp_params* p, const float*
 
 extern "C" clamp_status clamp_autotune_set_band(const clamp_params* p, int32_t row_variant) {
   API_TRY(clamp_check_params(p));
-  if (row_variant != 0 && row_variant != 1)
-    return api_fail(CLAMP_EINVAL, "clamp_autotune_set_band: row_variant=%d must be 0 or 1", row_variant);
+  if (row_variant < 0 || row_variant > 2)
+    return api_fail(CLAMP_EINVAL, "clamp_autotune_set_band: row_variant=%d must be 0, 1 or 2", row_variant);
   Geom g{p->nx, p->ny, p->nz, p->looks, (long long)p->nx * p->ny * p->nz};
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[tune_key(g)].band_x = row_variant;

@@ -28,7 +28,7 @@ __host__ __device__ constexpr int pipe_cols(int N) { return N > 128 ? 8 : 16; }
 struct AgentVariants {
   int v[5] = {0, 0, 0, 0, 0};
   int schedule = -1;   // forward-agent schedule: -1 not timed (band-limited when it fits), 0 full spectrum, 1 band-limited
-  int band_x = 0;      // band-limited row pass: 0 rows_per_cta rows per CTA, 1 half as many
+  int band_x = 0;      // band-limited row pass: 0 rows_per_cta rows per CTA, 1 half as many, 2 mu / r' read late
 };
 // True if variant V of pass `pass` can run on the geometry.
 bool variant_valid(int pass, int V, int nx, int ny, int nz);
@@ -95,14 +95,15 @@ BandShape band_shape(const float* pupil_host, int nx, int ny);
 size_t band_table_bytes(const BandShape& b, int nx, int ny);
 BandTables band_tables_at(const BandShape& b, int nx, int ny, void* base);
 int band_pS(const BandShape& b);
-// S1 / S3 partial sums per look of the row pass (x_variant 0: rows_per_cta rows per CTA; 1: half as many).
+// S1 / S3 partial sums per look of the row pass (x_variant 0, 2: rows_per_cta rows per CTA; 1: half as many).
 int band_px(int nx, int ny, int nz, int x_variant);
 // Builds the device tables from the device pupil (one CTA).
 cudaError_t launch_band_tables(const float* pupil, int nx, int ny, const BandTables& t, cudaStream_t st);
 // Ms <- F mu on the support (first axis x over whole rows, then y and z on band / support).
 cudaError_t launch_band_spectrum(const BandArgs& a, int L, cudaStream_t st);
 // P1-P5 and the line search: d, F d on the support, gamma_l and the floored mu-residual per look.
-// x_variant: 0 the row pass with rows_per_cta rows per CTA, 1 with half as many (three CTAs per SM).
+// x_variant: 0 the row pass with rows_per_cta rows per CTA, 1 with half as many (three CTAs per SM), 2 the
+// first with mu and r' prefetched to L2 and read after the inverse transform (three CTAs per SM).
 cudaError_t launch_band_agent(const BandArgs& a, int L, float nv, float* gamma, double* mures, int x_variant,
                               cudaStream_t st);
 

@@ -38,8 +38,9 @@ def main(argv=None) -> int:
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--schedule", choices=["auto", "band", "full"], default="auto")
     ap.add_argument("--prior", choices=["gauss", "cnn-bf16", "cnn-fp32"], default="gauss")
-    ap.add_argument("--band-row", type=int, choices=[-1, 0, 1], default=-1,
-                    help="band-limited row pass variant (0 default row tile, 1 half-height tiles; -1 autotune)")
+    ap.add_argument("--band-row", type=int, choices=[-1, 0, 1, 2], default=-1,
+                    help="band-limited row pass variant (0 default row tile, 1 half-height tiles, "
+                         "2 mu and r' read late; -1 autotune)")
     ap.add_argument("--dtype", choices=["fp32", "bf16"], default="bf16")
     ap.add_argument("--batch", type=int, default=24)
     ap.add_argument("--cuda-cores", action="store_true", help="unet: 3x3x3 convs on the CUDA cores")

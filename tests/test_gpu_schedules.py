@@ -59,7 +59,10 @@ def _problem(shape, L, pupil_kind, seed):
     return wl, a, y32
 
 
-@pytest.mark.parametrize("flag", ["full", "band", "band_pipelined"])
+ROW_VARIANT = {"band": 0, "band_half_rows": 1, "band_late_loads": 2}
+
+
+@pytest.mark.parametrize("flag", ["full", "band", "band_half_rows", "band_late_loads"])
 @pytest.mark.parametrize("shape,L,pupil_kind", [((64, 32, 16), 2, "circle"), ((96, 96, 32), 1, "circle"),
                                                  ((16, 8, 8), 1, "one_column"), ((96, 32, 16), 3, "ragged"),
                                                  ((32, 32, 16), 2, "wide"), ((256, 16, 8), 2, "circle")])
@@ -77,7 +80,7 @@ def test_forward_prox_both_schedules(C, flag, shape, L, pupil_kind):
             for l in range(L)]
     f = C.FLAG_FULL_SPECTRUM if flag == "full" else C.FLAG_BAND_SPECTRUM
     p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var, flags=f)
-    C.autotune_set_band(p, 1 if flag == "band_pipelined" else 0)
+    C.autotune_set_band(p, ROW_VARIANT.get(flag, 0))
     mu, r, wd = to_dev(mu0), to_dev(r0), to_dev(w0)
     mres = torch.zeros((), dtype=torch.float64, device="cuda")
     try:
@@ -101,10 +104,10 @@ def test_reconstruct_both_schedules(C, shape, L, pupil_kind):
     ref, st = O.reconstruct(y32.astype(np.complex128), wl.pupil, wl.window, wl.denoiser, wl.noise_var,
                             wl.prox_var, 6)
     out = {}
-    for flag in ("full", "band", "band_pipelined"):
+    for flag in ("full", "band", "band_half_rows", "band_late_loads"):
         f = C.FLAG_FULL_SPECTRUM if flag == "full" else C.FLAG_BAND_SPECTRUM
         p = C.make_params(wl.nx, wl.ny, wl.nz, L, wl.noise_var, wl.prox_var, max_iters=6, flags=f)
-        C.autotune_set_band(p, 1 if flag == "band_pipelined" else 0)
+        C.autotune_set_band(p, ROW_VARIANT.get(flag, 0))
         try:
             res = C.reconstruct(p, to_dev(y32), to_dev(wl.pupil), to_dev(wl.window), C.Denoiser.gauss(0.8))
         finally:
@@ -114,7 +117,8 @@ def test_reconstruct_both_schedules(C, shape, L, pupil_kind):
         np.testing.assert_allclose(res.ce_hist, st.ce_hist, rtol=1e-3)
         np.testing.assert_allclose(res.mu_hist, st.mu_res_hist, rtol=1e-3)
     assert rel(out["band"], out["full"]) < 2e-5
-    assert rel(out["band_pipelined"], out["band"]) < 2e-5
+    assert rel(out["band_half_rows"], out["band"]) < 2e-5
+    assert rel(out["band_late_loads"], out["band"]) < 2e-5
 
 
 def test_band_schedule_long_run_tracks_oracle(C):
