@@ -790,8 +790,10 @@ __global__ void __launch_bounds__(NT) k_pass_c(Geom g, PassC c) {
 // false> per voxel, with 16-byte loads of mu and d and 8-byte loads of r and w, so each
 // memory request carries two voxels (n even; the launcher checks the pointers'
 // alignment and otherwise uses the one-voxel kernel).  The look-sum loop keeps the loads
-// of the next two looks in flight (the grid is small, to keep the Mann loop's re-reads in
-// L2, so each thread needs more bytes in flight).
+// of the next two looks in flight and asks L2 for the look six ahead (the grid is small,
+// to keep the Mann loop's re-reads in L2, so each thread needs more bytes in flight).
+constexpr int kPassCPrefetch = 6;   // looks ahead that the look-sum loop prefetches into L2
+
 __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
   const long long n2 = g.n / 2;
   const int L = g.L;
@@ -817,6 +819,7 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
       m_a = MUi[n2 + vp];
       d_a = Di[n2 + vp];
     }
+    float kacc = 0.f;   // sum of K over the looks: non-finite iff some K (so some mu) is
     for (int l = 0; l < L; ++l) {
       const long long i = (long long)l * n2 + vp;
       const float2 wl = w_n, rp = r_n;
@@ -832,6 +835,13 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
         m_a = MUi[i + 2 * n2];
         d_a = Di[i + 2 * n2];
       }
+      if (l + kPassCPrefetch < L) {   // look l + kPassCPrefetch into L2: no registers held
+        const long long ip = i + kPassCPrefetch * n2;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(Wi + ip));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(Ri + ip));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(MUi + ip));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(Di + ip));
+      }
       if (c.closed_mu) {  // no-aperture ablation: d holds F^H y
         const float f0 = 1.0f / (1.0f + c.nv / (rp.x + c.nv)), f1 = 1.0f / (1.0f + c.nv / (rp.y + c.nv));
         m = make_float4(dd.x * f0, dd.y * f0, dd.z * f1, dd.w * f1);
@@ -846,7 +856,7 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
       const float2 rn = make_float2(prox_quad(wl.x, rp.x, K0, c.prox_var, c.inv_prox_var, c.beta, c.inv_beta),
                                     prox_quad(wl.y, rp.y, K1, c.prox_var, c.inv_prox_var, c.beta, c.inv_beta));
       Ro[i] = rn;
-      bad |= !isfinite(rn.x) || !isfinite(rn.y) || !isfinite(K0) || !isfinite(K1);   // K covers mu
+      kacc += K0 + K1;   // K covers mu: the prox's clip would hide a NaN there
       wb0.add(c.ups_look * wl.x);
       wb1.add(c.ups_look * wl.y);
       xb0.add(c.ups_look * (2.0f * rn.x - wl.x));
@@ -879,9 +889,13 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
       const float ups = j < L ? c.ups_look : c.ups_prior;
       wn0.add(ups * wn.x);
       wn1.add(ups * wn.y);
-      bad |= !isfinite(wn.x) || !isfinite(wn.y);
     }
-    reinterpret_cast<float2*>(c.wbar)[vp] = make_float2(wn0.get(), wn1.get());
+    const float wbn0 = wn0.get(), wbn1 = wn1.get();
+    reinterpret_cast<float2*>(c.wbar)[vp] = make_float2(wbn0, wbn1);
+    // a non-finite r, w or K of any look reaches these sums (NaN and Inf propagate through
+    // the adds), so one check per voxel pair replaces one per value
+    bad = !isfinite(kacc) || !isfinite(x0) || !isfinite(x1) || !isfinite(w0) || !isfinite(w1) ||
+          !isfinite(wbn0) || !isfinite(wbn1);
     acc[0] += num;
     acc[1] += (float)(L + 1) * (w0 * w0 + w1 * w1);
     if (bad && c.err) atomicOr(c.err, 1);
