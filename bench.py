@@ -629,8 +629,8 @@ def main():
         tensor_path = wl.nx % 128 == 0 and ch in (16, 32, 48) and wl.ny % 2 == 0 and wl.nz % 2 == 0
         if wl.denoiser.get("dtype", "fp32") == "bf16":
             roofline = {"bound": "tensor",
-                        "kernel": "the prior agent: k_conv3_tc<BF16> hidden layers, k_conv_first_tc, "
-                                  "k_last_taps_tc + k_last_gather",
+                        "kernel": "the prior agent: k_conv3_tc<BF16> hidden layers (the last one also "
+                                  "forming the tap sums), k_conv_first_tc, k_last_gather",
                         "achieved": cnn_tflops, "peak": bf16_peak, "unit": "TFLOP/s",
                         "frac": cnn_tflops / bf16_peak, "traffic": TRAFFIC.get((wl.name, "prior")),
                         "peak_source": "measured bf16_tflops_sustained",
@@ -673,11 +673,15 @@ def main():
         cpu = {"value": n * L / t_it, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle", "sample": desc}
 
     # kernels per iteration: the five agent passes and the line search, the prior (one per CNN
-    # layer; the BF16 last layer is a tap-sum GEMM plus a gather), the prox/Mann pass and the
-    # CE reduction (17 at 256x256x128 with the 8-layer BF16 CNN)
+    # layer; in BF16 the last hidden layer also forms the last layer's tap sums, which leaves
+    # the last layer a gather, except at 16 channels or with no hidden layer, where the tap
+    # sums are a kernel of their own), the prox/Mann pass and the CE reduction (16 at
+    # 256x256x128 with the 8-layer BF16 CNN)
     prior_k = 1
     if wl.denoiser["kind"] == "cnn":
-        prior_k = len(wl.denoiser["weights"]) + (1 if wl.denoiser.get("dtype", "fp32") == "bf16" else 0)
+        nlayers = len(wl.denoiser["weights"])
+        unfused = wl.denoiser["channels"] < 32 or nlayers < 3
+        prior_k = nlayers + (1 if wl.denoiser.get("dtype", "fp32") == "bf16" and unfused else 0)
     launches_per_iter = 5 + 1 + prior_k + 1 + 1
     warm = None
     if world == 1 and not args.no_warm_start:

@@ -134,11 +134,19 @@ __device__ __forceinline__ void cp_async_wait_all() {
 // tile fastest, then y pairs, then z pairs).  TMEM, the mbarrier and the zero block are set
 // up once; the first chunk of the next tile is staged while the current tile's epilogue
 // drains TMEM.
-template <int KIND, int CIN, int NPAD, bool LAST>
+//
+// TAPS (BF16, the network's last hidden layer): the layer's activations (bias, ReLU,
+// BF16) go to shared memory instead of HBM and feed at once the last layer's per-voxel tap
+// sums, P_tap[v] = sum_c W_last[tap][c] h[v][c], as a second GEMM (M = 128 voxels, K = C,
+// N = 27 taps padded to 32) into the tile's TMEM columns; the kernel writes P (FP32
+// [27][n]) and the last layer is left with its gather.  This saves writing and reading
+// the 2 C bytes per voxel of the last hidden activations.
+template <int KIND, int CIN, int NPAD, bool LAST, bool TAPS = false>
 __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
     k_conv3_tc(const uint4* __restrict__ in, const uint4* __restrict__ wpk, const float* __restrict__ bias,
                uint4* __restrict__ out_act, float* __restrict__ out_f32, const float* __restrict__ resid, int nx,
-               int ny, int nz, int* err) {
+               int ny, int nz, int* err, const uint4* __restrict__ wtaps = nullptr, float* __restrict__ P = nullptr) {
+  static_assert(!TAPS || (KIND == TC_BF16 && !LAST && NPAD >= 32 && NPAD % 16 == 0), "tap-sum fusion");
   using Cfg = TcCfg<KIND, CIN, NPAD>;
   using Kd = TcKind<KIND>;
   constexpr int TY = Cfg::TY, HY = Cfg::HY, HZ = Cfg::HZ, MT = Cfg::MT;
@@ -318,6 +326,81 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
     }
     if (aborted) break;
     const int next = tile + (int)gridDim.x;
+    if constexpr (TAPS) {
+      constexpr int G = NPAD / 8;   // channel groups of the activations (K of the tap GEMM)
+      // tap weights [G][32 taps][8 channels] into the weight buffer (free: the MMAs are done)
+      for (int e = tid; e < G * 32; e += TC_NT) cp_async16(&s_w[e], &wtaps[e], true);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      tc::fence_after_sync();
+      // the hidden layer's activations, as the tap GEMM's A: [MT][G][128 voxels] x 16 B in
+      // the halo buffer (free as well)
+      const int q = warp & 3, h = warp >> 2;
+#pragma unroll 1
+      for (int mt = 0; mt < MT; ++mt) {
+        const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * NPAD);
+        constexpr int HALF = NPAD / 2;
+#pragma unroll
+        for (int j = 0; j < HALF / 8; ++j) {
+          const int col = h * HALF + 8 * j;
+          float v[8];
+          tc::tmem_ld_x8(trow + (uint32_t)col, v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
+          s_halo[(mt * G + col / 8) * 128 + 32 * q + lane] =
+              make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                         pack_bf16x2(v[6], v[7]));
+        }
+      }
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      tc::fence_proxy_async();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (tid == 0) {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+          for (int ks = 0; ks < G / 2; ++ks)
+            tc::mma_bf16(tbase + (uint32_t)(mt * NPAD),
+                         tc::make_desc(halo_s + (uint32_t)((mt * G + 2 * ks) * 128 * 16), 128 * 16, 128),
+                         tc::make_desc(w_s + (uint32_t)(2 * ks * 32 * 16), 32 * 16, 128), Kd::idesc(128, 32),
+                         ks ? 1u : 0u);
+        tc::mma_commit(mbar);
+      }
+      if (tid == 0 && !tc::mbar_wait_bounded(mbar, phase & 1u, kWaitLimit)) *abort_flag = 1;
+      __syncthreads();
+      if (*abort_flag) {
+        aborted = true;
+        break;
+      }
+      ++phase;
+      tc::fence_after_sync();
+#pragma unroll 1
+      for (int mt = 0; mt < MT; ++mt) {
+        const int gy = y0 + mt % TY, gz = z0 + mt / TY, gx = x0 + 32 * q + lane;
+        const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
+        const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * NPAD);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          const int col = h * 16 + 8 * j;
+          float t[8];
+          tc::tmem_ld_x8(trow + (uint32_t)col, t);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (col + i < 27) P[(long long)(col + i) * n + vox] = t[i];
+        }
+      }
+      // TMEM reads and the shared buffers' last use complete before the next tile
+      tc::fence_before_sync();
+      __syncthreads();
+      if (next < ntiles) {
+        int nx0, ny0, nz0;
+        origin(next, nx0, ny0, nz0);
+        stage(0, nx0, ny0, nz0);
+      }
+      tile = next;
+      continue;
+    }
     if (next < ntiles) {   // the next tile's first chunk lands while this tile's epilogue runs
       int nx0, ny0, nz0;
       origin(next, nx0, ny0, nz0);
@@ -841,11 +924,12 @@ static float tf32_rn_host(float f) {
   return bits_to_float(u & 0xFFFFE000u);
 }
 
-template <int KIND, int CIN, int NPAD, bool LAST>
+template <int KIND, int CIN, int NPAD, bool LAST, bool TAPS = false>
 static cudaError_t run_tc(const uint4* in, const uint4* wpk, const float* bias, uint4* out_act, float* out_f32,
-                          const float* resid, int nx, int ny, int nz, int* err, cudaStream_t st) {
+                          const float* resid, int nx, int ny, int nz, int* err, cudaStream_t st,
+                          const uint4* wtaps = nullptr, float* P = nullptr) {
   using Cfg = TcCfg<KIND, CIN, NPAD>;
-  auto kern = k_conv3_tc<KIND, CIN, NPAD, LAST>;
+  auto kern = k_conv3_tc<KIND, CIN, NPAD, LAST, TAPS>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::SMEM);
   if (e != cudaSuccess) return e;
   // persistent: MIN_CTAS CTAs per SM, each walking tiles
@@ -855,7 +939,7 @@ static cudaError_t run_tc(const uint4* in, const uint4* wpk, const float* bias, 
   if (e != cudaSuccess) return e;
   const long long ntiles = (long long)(nx / TCX) * (ny / Cfg::TY) * (nz / Cfg::TZ);
   const int grid = (int)std::min<long long>(ntiles, (long long)sms * TcKind<KIND>::MIN_CTAS);
-  kern<<<grid, TC_NT, Cfg::SMEM, st>>>(in, wpk, bias, out_act, out_f32, resid, nx, ny, nz, err);
+  kern<<<grid, TC_NT, Cfg::SMEM, st>>>(in, wpk, bias, out_act, out_f32, resid, nx, ny, nz, err, wtaps, P);
   return cudaGetLastError();
 }
 
@@ -1152,13 +1236,23 @@ static cudaError_t apply_tc_c(const clamp_denoiser* d, const float* in, float* o
                       : run_first<C, KIND == TC_BF16>(in, d->w[0], d->b[0], A, nx, ny, nz, st);
   if (e != cudaSuccess) return e;
   uint4* cur = A;
+  // BF16 with at least one hidden layer and C >= 32: the last hidden layer also forms the
+  // last layer's tap sums (k_conv3_tc<..., TAPS>), so the last layer is only the gather
+  constexpr bool kFuse = KIND == TC_BF16 && C >= 32 && !tc_tall(KIND, C);
+  const bool fuse = kFuse && d->layers >= 3;
   for (int i = 1; i < d->layers; ++i) {
     const uint4* wp = static_cast<const uint4*>(d->w16[i]);
     if (i == d->layers - 1) {
       if constexpr (KIND == TC_BF16) {
-        // BF16: per-voxel tap sums on the tensor cores, then a gather (no halo staging)
-        float* P = reinterpret_cast<float*>(cur == A ? B : A);
-        e = run_last_tc<C>(cur, static_cast<const uint4*>(d->w_last), d->b[i], in, out, P, nx, ny, nz, err, st);
+        if (fuse) {   // cur holds the tap sums P
+          k_last_gather<<<(unsigned)((n + NT - 1) / NT), NT, 0, st>>>(reinterpret_cast<const float*>(cur), d->b[i],
+                                                                      in, out, nx, ny, nz);
+          e = cudaGetLastError();
+        } else {
+          // per-voxel tap sums on the tensor cores, then a gather (no halo staging)
+          float* P = reinterpret_cast<float*>(cur == A ? B : A);
+          e = run_last_tc<C>(cur, static_cast<const uint4*>(d->w_last), d->b[i], in, out, P, nx, ny, nz, err, st);
+        }
       } else {
         // TF32x3: the padded tile costs as much as a hidden layer; CUDA cores instead
         e = cudaFuncSetAttribute(k_conv_last<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CL_SMEM);
@@ -1170,10 +1264,17 @@ static cudaError_t apply_tc_c(const clamp_denoiser* d, const float* in, float* o
       }
     } else {
       uint4* dst = cur == A ? B : A;
-      if constexpr (tc_tall(KIND, C))
+      if constexpr (tc_tall(KIND, C)) {
         e = run_tc_plane<C, C>(cur, wp, d->b[i], dst, nx, ny, nz, err, st);
-      else
+      } else if constexpr (kFuse) {
+        if (fuse && i == d->layers - 2)   // P (FP32 [27][n]) goes to dst
+          e = run_tc<KIND, C, C, false, true>(cur, wp, d->b[i], nullptr, nullptr, nullptr, nx, ny, nz, err, st,
+                                              static_cast<const uint4*>(d->w_last), reinterpret_cast<float*>(dst));
+        else
+          e = run_tc<KIND, C, C, false>(cur, wp, d->b[i], dst, nullptr, nullptr, nx, ny, nz, err, st);
+      } else {
         e = run_tc<KIND, C, C, false>(cur, wp, d->b[i], dst, nullptr, nullptr, nx, ny, nz, err, st);
+      }
       cur = dst;
     }
     if (e != cudaSuccess) return e;
