@@ -125,14 +125,19 @@ def main(argv=None) -> int:
                                                     ctypes.byref(rep), st.cuda_stream), "clamp_reconstruct_host")
             call()
             torch.cuda.synchronize()
-            ts = []
+            ts, gs = [], []
             for _ in range(a.reps):
+                g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 t0 = time.perf_counter()
+                g0.record(st)
                 call()
+                g1.record(st)
                 torch.cuda.synchronize()
                 ts.append((time.perf_counter() - t0) * 1e3)
+                gs.append(g0.elapsed_time(g1))
             out[name + "_ms"] = sum(ts) / len(ts)
             out[name + "_ms_each"] = [round(t, 2) for t in ts]
+            out[name + "_gpu_ms_each"] = [round(t, 2) for t in gs]   # events on the stream around the call
         print(json.dumps(out), flush=True)
         return 0
     pupil = torch.from_numpy(I.circular_pupil(nx, ny, 0.35)).to(dev)
