@@ -102,7 +102,14 @@ struct TcCfg {
   static constexpr int HALO_VEC = 2 * HZ * HY * TC_HX;  // 16-byte vectors per chunk, per split
   static constexpr int W_VEC = 27 * 2 * NPAD;          // [dz][dx][2][dy = 2, 1, 0][NPAD]
   static constexpr int ZB_VEC = 2 * NPAD;              // zero weight block (accumulator clear)
-  static constexpr int TMEM_COLS = pow2_cols(MT * NPAD);
+  // BF16 2 x 2 tiles with 5 C_out <= 256: a halo row in the middle of both z-rows feeds the
+  // four tiles with one MMA (N = 5 C_out: the tiles' accumulators at TMEM columns
+  // (3 tz + ty) C_out, a spare block between the z-rows takes the fifth product), the
+  // weights held as [dx][cg][dz = 2, 1, 0][dy = 2, 1, 0] so the four taps (and the spare's)
+  // are consecutive blocks.
+  static constexpr bool MERGE = KIND == TC_BF16 && TY == 2 && TZ == 2 && 5 * NPAD <= 256;
+  static constexpr int CS = MERGE ? 3 : TY;             // accumulator blocks per z-row
+  static constexpr int TMEM_COLS = pow2_cols(MERGE ? 5 * NPAD : MT * NPAD);
   static constexpr size_t SMEM = 1024 + 16 * ((size_t)K::SPLIT * (HALO_VEC + W_VEC) + ZB_VEC) + 64;
   static_assert(CIN % CH == 0 && NPAD % 16 == 0 && MT * NPAD <= 512 && TY * NPAD <= 256, "tile");
   static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -178,8 +185,11 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   const uint32_t tbase = *tslot;
   const uint32_t halo_s = tc::smem_addr(s_halo), w_s = tc::smem_addr(s_w), z_s = tc::smem_addr(s_zero);
   constexpr uint32_t LBO_A = HZ * HY * TC_HX * 16;  // channel group 0 -> 1
-  constexpr uint32_t LBO_B = 3 * NPAD * 16;         // channel group 0 -> 1 within a (dz, dx) block
+  // channel group 0 -> 1: within a (dz, dx) block, or (merged layout) within a dx block
+  constexpr uint32_t LBO_B = (Cfg::MERGE ? 9 : 3) * NPAD * 16;
   constexpr uint32_t SPLIT_A = 16u * Cfg::HALO_VEC, SPLIT_B = 16u * Cfg::W_VEC;  // hi -> lo copies
+  // TMEM column of tile mt's accumulator (tile = ty + TY tz)
+  auto acc_col = [](int mt) { return (uint32_t)(((mt / TY) * Cfg::CS + mt % TY) * NPAD); };
   bool aborted = false;
   uint32_t phase = 0;   // MMA commits completed so far (the mbarrier's phase parity)
 
@@ -201,8 +211,15 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
       if (hz < 3) {
         for (int sp = 0; sp < Kd::SPLIT; ++sp) {
           const uint4* wsrc = wpk + ((long long)sp * Cfg::CHUNKS + c) * Cfg::W_VEC + hz * WDZ;
-          uint4* wdst = s_w + sp * Cfg::W_VEC + hz * WDZ;
-          for (int e = tid; e < WDZ; e += TC_NT) cp_async16(&wdst[e], &wsrc[e], true);
+          if constexpr (Cfg::MERGE) {   // packed [dx][cg][dy blk][n] of this dz -> [dx][cg][dz blk][dy blk][n]
+            for (int e = tid; e < WDZ; e += TC_NT) {
+              const int nn = e % NPAD, t = e / NPAD, dyb = t % 3, dxc = t / 3;   // dxc = 2 dx + cg
+              cp_async16(&s_w[(dxc * 9 + (2 - hz) * 3 + dyb) * NPAD + nn], &wsrc[e], true);
+            }
+          } else {
+            uint4* wdst = s_w + sp * Cfg::W_VEC + hz * WDZ;
+            for (int e = tid; e < WDZ; e += TC_NT) cp_async16(&wdst[e], &wsrc[e], true);
+          }
         }
       }
       const int gz = z0 + hz - 1;
@@ -225,22 +242,38 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   // differ only in the start-address field (bits 0-13, 16-byte units), so each MMA adds a
   // compile-time offset to a base descriptor.
   auto issue_plane = [&](int hz) {
+    if constexpr (Cfg::MERGE) {
+      if (hz == 1 || hz == 2) {   // middle rows of a middle plane: all four tiles, one MMA per dx
+#pragma unroll
+        for (int hy = 1; hy <= 2; ++hy) {
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) {
+            const uint64_t aoff = (uint64_t)((hz * HY + hy) * TC_HX + dx);
+            // blocks (dz, dy) = (hz, hy), (hz, hy - 1), spare, (hz - 1, hy), (hz - 1, hy - 1)
+            const uint64_t boff = (uint64_t)((dx * 18 + (2 - hz) * 3 + (2 - hy)) * NPAD);
+            mma_kind(KIND, tbase, a0 + aoff, b0 + boff, Kd::idesc(128, 5 * NPAD), 1u);
+          }
+        }
+      }
+    }
 #pragma unroll
     for (int tz = 0; tz < Cfg::TZ; ++tz) {
       const int dz = hz - tz;
       if (dz < 0 || dz > 2) continue;
 #pragma unroll
       for (int hy = 0; hy < HY; ++hy) {
+        if (Cfg::MERGE && (hz == 1 || hz == 2) && (hy == 1 || hy == 2)) continue;   // merged above
         // tiles ty_lo..ty_hi of z-row tz read halo row hy with taps dy = hy - ty
         const int ty_lo = hy - 2 > 0 ? hy - 2 : 0, ty_hi = hy < TY - 1 ? hy : TY - 1;
         const int ntile = ty_hi - ty_lo + 1;
         const uint32_t idesc = Kd::idesc(128, ntile * NPAD);
-        const uint32_t dcol = tbase + (uint32_t)((tz * TY + ty_lo) * NPAD);
+        const uint32_t dcol = tbase + acc_col(tz * TY + ty_lo);
         const int dyp = 2 - (hy - ty_lo);   // block index of the first tile's tap (dy = hy - ty_lo)
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) {
           const uint64_t aoff = (uint64_t)((hz * HY + hy) * TC_HX + dx);
-          const uint64_t boff = (uint64_t)((dz * 3 + dx) * 6 * NPAD + dyp * NPAD);
+          const uint64_t boff = Cfg::MERGE ? (uint64_t)((dx * 18 + (2 - dz) * 3 + dyp) * NPAD)
+                                           : (uint64_t)((dz * 3 + dx) * 6 * NPAD + dyp * NPAD);
 #pragma unroll
           for (int sp = 0; sp < (KIND == TC_BF16 ? 1 : 3); ++sp) {
             // TF32x3 terms: (a_lo, b_hi), (a_hi, b_lo), (a_hi, b_hi)
@@ -255,7 +288,7 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   auto clear_acc = [&]() {   // D = A x 0 for every accumulator (first chunk of a tile)
     const uint64_t bz = tc::make_desc(z_s, NPAD * 16, 128);
 #pragma unroll
-    for (int mt = 0; mt < MT; ++mt) mma_kind(KIND, tbase + (uint32_t)(mt * NPAD), a0, bz, Kd::idesc(128, NPAD), 0u);
+    for (int mt = 0; mt < MT; ++mt) mma_kind(KIND, tbase + acc_col(mt), a0, bz, Kd::idesc(128, NPAD), 0u);
   };
   static_assert(HZ == 4, "one commit group per halo plane: the waits below name groups 3..0");
 
@@ -337,7 +370,7 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
       const int q = warp & 3, h = warp >> 2;
 #pragma unroll 1
       for (int mt = 0; mt < MT; ++mt) {
-        const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * NPAD);
+        const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + acc_col(mt);
         constexpr int HALF = NPAD / 2;
 #pragma unroll
         for (int j = 0; j < HALF / 8; ++j) {
@@ -361,7 +394,7 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
         for (int mt = 0; mt < MT; ++mt)
 #pragma unroll
           for (int ks = 0; ks < G / 2; ++ks)
-            tc::mma_bf16(tbase + (uint32_t)(mt * NPAD),
+            tc::mma_bf16(tbase + acc_col(mt),
                          tc::make_desc(halo_s + (uint32_t)((mt * G + 2 * ks) * 128 * 16), 128 * 16, 128),
                          tc::make_desc(w_s + (uint32_t)(2 * ks * 32 * 16), 32 * 16, 128), Kd::idesc(128, 32),
                          ks ? 1u : 0u);
@@ -379,7 +412,7 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
       for (int mt = 0; mt < MT; ++mt) {
         const int gy = y0 + mt % TY, gz = z0 + mt / TY, gx = x0 + 32 * q + lane;
         const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
-        const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * NPAD);
+        const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + acc_col(mt);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
           const int col = h * 16 + 8 * j;
@@ -412,7 +445,7 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
     for (int mt = 0; mt < MT; ++mt) {
       const int gy = y0 + mt % TY, gz = z0 + mt / TY, gx = x0 + 32 * q + lane;
       const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
-      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * NPAD);
+      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + acc_col(mt);
       if constexpr (LAST) {   // one output channel (column 0): FP32 plus the residual input
         if (h == 0) {
           float v[8];
