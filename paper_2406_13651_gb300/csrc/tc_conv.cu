@@ -407,6 +407,13 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
         break;
       }
       ++phase;
+      // the tap GEMM has read both shared buffers: the next tile's first chunk lands while
+      // the tap sums drain
+      if (next < ntiles) {
+        int nx0, ny0, nz0;
+        origin(next, nx0, ny0, nz0);
+        stage(0, nx0, ny0, nz0);
+      }
       tc::fence_after_sync();
 #pragma unroll 1
       for (int mt = 0; mt < MT; ++mt) {
@@ -423,14 +430,9 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
             if (col + i < 27) P[(long long)(col + i) * n + vox] = t[i];
         }
       }
-      // TMEM reads and the shared buffers' last use complete before the next tile
+      // TMEM reads complete before the next tile's first MMA overwrites them
       tc::fence_before_sync();
       __syncthreads();
-      if (next < ntiles) {
-        int nx0, ny0, nz0;
-        origin(next, nx0, ny0, nz0);
-        stage(0, nx0, ny0, nz0);
-      }
       tile = next;
       continue;
     }
@@ -1002,7 +1004,8 @@ static cudaError_t run_first(const float* in, const float* w, const float* b, ui
 // row, the im2col tile A[v][k] = x[v + tap k] (k = 9 dz + 3 dy + dx < 27, zero for
 // 27 <= k < 32) in BF16 from its input halo, and two K = 16 MMAs against the packed weights
 // B[co][k] give all C outputs in TMEM; the epilogue is the hidden layers'.  Tiles of 2 rows
-// x 2 planes, as k_conv3_tc<BF16>.  Layouts (no-swizzle K-major): element (row, k) of A at
+// x 2 planes, as k_conv3_tc<BF16> (tiles of 2 rows x 1 plane, four CTAs per SM by TMEM,
+// measured slower).  Layouts (no-swizzle K-major): element (row, k) of A at
 // (row / 8) * 512 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2, the same for B with co.
 constexpr int CF1_TY = 2, CF1_TZ = 2, CF1_MT = CF1_TY * CF1_TZ;
 constexpr int CF1_HY = CF1_TY + 2, CF1_HZ = CF1_TZ + 2;
