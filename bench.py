@@ -38,12 +38,12 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch set, measured by ncu
 # on the current kernels, keyed by (workload, part); parts without a capture report null.
 #  * cfg3 prior: one BF16 prior call (first layer, six hidden layers, the last with the tap
-#    sums, gather) captured at 256x256x64 (5.58 GB) and doubled: every kernel streams its
+#    sums, gather) captured at 256x256x64 (5.53 GB) and doubled: every kernel streams its
 #    volume once, so the traffic grows with the voxel count.
 #  * cfg3 agent: one band-limited iteration's passes, line search and prox/Mann pass
 #    captured at 256x256x128 with L = 4 looks (2.53 GB) and scaled to L = 32: all but the
 #    prox/Mann pass's 16 B per voxel (the prior agent's r, w and wbar) grows with the looks.
-TRAFFIC = {("cfg3", "prior"): 11.17e9, ("cfg3", "agent", "band-limited"): 19.3e9}
+TRAFFIC = {("cfg3", "prior"): 11.06e9, ("cfg3", "agent", "band-limited"): 19.3e9}
 
 def agent_bytes_per_iteration(sched: dict, nx: int, ny: int, nz: int, L: int) -> float:
     """Algorithmic DRAM bytes of one iteration's forward agents and fused prox/Mann pass:
