@@ -223,6 +223,18 @@ void clamp_denoiser_destroy(clamp_denoiser* den);
  * has no counterpart. */
 clamp_status clamp_selftest_bounded_wait(int32_t limit, int32_t* result);
 
+/* Bounds-checking build query.  The test variant of the library (built with
+ * CLAMP_BOUNDS_CHECK defined) tests every global-memory index of the hot-path kernels (the
+ * forward agents' band passes, pass C, the CNN prior's tensor-core convolutions and tap
+ * gather) against the extent of the buffer it addresses, skips an access that falls
+ * outside and records the first offending site code (101-199 band passes, 201-299 pass C,
+ * 301-399 CNN prior).  Writes that code, or 0 if none was recorded, to *site (host
+ * pointer) and clears the record if `reset` is non-zero.  Returns 1 for the checked
+ * build, 0 for the product build (*site is then always 0), or a negative clamp_status
+ * if reading the record failed.  Synchronous (reads device memory).  The paper has no
+ * counterpart. */
+int32_t clamp_bounds_check(int32_t reset, uint32_t* site);
+
 /* Tensor-core building block check: D[128][n] = A[128][k] B[n][k]^T with A, B BF16
  * (row-major, k contiguous) and D FP32, on one CTA through tcgen05 MMAs with TMEM
  * accumulators -- the same descriptor conventions the BF16 CNN prior uses.

@@ -3,6 +3,12 @@
 Each translation unit is compiled by nvcc in parallel, then linked into
 ``paper_2406_13651_gb300/_lib/libclamp.so``.  Rebuilds only when a source or
 header is newer than the library.
+
+``build(checked=True)`` makes the bounds-checking variant
+``_lib/libclamp_checked.so`` (``-DCLAMP_BOUNDS_CHECK=1``, its own object folder): the
+hot-path kernels test every global index against its buffer's extent, skip an access
+that falls outside and record the first offending site, which ``clamp_bounds_check``
+returns.  It is a test build, slower than the product one.
 """
 from __future__ import annotations
 
@@ -20,6 +26,7 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 BUILD_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libclamp.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "libclamp_checked.so")
 GENCODE = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -39,39 +46,45 @@ def _deps():
                                                                    os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(checked: bool = False) -> bool:
+    lib = LIB_CHECKED if checked else LIB
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
     """Compile and link; returns the library path.  Concurrent callers (one process per
     GPU) serialise on a lock file, so only the first one compiles."""
-    if not force and up_to_date():
-        return LIB
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(checked):
+        return lib
     os.makedirs(OUT_DIR, exist_ok=True)
     with open(os.path.join(OUT_DIR, ".build.lock"), "w") as lock:
         fcntl.flock(lock, fcntl.LOCK_EX)
         try:
-            if not force and up_to_date():   # another process finished the build meanwhile
-                return LIB
-            return _compile_and_link(verbose, extra_flags)
+            if not force and up_to_date(checked):   # another process finished the build meanwhile
+                return lib
+            return _compile_and_link(verbose, extra_flags, checked)
         finally:
             fcntl.flock(lock, fcntl.LOCK_UN)
 
 
-def _compile_and_link(verbose: bool, extra_flags) -> str:
+def _compile_and_link(verbose: bool, extra_flags, checked: bool = False) -> str:
     nvcc = _nvcc()
+    lib = LIB_CHECKED if checked else LIB
+    build_dir = BUILD_DIR + ("_checked" if checked else "")
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    os.makedirs(build_dir, exist_ok=True)
     common = [GENCODE, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-I" + os.path.join(ROOT, "include"), *extra_flags]
+    if checked:
+        common.append("-DCLAMP_BOUNDS_CHECK=1")
     objs = []
 
     def compile_one(src):
-        obj = os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(build_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc, *common, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
@@ -84,15 +97,15 @@ def _compile_and_link(verbose: bool, extra_flags) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, GENCODE, "-shared", "-cudart", "shared", "-o", tmp, *objs,
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -17,6 +17,9 @@ import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libclamp.so")
+# the bounds-checking test build (build.build(checked=True)); load() takes it when the
+# environment sets CLAMP_BOUNDS_CHECK=1
+LIB_CHECKED_PATH = os.path.join(_PKG, "_lib", "libclamp_checked.so")
 
 CLAMP_OK = 0
 STATUS = {0: "CLAMP_OK", 1: "CLAMP_EINVAL", 2: "CLAMP_ENOMEM", 3: "CLAMP_ECUDA", 4: "CLAMP_ENOTCONV",
@@ -46,6 +49,7 @@ EXPORTS = [
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
     "clamp_point_cloud_workspace_size", "clamp_point_cloud_metrics", "clamp_denoiser_create_unet",
     "clamp_selftest_bounded_wait", "clamp_prior_concurrent", "clamp_unet_set_tensor_cores", "clamp_unet_check",
+    "clamp_bounds_check",
 ]
 
 
@@ -80,11 +84,14 @@ class Report(ctypes.Structure):
 _lib = None
 
 
-def load(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Loads libclamp.so (raises if it is missing: build it with ``__graft_entry__.build()``)."""
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Loads libclamp.so (raises if it is missing: build it with ``__graft_entry__.build()``);
+    with CLAMP_BOUNDS_CHECK=1 in the environment, the bounds-checking libclamp_checked.so."""
     global _lib
     if _lib is not None:
         return _lib
+    if path is None:
+        path = LIB_CHECKED_PATH if os.environ.get("CLAMP_BOUNDS_CHECK") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"CLAMP CUDA library not built: {path} is missing "
                            "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
@@ -146,6 +153,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "clamp_point_cloud_workspace_size": (S, []),
         "clamp_denoiser_create_unet": (I, [P, ctypes.c_float, ctypes.POINTER(P)]),
         "clamp_selftest_bounded_wait": (I, [I, ctypes.POINTER(ctypes.c_int32)]),
+        "clamp_bounds_check": (I, [I, ctypes.POINTER(ctypes.c_uint32)]),
         "clamp_point_cloud_metrics": (I, [P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
@@ -278,6 +286,16 @@ def autotune(p: Params, y, pupil, window, ws=None, stream=None) -> list:
 def autotune_set(p: Params, variants) -> None:
     arr = (ctypes.c_int32 * 5)(*variants)
     _check(load().clamp_autotune_set(ctypes.byref(p), arr), "clamp_autotune_set")
+
+
+def bounds_check(reset: bool = True) -> tuple[bool, int]:
+    """(checked build?, first out-of-range site code recorded, 0 if none); clears the
+    record when ``reset``.  Only the bounds-checking build records anything."""
+    site = ctypes.c_uint32(0)
+    r = load().clamp_bounds_check(1 if reset else 0, ctypes.byref(site))
+    if r < 0:
+        _check(-r, "clamp_bounds_check")
+    return bool(r), int(site.value)
 
 
 def autotune_set_band(p: Params, row_variant: int) -> None:

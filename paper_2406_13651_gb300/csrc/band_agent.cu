@@ -124,6 +124,8 @@ __global__ void __launch_bounds__(1024) k_band_tables(const float* __restrict__ 
 
 template <int N>
 __global__ void __launch_bounds__(NT) k_band_z_inv(BandArgs a, const float2* __restrict__ tw) {
+  [[maybe_unused]] const long long nL = (long long)a.L * a.n, sL = (long long)a.L * a.nz * a.t.nSp,
+                                   bL = (long long)a.L * a.nz * a.ny * a.t.nbxp;   // buffer extents
   constexpr int LD = N + 1, CNT = BC * N, PER = (CNT + NT - 1) / NT;
   float2* sm = reinterpret_cast<float2*>(band_smem);
   const int s0 = blockIdx.x * BC, l = blockIdx.y;
@@ -140,10 +142,11 @@ __global__ void __launch_bounds__(NT) k_band_z_inv(BandArgs a, const float2* __r
       const long long ci = cbase + (long long)kz * a.t.nSp + col;
       const int s = s0 + col;
       const bool valid = s < a.t.nS;   // padding columns hold stale values: read as zero
-      mv[p] = valid ? a.Ms[ci] : make_float2(0.f, 0.f);
-      fv[p] = (valid && a.gamma_prev) ? a.Fd[ci] : make_float2(0.f, 0.f);
+      mv[p] = valid && CLAMP_IN_BOUNDS(ci, sL, 101) ? a.Ms[ci] : make_float2(0.f, 0.f);
+      fv[p] = (valid && a.gamma_prev && CLAMP_IN_BOUNDS(ci, sL, 102)) ? a.Fd[ci] : make_float2(0.f, 0.f);
       av[p] = __ldg(&a.t.s_pup[s]) * __ldg(&a.window[kz]);
-      yv[p] = a.y[ybase + (long long)kz * a.plane + __ldg(&a.t.s_kykx[s])];
+      const long long yi = ybase + (long long)kz * a.plane + __ldg(&a.t.s_kykx[s]);
+      yv[p] = CLAMP_IN_BOUNDS(yi, nL, 103) ? a.y[yi] : make_float2(0.f, 0.f);
     }
   }
   float acc[1] = {0.f};
@@ -156,7 +159,8 @@ __global__ void __launch_bounds__(NT) k_band_z_inv(BandArgs a, const float2* __r
       if (a.gamma_prev && s0 + col < a.t.nS) {   // the previous step's spectrum update M += gamma F d
         M.x = fmaf(gp, fv[p].x, M.x);
         M.y = fmaf(gp, fv[p].y, M.y);
-        a.Ms[cbase + (long long)kz * a.t.nSp + col] = M;
+        const long long mi = cbase + (long long)kz * a.t.nSp + col;
+        if (CLAMP_IN_BOUNDS(mi, sL, 104)) a.Ms[mi] = M;
       }
       const float f = av[p] * a.inv_nv;
       sm[col * LD + kz] = make_float2(f * fmaf(-av[p], M.x, yv[p].x), f * fmaf(-av[p], M.y, yv[p].y));
@@ -170,7 +174,8 @@ __global__ void __launch_bounds__(NT) k_band_z_inv(BandArgs a, const float2* __r
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
       const int col = e % BC, z = e / BC;
-      a.Fd[cbase + (long long)z * a.t.nSp + col] = cscale(sm[col * LD + z], a.sc_z);   // Gz, in place
+      const long long fi = cbase + (long long)z * a.t.nSp + col;
+      if (CLAMP_IN_BOUNDS(fi, sL, 105)) a.Fd[fi] = cscale(sm[col * LD + z], a.sc_z);   // Gz, in place
     }
   }
   double* const outs[1] = {a.s4};
@@ -182,6 +187,8 @@ __global__ void __launch_bounds__(NT) k_band_z_inv(BandArgs a, const float2* __r
 // INV: Gz on the support -> E on the band (zero off the support).  !INV: band -> support.
 template <int N, bool INV>
 __global__ void __launch_bounds__(NT) k_band_y(BandArgs a, const float2* __restrict__ tw) {
+  [[maybe_unused]] const long long nL = (long long)a.L * a.n, sL = (long long)a.L * a.nz * a.t.nSp,
+                                   bL = (long long)a.L * a.nz * a.ny * a.t.nbxp;   // buffer extents
   constexpr int LD = N + 1, CNT = BC * N, PER = (CNT + NT - 1) / NT;
   float2* sm = reinterpret_cast<float2*>(band_smem);
   const int b0 = blockIdx.x * BC, z = blockIdx.y, l = blockIdx.z;
@@ -195,9 +202,10 @@ __global__ void __launch_bounds__(NT) k_band_y(BandArgs a, const float2* __restr
       const int col = e % BC, yi = e / BC;
       if constexpr (INV) {
         const int s = __ldg(&a.t.sidx[yi * a.t.nbxp + b0 + col]);
-        iv[p] = s >= 0 ? a.Fd[cplane + s] : make_float2(0.f, 0.f);
+        iv[p] = s >= 0 && CLAMP_IN_BOUNDS(cplane + s, sL, 111) ? a.Fd[cplane + s] : make_float2(0.f, 0.f);
       } else {
-        iv[p] = a.band[bbase + (long long)yi * a.t.nbxp + col];
+        const long long bi = bbase + (long long)yi * a.t.nbxp + col;
+        iv[p] = CLAMP_IN_BOUNDS(bi, bL, 112) ? a.band[bi] : make_float2(0.f, 0.f);
       }
     }
   }
@@ -215,10 +223,11 @@ __global__ void __launch_bounds__(NT) k_band_y(BandArgs a, const float2* __restr
       const int col = e % BC, yi = e / BC;
       const float2 v = cscale(sm[col * LD + yi], a.sc_y);
       if constexpr (INV) {
-        a.band[bbase + (long long)yi * a.t.nbxp + col] = v;
+        const long long bi = bbase + (long long)yi * a.t.nbxp + col;
+        if (CLAMP_IN_BOUNDS(bi, bL, 113)) a.band[bi] = v;
       } else {
         const int s = __ldg(&a.t.sidx[yi * a.t.nbxp + b0 + col]);
-        if (s >= 0) a.Fd[cplane + s] = v;
+        if (s >= 0 && CLAMP_IN_BOUNDS(cplane + s, sL, 114)) a.Fd[cplane + s] = v;
       }
     }
   }
@@ -240,6 +249,8 @@ enum BandRowMode { BAND_GRAD = 0, BAND_SPEC = 1 };
 // transform, so three CTAs share an SM.
 template <int N, int MODE, int V>
 __global__ void __launch_bounds__(NT, V == 0 ? 2 : 3) k_band_x(BandArgs a, const float2* __restrict__ tw) {
+  [[maybe_unused]] const long long nL = (long long)a.L * a.n, sL = (long long)a.L * a.nz * a.t.nSp,
+                                   bL = (long long)a.L * a.nz * a.ny * a.t.nbxp;   // buffer extents
   constexpr int LX = V == 1 ? variant_rows(N, 2) : rows_per_cta(N), LD = N + 1, CNT = LX * N,
                 PER = (CNT + NT - 1) / NT;
   constexpr bool LATE = V == 2 && MODE == BAND_GRAD;   // mu, r' read after the inverse transform
@@ -263,12 +274,13 @@ __global__ void __launch_bounds__(NT, V == 0 ? 2 : 3) k_band_x(BandArgs a, const
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
     if (CNT % NT == 0 || e < CNT) {
-      if constexpr (!LATE) mv[p] = a.mu[e0 + e];
+      if constexpr (!LATE) mv[p] = CLAMP_IN_BOUNDS(e0 + e, nL, 121) ? a.mu[e0 + e] : make_float2(0.f, 0.f);
       if constexpr (MODE == BAND_GRAD) {
-        if constexpr (!LATE) rv[p] = a.rprev[e0 + e];
+        if constexpr (!LATE) rv[p] = CLAMP_IN_BOUNDS(e0 + e, nL, 122) ? a.rprev[e0 + e] : 1.0f;
         const int line = e / N, i = e - line * N;
         const int b = FIXED_COL ? b_fixed : __ldg(&a.t.bpos[i]);
-        ev[p] = b >= 0 ? a.band[(row0 + line) * a.t.nbxp + b] : make_float2(0.f, 0.f);
+        ev[p] = b >= 0 && CLAMP_IN_BOUNDS((row0 + line) * a.t.nbxp + b, bL, 123) ? a.band[(row0 + line) * a.t.nbxp + b]
+                                                                               : make_float2(0.f, 0.f);
       }
     }
   }
@@ -290,10 +302,11 @@ __global__ void __launch_bounds__(NT, V == 0 ? 2 : 3) k_band_x(BandArgs a, const
       if (CNT % NT == 0 || e < CNT) {
         const int line = e / N, i = e - line * N;
         const float2 ee = cscale(sm[line * LD + i], a.sc_x);
-        const float2 m = LATE ? a.mu[e0 + e] : mv[LATE ? 0 : p];
-        const float D = __frcp_rn((LATE ? a.rprev[e0 + e] : rv[LATE ? 0 : p]) + a.floor);
+        const bool ok = !LATE || CLAMP_IN_BOUNDS(e0 + e, nL, 124);
+        const float2 m = LATE ? (ok ? a.mu[e0 + e] : make_float2(0.f, 0.f)) : mv[LATE ? 0 : p];
+        const float D = __frcp_rn((LATE ? (ok ? a.rprev[e0 + e] : 1.0f) : rv[LATE ? 0 : p]) + a.floor);
         const float2 dv = make_float2(fmaf(-D, m.x, ee.x), fmaf(-D, m.y, ee.y));
-        a.d[e0 + e] = dv;
+        if (CLAMP_IN_BOUNDS(e0 + e, nL, 126)) a.d[e0 + e] = dv;
         const float d2 = cabs2(dv);
         acc[0] += d2;
         acc[1] += D * d2;
@@ -310,7 +323,8 @@ __global__ void __launch_bounds__(NT, V == 0 ? 2 : 3) k_band_x(BandArgs a, const
     float2* brow = a.band + (row0 + line) * nbxp;
     for (int b = threadIdx.x & 31; b < nbxp; b += 32) {
       const int kx = __ldg(&a.t.bx[b]);
-      brow[b] = kx >= 0 ? cscale(sm[line * LD + kx], a.sc_x) : make_float2(0.f, 0.f);
+      if (CLAMP_IN_BOUNDS((row0 + line) * nbxp + b, bL, 127))
+        brow[b] = kx >= 0 ? cscale(sm[line * LD + kx], a.sc_x) : make_float2(0.f, 0.f);
     }
   }
   if constexpr (MODE == BAND_GRAD) {
@@ -326,6 +340,8 @@ __global__ void __launch_bounds__(NT, V == 0 ? 2 : 3) k_band_x(BandArgs a, const
 // BAND_GRAD: F d on the support (in place) and S2 = ||a F d||^2.  BAND_SPEC: writes M.
 template <int N, int MODE>
 __global__ void __launch_bounds__(NT) k_band_z_fwd(BandArgs a, const float2* __restrict__ tw) {
+  [[maybe_unused]] const long long nL = (long long)a.L * a.n, sL = (long long)a.L * a.nz * a.t.nSp,
+                                   bL = (long long)a.L * a.nz * a.ny * a.t.nbxp;   // buffer extents
   constexpr int LD = N + 1, CNT = BC * N, PER = (CNT + NT - 1) / NT;
   float2* sm = reinterpret_cast<float2*>(band_smem);
   const int s0 = blockIdx.x * BC, l = blockIdx.y;
@@ -334,8 +350,10 @@ __global__ void __launch_bounds__(NT) k_band_z_fwd(BandArgs a, const float2* __r
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
     const int e = threadIdx.x + p * NT;
-    if (CNT % NT == 0 || e < CNT)
-      iv[p] = s0 + e % BC < a.t.nS ? a.Fd[cbase + (long long)(e / BC) * a.t.nSp + e % BC] : make_float2(0.f, 0.f);
+    if (CNT % NT == 0 || e < CNT) {
+      const long long fi = cbase + (long long)(e / BC) * a.t.nSp + e % BC;
+      iv[p] = s0 + e % BC < a.t.nS && CLAMP_IN_BOUNDS(fi, sL, 131) ? a.Fd[fi] : make_float2(0.f, 0.f);
+    }
   }
 #pragma unroll
   for (int p = 0; p < PER; ++p) {
@@ -353,11 +371,11 @@ __global__ void __launch_bounds__(NT) k_band_z_fwd(BandArgs a, const float2* __r
       const float2 v = cscale(sm[col * LD + kz], a.sc_z);
       const long long ci = cbase + (long long)kz * a.t.nSp + col;
       if constexpr (MODE == BAND_GRAD) {
-        a.Fd[ci] = v;
+        if (CLAMP_IN_BOUNDS(ci, sL, 132)) a.Fd[ci] = v;
         const float av = __ldg(&a.t.s_pup[s0 + col]) * __ldg(&a.window[kz]);
         acc[0] += av * av * cabs2(v);
       } else {
-        a.Ms[ci] = v;
+        if (CLAMP_IN_BOUNDS(ci, sL, 133)) a.Ms[ci] = v;
       }
     }
   }
@@ -547,7 +565,9 @@ cudaError_t launch_band_tables(const float* pupil, int nx, int ny, const BandTab
   return cudaGetLastError();
 }
 
-cudaError_t launch_band_spectrum(const BandArgs& a, int L, cudaStream_t st) {
+cudaError_t launch_band_spectrum(const BandArgs& a0, int L, cudaStream_t st) {
+  BandArgs a = a0;
+  a.L = L;
   BAND_TRY(run_x(a, L, BAND_SPEC, 0, st));
   BAND_TRY(run_y(a, L, false, st));
   return run_z(a, L, false, BAND_SPEC, st);
@@ -556,6 +576,7 @@ cudaError_t launch_band_spectrum(const BandArgs& a, int L, cudaStream_t st) {
 cudaError_t launch_band_agent(const BandArgs& a, int L, float nv, float* gamma, double* mures, int x_variant,
                               cudaStream_t st) {
   BandArgs b = a;
+  b.L = L;
   b.px = band_px(a.nx, a.ny, a.nz, x_variant);
   BAND_TRY(run_z(b, L, true, BAND_GRAD, st));
   BAND_TRY(run_y(b, L, true, st));
@@ -565,5 +586,7 @@ cudaError_t launch_band_agent(const BandArgs& a, int L, float nv, float* gamma, 
   k_band_gamma<<<L, NT, 0, st>>>(b, band_pS(BandShape{a.t.nS, a.t.nSp, a.t.nbx, a.t.nbxp}), nv, gamma, mures);
   return cudaGetLastError();
 }
+
+cudaError_t bounds_site_band(unsigned int* site, bool reset) { return bounds_site_local(site, reset); }
 
 }  // namespace clamp

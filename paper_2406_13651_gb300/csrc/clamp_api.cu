@@ -48,6 +48,22 @@ static clamp_status cuda_fail(cudaError_t e, const char* where) {
 extern "C" const char* clamp_last_error(void) { return g_err.c_str(); }
 extern "C" const char* clamp_version(void) { return "clamp-gb300 0.1 (sm_103a)"; }
 
+extern "C" int32_t clamp_bounds_check(int32_t reset, uint32_t* site) {
+  if (!site) return -(int32_t)api_fail(CLAMP_EINVAL, "clamp_bounds_check: null site");
+  // each translation unit keeps its own record: report the first non-zero one
+  unsigned int s[3] = {0u, 0u, 0u};
+  cudaError_t e = bounds_site_band(&s[0], reset != 0);
+  if (e == cudaSuccess) e = bounds_site_kernels(&s[1], reset != 0);
+  if (e == cudaSuccess) e = bounds_site_tc(&s[2], reset != 0);
+  if (e != cudaSuccess) return -(int32_t)cuda_fail(e, "clamp_bounds_check");
+  *site = s[0] ? s[0] : (s[1] ? s[1] : s[2]);
+#if defined(CLAMP_BOUNDS_CHECK)
+  return 1;
+#else
+  return 0;
+#endif
+}
+
 // ---------------------------------------------------------------- per-device set-up
 
 static std::mutex g_dev_mu;
@@ -443,6 +459,7 @@ static BandArgs band_args(const clamp_params* p, const Derived& d, const float* 
   a.s2 = at<double>(ws, al.s2);
   a.s3 = at<double>(ws, al.s3);
   a.s4 = at<double>(ws, al.s4);
+  a.L = p->looks;
   a.px = band_px(p->nx, p->ny, p->nz, 0);
   return a;
 }

@@ -804,6 +804,7 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
   const float4* __restrict__ MUi = reinterpret_cast<const float4*>(c.mu);
   float4* __restrict__ MUo = reinterpret_cast<float4*>(c.mu);
   const float4* __restrict__ Di = reinterpret_cast<const float4*>(c.d);
+  [[maybe_unused]] const long long look_ext = (long long)L * n2, row_ext = (long long)(L + 1) * n2;   // in pairs
   float acc[2] = {0.f, 0.f};
   for (long long vp = (long long)blockIdx.x * NT + threadIdx.x; vp < n2; vp += (long long)gridDim.x * NT) {
     CSum wb0, xb0, wb1, xb1;
@@ -829,7 +830,7 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
       r_n = r_a;
       m_n = m_a;
       d_n = d_a;
-      if (l + 2 < L) {
+      if (l + 2 < L && CLAMP_IN_BOUNDS(i + 2 * n2, look_ext, 201)) {
         w_a = Wi[i + 2 * n2];
         r_a = Ri[i + 2 * n2];
         m_a = MUi[i + 2 * n2];
@@ -849,13 +850,14 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
         const float gm = __ldg(&c.gamma[l]);
         m = make_float4(fmaf(gm, dd.x, m.x), fmaf(gm, dd.y, m.y), fmaf(gm, dd.z, m.z), fmaf(gm, dd.w, m.w));
       }
-      MUo[i] = m;
+      const bool in_look = CLAMP_IN_BOUNDS(i, look_ext, 202);
+      if (in_look) MUo[i] = m;
       const float c0 = c.nv * rp.x * __frcp_rn(fmaf(c.alpha, rp.x, c.nv));
       const float c1 = c.nv * rp.y * __frcp_rn(fmaf(c.alpha, rp.y, c.nv));
       const float K0 = c0 + fmaf(m.x, m.x, m.y * m.y), K1 = c1 + fmaf(m.z, m.z, m.w * m.w);
       const float2 rn = make_float2(prox_quad(wl.x, rp.x, K0, c.prox_var, c.inv_prox_var, c.beta, c.inv_beta),
                                     prox_quad(wl.y, rp.y, K1, c.prox_var, c.inv_prox_var, c.beta, c.inv_beta));
-      Ro[i] = rn;
+      if (in_look) Ro[i] = rn;
       kacc += K0 + K1;   // K covers mu: the prox's clip would hide a NaN there
       wb0.add(c.ups_look * wl.x);
       wb1.add(c.ups_look * wl.y);
@@ -878,14 +880,14 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
       const float2 rj = rj_n, wj = wj_n;
       rj_n = rj_a;
       wj_n = wj_a;
-      if (j + 2 <= L) {
+      if (j + 2 <= L && CLAMP_IN_BOUNDS(i + 2 * n2, row_ext, 203)) {
         rj_a = Ri[i + 2 * n2];
         wj_a = Wi[i + 2 * n2];
       }
       const float dv0 = rj.x - w0, dv1 = rj.y - w1;
       num = fmaf(dv0, dv0, fmaf(dv1, dv1, num));
       const float2 wn = make_float2(fmaf(2.0f * c.rho, x0 - rj.x, wj.x), fmaf(2.0f * c.rho, x1 - rj.y, wj.y));
-      Wo[i] = wn;
+      if (CLAMP_IN_BOUNDS(i, row_ext, 204)) Wo[i] = wn;
       const float ups = j < L ? c.ups_look : c.ups_prior;
       wn0.add(ups * wn.x);
       wn1.add(ups * wn.y);
@@ -1154,5 +1156,7 @@ cudaError_t launch_nonfinite_check(const float* x, long long count, int* err, cu
   k_nonfinite<<<152 * 4, NT, 0, st>>>(x, count, err);
   return cudaGetLastError();
 }
+
+cudaError_t bounds_site_kernels(unsigned int* site, bool reset) { return bounds_site_local(site, reset); }
 
 }  // namespace clamp

@@ -5,6 +5,40 @@
 
 namespace clamp {
 
+// ---- bounds-checking build
+// Compiled with -DCLAMP_BOUNDS_CHECK (a build of its own, libclamp_checked.so), the hot
+// kernels test each global index they compute against the extent of its buffer before the
+// access; an index outside skips the access and records its site code (the first one wins)
+// in a device word of the translation unit.  The default build compiles the tests away.
+#if defined(CLAMP_BOUNDS_CHECK)
+static __device__ unsigned int s_bounds_site;
+__device__ __forceinline__ bool clamp_in_bounds(long long i, long long n, unsigned int site) {
+  if (i >= 0 && i < n) return true;
+  atomicCAS(&s_bounds_site, 0u, site);
+  return false;
+}
+#define CLAMP_IN_BOUNDS(i, n, site) ::clamp::clamp_in_bounds((long long)(i), (long long)(n), (site))
+// Reads (and with reset clears) this translation unit's recorded site.
+static inline cudaError_t bounds_site_local(unsigned int* site, bool reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(site, s_bounds_site, sizeof(unsigned int));
+  if (e == cudaSuccess && reset) {
+    const unsigned int zero = 0;
+    e = cudaMemcpyToSymbol(s_bounds_site, &zero, sizeof(unsigned int));
+  }
+  return e;
+}
+#else
+#define CLAMP_IN_BOUNDS(i, n, site) true
+static inline cudaError_t bounds_site_local(unsigned int* site, bool) {
+  *site = 0;
+  return cudaSuccess;
+}
+#endif
+// Per translation unit (band passes, set-up and prox/Mann passes, tensor-core convs).
+cudaError_t bounds_site_band(unsigned int* site, bool reset);
+cudaError_t bounds_site_kernels(unsigned int* site, bool reset);
+cudaError_t bounds_site_tc(unsigned int* site, bool reset);
+
 constexpr int NT = 256;   // threads per CTA in every FFT pass
 constexpr int LC = 16;    // adjacent x-columns per CTA in the y / z passes
 
@@ -76,7 +110,7 @@ struct BandTables {
 };
 struct BandArgs {
   BandTables t;
-  int nx, ny, nz;
+  int nx, ny, nz, L;          // L: looks (the launchers set it)
   long long n, plane;         // nx ny nz, nx ny
   const float2* y;            // [L][n] data (full spectrum layout)
   const float* window;        // [nz]

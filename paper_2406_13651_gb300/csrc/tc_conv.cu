@@ -169,6 +169,10 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long plane = (long long)nx * ny, n = plane * nz;
   const int tiles_x = nx / TCX, tiles_y = ny / TY, ntiles = tiles_x * tiles_y * (nz / Cfg::TZ);
+  // extents of the global buffers (16-byte vectors) that the bounds-checking build tests
+  [[maybe_unused]] const long long in_ext = (long long)(CIN / Kd::EPV) * n,
+                                   out_ext = (long long)(NPAD / Kd::EPV) * n,
+                                   w_ext = (long long)Kd::SPLIT * Cfg::CHUNKS * Cfg::W_VEC;
 
   if (tid == 0) {
     tc::mbar_init(mbar, 1);
@@ -214,11 +218,14 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
           if constexpr (Cfg::MERGE) {   // packed [dx][cg][dy blk][n] of this dz -> [dx][cg][dz blk][dy blk][n]
             for (int e = tid; e < WDZ; e += TC_NT) {
               const int nn = e % NPAD, t = e / NPAD, dyb = t % 3, dxc = t / 3;   // dxc = 2 dx + cg
-              cp_async16(&s_w[(dxc * 9 + (2 - hz) * 3 + dyb) * NPAD + nn], &wsrc[e], true);
+              cp_async16(&s_w[(dxc * 9 + (2 - hz) * 3 + dyb) * NPAD + nn], &wsrc[e],
+                         CLAMP_IN_BOUNDS(wsrc + e - wpk, w_ext, 301) &&
+                             CLAMP_IN_BOUNDS((dxc * 9 + (2 - hz) * 3 + dyb) * NPAD + nn, Cfg::W_VEC, 302));
             }
           } else {
             uint4* wdst = s_w + sp * Cfg::W_VEC + hz * WDZ;
-            for (int e = tid; e < WDZ; e += TC_NT) cp_async16(&wdst[e], &wsrc[e], true);
+            for (int e = tid; e < WDZ; e += TC_NT)
+              cp_async16(&wdst[e], &wsrc[e], CLAMP_IN_BOUNDS(wsrc + e - wpk, w_ext, 301));
           }
         }
       }
@@ -232,7 +239,7 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
         for (int xr = lane; xr < TC_HX; xr += 32) {
           const int gx = x0 + xr - 1;
           const bool inb = rin && gx >= 0 && gx < nx;
-          cp_async16(&drow[xr], inb ? &in[rbase + gx] : in, inb);
+          cp_async16(&drow[xr], inb ? &in[rbase + gx] : in, inb && CLAMP_IN_BOUNDS(rbase + gx, in_ext, 303));
         }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
@@ -427,7 +434,8 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
           tc::tmem_ld_x8(trow + (uint32_t)col, t);
 #pragma unroll
           for (int i = 0; i < 8; ++i)
-            if (col + i < 27) P[(long long)(col + i) * n + vox] = t[i];
+            if (col + i < 27 && CLAMP_IN_BOUNDS((long long)(col + i) * n + vox, 27 * n, 304))
+              P[(long long)(col + i) * n + vox] = t[i];
         }
       }
       // TMEM reads complete before the next tile's first MMA overwrites them
@@ -449,7 +457,7 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
       const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
       const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + acc_col(mt);
       if constexpr (LAST) {   // one output channel (column 0): FP32 plus the residual input
-        if (h == 0) {
+        if (h == 0 && CLAMP_IN_BOUNDS(vox, n, 305)) {
           float v[8];
           tc::tmem_ld_x8(trow, v);
           out_f32[vox] = v[0] + __ldg(&bias[0]) + resid[vox];
@@ -470,11 +478,14 @@ __global__ void __launch_bounds__(TC_NT, TcKind<KIND>::MIN_CTAS)
           o.y = pack_bf16x2(v[2], v[3]);
           o.z = pack_bf16x2(v[4], v[5]);
           o.w = pack_bf16x2(v[6], v[7]);
-          out_act[(long long)(col / 8) * n + vox] = o;
+          if (CLAMP_IN_BOUNDS((long long)(col / 8) * n + vox, out_ext, 306)) out_act[(long long)(col / 8) * n + vox] = o;
         } else {
           float4* o4 = reinterpret_cast<float4*>(out_act);
-          o4[(long long)(col / 4) * n + vox] = make_float4(v[0], v[1], v[2], v[3]);
-          o4[(long long)(col / 4 + 1) * n + vox] = make_float4(v[4], v[5], v[6], v[7]);
+          if (CLAMP_IN_BOUNDS((long long)(col / 4 + 1) * n + vox, out_ext, 306) &&
+              CLAMP_IN_BOUNDS((long long)(col / 4) * n + vox, out_ext, 306)) {
+            o4[(long long)(col / 4) * n + vox] = make_float4(v[0], v[1], v[2], v[3]);
+            o4[(long long)(col / 4 + 1) * n + vox] = make_float4(v[4], v[5], v[6], v[7]);
+          }
         }
       }
     }
@@ -578,7 +589,8 @@ __global__ void __launch_bounds__(TC_NT, TcPlaneCfg<CIN, NPAD>::CTAS)
         const int gx = x0 + xr - 1, gy = y0 + yr - 1;
         const bool inb = zin && gx >= 0 && gx < nx && gy >= 0 && gy < ny;
         float4 f = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (inb) f = __ldg(&in4[(long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx + gx]);
+        const long long ii = (long long)(2 * c + cg) * n + (long long)gz * plane + (long long)gy * nx + gx;
+        if (inb && CLAMP_IN_BOUNDS(ii, (long long)(CIN / 4) * n, 341)) f = __ldg(&in4[ii]);
         const float4 h = make_float4(tf32_rn(f.x), tf32_rn(f.y), tf32_rn(f.z), tf32_rn(f.w));
         hi[e] = h;
         lo[e] = make_float4(tf32_rn(f.x - h.x), tf32_rn(f.y - h.y), tf32_rn(f.z - h.z), tf32_rn(f.w - h.w));
@@ -644,8 +656,11 @@ __global__ void __launch_bounds__(TC_NT, TcPlaneCfg<CIN, NPAD>::CTAS)
         tc::tmem_ld_x8(trow + (uint32_t)col, v);
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
-        o4[(long long)(col / 4) * n + vox] = make_float4(v[0], v[1], v[2], v[3]);
-        o4[(long long)(col / 4 + 1) * n + vox] = make_float4(v[4], v[5], v[6], v[7]);
+        if (CLAMP_IN_BOUNDS((long long)(col / 4 + 1) * n + vox, (long long)(NPAD / 4) * n, 342) &&
+            CLAMP_IN_BOUNDS((long long)(col / 4) * n + vox, (long long)(NPAD / 4) * n, 342)) {
+          o4[(long long)(col / 4) * n + vox] = make_float4(v[0], v[1], v[2], v[3]);
+          o4[(long long)(col / 4 + 1) * n + vox] = make_float4(v[4], v[5], v[6], v[7]);
+        }
       }
     }
   } else if (tid == 0) {
@@ -1044,7 +1059,9 @@ __global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict
     const float* src = in + (long long)gz * plane + (long long)gy * nx;
     for (int xr = lane; xr < TC_HX; xr += 32) {
       const int gx = x0 + xr - 1;
-      const float v = rin && gx >= 0 && gx < nx ? __ldg(&src[gx]) : 0.f;
+      const bool inb = rin && gx >= 0 && gx < nx &&
+                       CLAMP_IN_BOUNDS((long long)gz * plane + (long long)gy * nx + gx, n, 311);
+      const float v = inb ? __ldg(&src[gx]) : 0.f;
       s_x[r * TC_HX + xr] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
     }
   }
@@ -1110,7 +1127,8 @@ __global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict
         o.y = pack_bf16x2(v[2], v[3]);
         o.z = pack_bf16x2(v[4], v[5]);
         o.w = pack_bf16x2(v[6], v[7]);
-        out[(long long)(col / 8) * n + vox] = o;
+        if (CLAMP_IN_BOUNDS((long long)(col / 8) * n + vox, (long long)(C / 8) * n, 312))
+          out[(long long)(col / 8) * n + vox] = o;
       }
     }
   } else if (tid == 0) {
@@ -1172,7 +1190,8 @@ __global__ void __launch_bounds__(TC_NT) k_last_taps_tc(const uint4* __restrict_
   }
   for (int e = tid; e < CL2_MT * G * 128; e += TC_NT) {
     const int vv = e % 128, g = (e / 128) % G, mt = e / (128 * G);
-    cp_async16(&s_a[e], &act[(long long)g * n + v0 + mt * 128 + vv], true);
+    cp_async16(&s_a[e], &act[(long long)g * n + v0 + mt * 128 + vv],
+               CLAMP_IN_BOUNDS((long long)g * n + v0 + mt * 128 + vv, (long long)G * n, 321));
   }
   for (int e = tid; e < G * 32; e += TC_NT) cp_async16(&s_w[e], &wpk[e], true);
   cp_async_wait_all();
@@ -1208,7 +1227,8 @@ __global__ void __launch_bounds__(TC_NT) k_last_taps_tc(const uint4* __restrict_
         tc::tmem_ld_x8(trow + (uint32_t)col, t);
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-          if (col + i < 27) P[(long long)(col + i) * n + v] = t[i];
+          if (col + i < 27 && CLAMP_IN_BOUNDS((long long)(col + i) * n + v, 27 * n, 322))
+            P[(long long)(col + i) * n + v] = t[i];
       }
     }
   } else if (tid == 0) {
@@ -1242,7 +1262,8 @@ __global__ void __launch_bounds__(NT) k_last_gather(const float* __restrict__ P,
         const int xx = x + dx - 1;
         if (xx < 0 || xx >= nx) continue;
         const int tap = 9 * dz + 3 * dy + dx;
-        acc += __ldg(&P[(long long)tap * n + (long long)zz * plane + (long long)yy * nx + xx]);
+        const long long pi = (long long)tap * n + (long long)zz * plane + (long long)yy * nx + xx;
+        if (CLAMP_IN_BOUNDS(pi, 27 * n, 331)) acc += __ldg(&P[pi]);
       }
     }
   }
@@ -1396,6 +1417,8 @@ std::vector<uint8_t> pack_tc_weights(const float* W, int cin, int cout, int npad
           }
   return p;
 }
+
+cudaError_t bounds_site_tc(unsigned int* site, bool reset) { return bounds_site_local(site, reset); }
 
 }  // namespace clamp
 
