@@ -45,6 +45,44 @@ FP32_LANES_PER_SM = 128
 #    prox/Mann pass's 16 B per voxel (the prior agent's r, w and wbar) grows with the looks.
 TRAFFIC = {("cfg3", "prior"): 11.06e9, ("cfg3", "agent", "band-limited"): 19.3e9}
 
+def measure_tf32_tflops(dev, seconds: float = 2.0, size: int = 8192) -> dict:
+    """TF32 tensor-core rate on this GPU: a cuBLAS FP32 GEMM with TF32 math allowed, the best
+    of 5 single calls (burst) and back to back for ``seconds`` (sustained), 2 size^3 FLOP
+    each.  It is the denominator of the TF32x3 prior's roofline, taken after the timed
+    region."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        g = torch.Generator(device=dev).manual_seed(0)
+        a = torch.randn(size, size, device=dev, generator=g)
+        b = torch.randn(size, size, device=dev, generator=g)
+        c = torch.empty(size, size, device=dev)
+        flop = 2.0 * size ** 3
+        for _ in range(3):
+            torch.matmul(a, b, out=c)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        best = float("inf")
+        for _ in range(5):
+            e0.record()
+            torch.matmul(a, b, out=c)
+            e1.record()
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1) / 1e3)
+        reps = max(1, int(seconds / best))
+        e0.record()
+        for _ in range(reps):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        sustained = flop * reps / (e0.elapsed_time(e1) / 1e3) / 1e12
+        del a, b, c
+        return {"burst": flop / best / 1e12, "sustained": sustained}
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def agent_bytes_per_iteration(sched: dict, nx: int, ny: int, nz: int, L: int) -> float:
     """Algorithmic DRAM bytes of one iteration's forward agents and fused prox/Mann pass:
     what each kernel must read and write by its definition, for the schedule that ran.
@@ -636,11 +674,13 @@ def main():
                         "peak_source": "measured bf16_tflops_sustained",
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
         elif tensor_path:
-            tf32x3_peak = bf16_peak * (1.1 / 2.25) / 3.0
+            tf32 = measure_tf32_tflops(dev)
+            tf32x3_peak = tf32["sustained"] / 3.0
             roofline = {"bound": "tensor", "kernel": "k_conv3_tc_plane<TF32x3> (+ SIMT first and last layers): the prior agent",
                         "achieved": cnn_tflops, "peak": tf32x3_peak, "unit": "TFLOP/s",
                         "frac": cnn_tflops / tf32x3_peak, "traffic": TRAFFIC.get((wl.name, "prior")),
-                        "peak_source": "measured bf16_tflops_sustained x nominal TF32/BF16 ratio (1.1/2.25), "
+                        "peak_source": "measured in this run: cuBLAS TF32 GEMM 8192^3 back to back "
+                                       f"({tf32['sustained']:.0f} TFLOP/s sustained, {tf32['burst']:.0f} burst), "
                                        "/3 for the three TF32 MMAs per FP32 product",
                         "algorithmic": f"{macs} MAC/voxel x {n} voxels per prior-agent call"}
         else:

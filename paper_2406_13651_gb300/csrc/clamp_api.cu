@@ -248,19 +248,32 @@ clamp_status recon_prepare(const clamp_params* p, const float* pupil, const floa
   API_CUDA(cudaMemcpyAsync(hp.data(), pupil, hp.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "pupil read");
   API_CUDA(cudaMemcpyAsync(hw.data(), window, hw.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "window read");
   API_CUDA(cudaStreamSynchronize(st), "pupil read");
+  return recon_prepare_host(p, hp.data(), hw.data(), d);
+}
+
+// The same from host copies of the pupil and window (no device access, no synchronisation).
+clamp_status recon_prepare_host(const clamp_params* p, const float* hp, const float* hw, ReconPlan* d) {
+  d->g.nx = p->nx;
+  d->g.ny = p->ny;
+  d->g.nz = p->nz;
+  d->g.L = p->looks;
+  d->g.n = (long long)p->nx * p->ny * p->nz;
+  d->band = BandShape{};
+  d->band_fits = false;
+  const size_t np = (size_t)p->nx * p->ny;
   double sp = 0, sw = 0;
-  for (float v : hp) {
-    if (!isfinite(v)) return api_fail(CLAMP_EINVAL, "pupil has a non-finite value");
-    sp += (double)v * v;
+  for (size_t i = 0; i < np; ++i) {
+    if (!isfinite(hp[i])) return api_fail(CLAMP_EINVAL, "pupil has a non-finite value");
+    sp += (double)hp[i] * hp[i];
   }
-  for (float v : hw) {
-    if (!isfinite(v)) return api_fail(CLAMP_EINVAL, "window has a non-finite value");
-    sw += (double)v * v;
+  for (int i = 0; i < p->nz; ++i) {
+    if (!isfinite(hw[i])) return api_fail(CLAMP_EINVAL, "window has a non-finite value");
+    sw += (double)hw[i] * hw[i];
   }
-  const double alpha = (sp / hp.size()) * (sw / hw.size());
+  const double alpha = (sp / np) * (sw / p->nz);
   if (!(alpha > 0)) return api_fail(CLAMP_EINVAL, "aperture is identically zero (alpha = 0)");
   d->alpha = alpha;
-  d->band = band_shape(hp.data(), p->nx, p->ny);
+  d->band = band_shape(hp, p->nx, p->ny);
   d->band_fits = band_fits(p, d->band);
   d->s.nv = p->noise_var;
   d->s.alpha = (float)alpha;
@@ -898,9 +911,12 @@ extern "C" clamp_status clamp_iterate(const clamp_params* p, int32_t k_first, in
                       mu_out, ws, events, false, st);
 }
 
+// `plan`: the aperture statistics when the caller already has them (host inputs), else NULL
+// (read from the device pupil and window, one synchronisation).
 static clamp_status reconstruct_impl(const clamp_params* p, const float* y, const float* pupil, const float* window,
                                      const clamp_denoiser* den, const float* r_init, float* r_out,
-                                     clamp_report* report, void* ws, cudaStream_t st) {
+                                     clamp_report* report, void* ws, cudaStream_t st,
+                                     const ReconPlan* plan = nullptr) {
   const ReconLayout rl = recon_layout(p, den);
   const AgentLayout al = agent_layout(p);
   void* aws = static_cast<char*>(ws) + rl.agent;
@@ -911,7 +927,8 @@ static clamp_status reconstruct_impl(const clamp_params* p, const float* y, cons
   double* mu_ring = at<double>(ws, rl.mu_ring);
   const long long n = (long long)p->nx * p->ny * p->nz;
   Derived d;
-  API_TRY(recon_prepare(p, pupil, window, st, &d));
+  if (plan) d = *plan;
+  else API_TRY(recon_prepare(p, pupil, window, st, &d));
   API_CUDA(cudaMemsetAsync(at<int>(aws, al.err), 0, sizeof(int), st), "memset");
   API_TRY(do_init_warm(p, d, y, pupil, window, r_init, mu, r, w, al, aws, st));
   if (p->max_iters == 0) {
@@ -1057,6 +1074,10 @@ extern "C" clamp_status clamp_reconstruct_host(const clamp_params* p, const floa
     API_CUDA(cudaMalloc(&hc->buf, need), "device cache allocation");
     hc->bytes = need;
   }
+  // the aperture statistics come from the host copies: the call synchronises only at its end
+  ReconPlan plan;
+  if (p->flags & CLAMP_FLAG_NO_APERTURE) API_TRY(recon_prepare(p, nullptr, nullptr, st, &plan));
+  else API_TRY(recon_prepare_host(p, pupil_host, window_host, &plan));
   char* b = static_cast<char*>(hc->buf);
   API_CUDA(cudaMemcpyAsync(b + o_y, y_host, L * n * sizeof(float2), cudaMemcpyHostToDevice, st), "y upload");
   API_CUDA(cudaMemcpyAsync(b + o_p, pupil_host, (size_t)p->nx * p->ny * sizeof(float), cudaMemcpyHostToDevice, st),
@@ -1067,7 +1088,7 @@ extern "C" clamp_status clamp_reconstruct_host(const clamp_params* p, const floa
   clamp_status s = reconstruct_impl(p, reinterpret_cast<float*>(b + o_y), reinterpret_cast<float*>(b + o_p),
                                     reinterpret_cast<float*>(b + o_w), den,
                                     r_init_host ? reinterpret_cast<float*>(b + o_ri) : nullptr,
-                                    reinterpret_cast<float*>(b + o_ro), report, b + o_ws, st);
+                                    reinterpret_cast<float*>(b + o_ro), report, b + o_ws, st, &plan);
   if (s != CLAMP_OK) return s;
   API_CUDA(cudaMemcpyAsync(r_out_host, b + o_ro, n * sizeof(float), cudaMemcpyDeviceToHost, st), "r_out download");
   API_CUDA(cudaStreamSynchronize(st), "sync");

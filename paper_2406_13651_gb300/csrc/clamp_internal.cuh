@@ -22,6 +22,8 @@ struct ReconPlan {
 // Reads the aperture back to compute alpha (synchronises `st`): call before any capture.
 clamp_status recon_prepare(const clamp_params* p, const float* pupil, const float* window, cudaStream_t st,
                            ReconPlan* out);
+clamp_status recon_prepare_host(const clamp_params* p, const float* pupil_host, const float* window_host,
+                                ReconPlan* d);
 // Enqueues the Alg. 2 initialisation and p->max_iters iterations on `st` without any host
 // synchronisation; ws is laid out as for clamp_reconstruct.
 clamp_status recon_enqueue(const clamp_params* p, const ReconPlan& plan, const float* y, const float* pupil,
