@@ -49,7 +49,7 @@ EXPORTS = [
     "clamp_speckle_average", "clamp_unet_normalize", "clamp_unet_warm_start", "clamp_unet_loss",
     "clamp_point_cloud_workspace_size", "clamp_point_cloud_metrics", "clamp_denoiser_create_unet",
     "clamp_selftest_bounded_wait", "clamp_prior_concurrent", "clamp_unet_set_tensor_cores", "clamp_unet_check",
-    "clamp_bounds_check",
+    "clamp_bounds_check", "clamp_host_alloc", "clamp_host_free",
 ]
 
 
@@ -154,6 +154,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "clamp_denoiser_create_unet": (I, [P, ctypes.c_float, ctypes.POINTER(P)]),
         "clamp_selftest_bounded_wait": (I, [I, ctypes.POINTER(ctypes.c_int32)]),
         "clamp_bounds_check": (I, [I, ctypes.POINTER(ctypes.c_uint32)]),
+        "clamp_host_alloc": (I, [S, ctypes.POINTER(P)]),
+        "clamp_host_free": (V, [P]),
         "clamp_point_cloud_metrics": (I, [P, P, I, I, I, ctypes.c_float, ctypes.c_float, P, P, S, P]),
     }
     for name, (res, args) in sig.items():
@@ -286,6 +288,35 @@ def autotune(p: Params, y, pupil, window, ws=None, stream=None) -> list:
 def autotune_set(p: Params, variants) -> None:
     arr = (ctypes.c_int32 * 5)(*variants)
     _check(load().clamp_autotune_set(ctypes.byref(p), arr), "clamp_autotune_set")
+
+
+class _HostBlock:
+    """Owns one clamp_host_alloc block; freed when the last tensor viewing it goes away."""
+
+    def __init__(self, nbytes: int):
+        ptr = ctypes.c_void_p()
+        _check(load().clamp_host_alloc(nbytes, ctypes.byref(ptr)), "clamp_host_alloc")
+        self.ptr = ptr.value
+        self.nbytes = nbytes
+
+    def __del__(self):
+        if getattr(self, "ptr", None) and _lib is not None:
+            _lib.clamp_host_free(self.ptr)
+            self.ptr = None
+
+
+def host_empty(shape, dtype):
+    """A CPU torch tensor in huge-page, page-locked host memory from clamp_host_alloc (zeroed):
+    the staging buffers for clamp_reconstruct_host."""
+    import torch
+    n = 1
+    for d in shape:
+        n *= int(d)
+    esize = torch.empty((), dtype=dtype).element_size()
+    blk = _HostBlock(max(n * esize, 1))
+    arr = (ctypes.c_char * blk.nbytes).from_address(blk.ptr)
+    arr._owner = blk   # the array (held by the tensor) keeps the block alive
+    return torch.frombuffer(arr, dtype=dtype, count=n).view(tuple(int(d) for d in shape))
 
 
 def bounds_check(reset: bool = True) -> tuple[bool, int]:

@@ -6,6 +6,8 @@
 #include "denoise.cuh"
 
 #include <math.h>
+#include <sys/mman.h>
+#include <unistd.h>
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
@@ -1093,4 +1095,58 @@ extern "C" clamp_status clamp_reconstruct_host(const clamp_params* p, const floa
   API_CUDA(cudaMemcpyAsync(r_out_host, b + o_ro, n * sizeof(float), cudaMemcpyDeviceToHost, st), "r_out download");
   API_CUDA(cudaStreamSynchronize(st), "sync");
   return CLAMP_OK;
+}
+
+// ---------------------------------------------------------------- huge-page host staging memory
+
+namespace {
+std::mutex g_host_mu;
+std::map<void*, std::pair<void*, size_t>> g_host_allocs;   // user pointer -> (mapping, mapping length)
+
+size_t huge_page_bytes() {
+  size_t hp = 2u << 20;   // the usual PMD size with 4 KB base pages
+  if (FILE* f = fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+    unsigned long long v = 0;
+    if (fscanf(f, "%llu", &v) == 1 && v >= 4096 && (v & (v - 1)) == 0) hp = (size_t)v;
+    fclose(f);
+  }
+  return hp;
+}
+}  // namespace
+
+extern "C" clamp_status clamp_host_alloc(size_t bytes, void** out) {
+  if (!out || bytes == 0) return api_fail(CLAMP_EINVAL, "clamp_host_alloc: bytes must be > 0 and out non-NULL");
+  *out = nullptr;
+  const size_t page = (size_t)sysconf(_SC_PAGESIZE);
+  const size_t hp = huge_page_bytes();
+  const size_t len = (bytes + page - 1) / page * page;
+  const size_t map_len = len + hp;   // slack to start the block on a huge-page boundary
+  void* raw = mmap(nullptr, map_len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+  if (raw == MAP_FAILED) return api_fail(CLAMP_ENOMEM, "clamp_host_alloc: mmap of %zu bytes failed", map_len);
+  char* p = reinterpret_cast<char*>(((uintptr_t)raw + hp - 1) / hp * hp);
+  madvise(p, len, MADV_HUGEPAGE);   // advisory: base pages remain if the kernel declines
+  for (size_t o = 0; o < len; o += 4096) p[o] = 0;   // populate before registering
+  const cudaError_t e = cudaHostRegister(p, len, cudaHostRegisterDefault);
+  if (e != cudaSuccess) {
+    munmap(raw, map_len);
+    return cuda_fail(e, "clamp_host_alloc: cudaHostRegister");
+  }
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  g_host_allocs[p] = {raw, map_len};
+  *out = p;
+  return CLAMP_OK;
+}
+
+extern "C" void clamp_host_free(void* p) {
+  if (!p) return;
+  std::pair<void*, size_t> m;
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    auto it = g_host_allocs.find(p);
+    if (it == g_host_allocs.end()) return;
+    m = it->second;
+    g_host_allocs.erase(it);
+  }
+  cudaHostUnregister(p);
+  munmap(m.first, m.second);
 }

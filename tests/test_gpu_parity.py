@@ -4,6 +4,7 @@ inputs (fp32-rounded inputs are given to both sides).
 Tolerances: the FP32 FFT/MM path must match the oracle within relative L2
 error 1e-4 on reflectance (the FP32 target); single FFTs within 1e-5.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -315,6 +316,34 @@ def test_reconstruct_host_matches_device(C):
     np.testing.assert_array_equal(hres.r, dres.r.cpu().numpy())
     hres2 = C.reconstruct_host(p, y32, wl.pupil, wl.window, den)   # cached device buffers reused
     np.testing.assert_array_equal(hres2.r, hres.r)
+
+
+def test_reconstruct_host_from_huge_page_buffers(C):
+    """Staging buffers from clamp_host_alloc (huge pages, page-locked) give the same result as
+    pageable numpy arrays; the blocks are zeroed, huge-page aligned, and freed with their tensors."""
+    import gc
+    wl, a, y32, y64 = problem("cfg1", seed=3, iters=6)
+    p = params(C, wl, max_iters=6)
+    den = C.Denoiser.gauss(0.8)
+    ref = C.reconstruct_host(p, y32, wl.pupil, wl.window, den)
+    yh = C.host_empty(y32.shape, torch.complex64)
+    assert not yh.any() and yh.data_ptr() % (2 << 20) == 0
+    yh.copy_(torch.from_numpy(y32))
+    ph = C.host_empty(wl.pupil.shape, torch.float32)
+    ph.copy_(torch.from_numpy(wl.pupil))
+    wh = C.host_empty(wl.window.shape, torch.float32)
+    wh.copy_(torch.from_numpy(wl.window))
+    rh = C.host_empty((wl.nz, wl.ny, wl.nx), torch.float32)
+    res = C.reconstruct_host(p, yh.numpy(), ph.numpy(), wh.numpy(), den, r_out=rh.numpy())
+    np.testing.assert_array_equal(rh.numpy(), ref.r)
+    np.testing.assert_array_equal(res.r, ref.r)
+    del yh, ph, wh, rh, res
+    gc.collect()
+    lib = C.load()
+    lib.clamp_host_free(None)                     # ignored
+    lib.clamp_host_free(ctypes.c_void_p(4096))    # not from the allocator: ignored
+    out = ctypes.c_void_p()
+    assert lib.clamp_host_alloc(0, ctypes.byref(out)) == 1   # CLAMP_EINVAL
 
 
 def test_reconstruct_cnn_prior_matches_oracle(C):
