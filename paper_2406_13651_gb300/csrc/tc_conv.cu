@@ -133,6 +133,12 @@ __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, boo
                "r"(valid ? 16 : 0)
                : "memory");
 }
+// 4-byte variant (cp.async.ca): for rows whose start is not 16-byte aligned.
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(tc::smem_addr(smem_dst)), "l"(gsrc),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
@@ -1022,11 +1028,17 @@ static cudaError_t run_first(const float* in, const float* w, const float* b, ui
 // x 2 planes, as k_conv3_tc<BF16> (tiles of 2 rows x 1 plane, four CTAs per SM by TMEM,
 // measured slower).  Layouts (no-swizzle K-major): element (row, k) of A at
 // (row / 8) * 512 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2, the same for B with co.
+//
+// Persistent: TMEM (256 columns at 48 channels) admits two CTAs per SM, so each CTA takes
+// its TMEM and weights once and walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...;
+// the next tile's FP32 halo is copied (cp.async, 4-byte elements: the halo row starts at
+// x0 - 1) into a raw buffer while the current tile's im2col, MMAs and epilogue run.
 constexpr int CF1_TY = 2, CF1_TZ = 2, CF1_MT = CF1_TY * CF1_TZ;
-constexpr int CF1_HY = CF1_TY + 2, CF1_HZ = CF1_TZ + 2;
+constexpr int CF1_HY = CF1_TY + 2, CF1_HZ = CF1_TZ + 2, CF1_HROWS = CF1_HY * CF1_HZ;
 constexpr int CF1_A_BYTES = 128 * 64;                               // one im2col tile (K = 32)
 __host__ __device__ constexpr size_t cf1_smem(int C) {
-  return 1024 + (size_t)CF1_MT * CF1_A_BYTES + (size_t)C * 64 + 2 * CF1_HZ * CF1_HY * TC_HX + 64;
+  // im2col tiles, weights, BF16 halo, FP32 raw halo, mbarrier + TMEM slot + abort flag
+  return 1024 + (size_t)CF1_MT * CF1_A_BYTES + (size_t)C * 64 + 2 * CF1_HROWS * TC_HX + 4 * CF1_HROWS * TC_HX + 64;
 }
 
 template <int C>
@@ -1040,74 +1052,109 @@ __global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict
   unsigned char* s_a = base;                                            // [MT][8 KB]
   uint4* s_w = reinterpret_cast<uint4*>(s_a + CF1_MT * CF1_A_BYTES);    // C * 64 bytes
   uint16_t* s_x = reinterpret_cast<uint16_t*>(reinterpret_cast<unsigned char*>(s_w) + C * 64);  // [HZ][HY][HX]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_x + CF1_HZ * CF1_HY * TC_HX + 8);
+  float* s_raw = reinterpret_cast<float*>(s_x + CF1_HROWS * TC_HX);     // [HZ][HY][HX], FP32
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(s_raw + CF1_HROWS * TC_HX);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+  int* abort_flag = reinterpret_cast<int*>(tslot + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int x0 = blockIdx.x * TCX, y0 = blockIdx.y * CF1_TY, z0 = blockIdx.z * CF1_TZ;
   const long long plane = (long long)nx * ny, n = plane * nz;
-  if (tid == 0) tc::mbar_init(mbar, 1);
+  const int tiles_x = nx / TCX, tiles_y = ny / CF1_TY, ntiles = tiles_x * tiles_y * (nz / CF1_TZ);
+  auto origin = [&](int t, int& x0, int& y0, int& z0) {
+    x0 = (t % tiles_x) * TCX;
+    t /= tiles_x;
+    y0 = (t % tiles_y) * CF1_TY;
+    z0 = (t / tiles_y) * CF1_TZ;
+  };
+  // the FP32 input halo of tile t into s_raw, zeros outside: a warp per halo row, lanes along x
+  auto stage_raw = [&](int t) {
+    int x0, y0, z0;
+    origin(t, x0, y0, z0);
+    for (int r = warp; r < CF1_HROWS; r += TC_NT / 32) {
+      const int yr = r % CF1_HY, zr = r / CF1_HY;
+      const int gy = y0 + yr - 1, gz = z0 + zr - 1;
+      const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
+      const long long rbase = (long long)gz * plane + (long long)gy * nx;
+      for (int xr = lane; xr < TC_HX; xr += 32) {
+        const int gx = x0 + xr - 1;
+        const bool inb = rin && gx >= 0 && gx < nx && CLAMP_IN_BOUNDS(rbase + gx, n, 311);
+        cp_async4(&s_raw[r * TC_HX + xr], inb ? &in[rbase + gx] : in, inb);
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+
+  if (tid == 0) {
+    tc::mbar_init(mbar, 1);
+    *abort_flag = 0;
+  }
   if (warp == 0) {
     tc::tmem_alloc(tslot, TMEM_COLS);
     tc::tmem_relinquish();
   }
   for (int e = tid; e < C * 4; e += TC_NT) cp_async16(&s_w[e], &wpk[e], true);
-  // input halo, BF16, zeros outside: a warp per halo row, lanes along x
-  for (int r = warp; r < CF1_HZ * CF1_HY; r += TC_NT / 32) {
-    const int yr = r % CF1_HY, zr = r / CF1_HY;
-    const int gy = y0 + yr - 1, gz = z0 + zr - 1;
-    const bool rin = gy >= 0 && gy < ny && gz >= 0 && gz < nz;
-    const float* src = in + (long long)gz * plane + (long long)gy * nx;
-    for (int xr = lane; xr < TC_HX; xr += 32) {
-      const int gx = x0 + xr - 1;
-      const bool inb = rin && gx >= 0 && gx < nx &&
-                       CLAMP_IN_BOUNDS((long long)gz * plane + (long long)gy * nx + gx, n, 311);
-      const float v = inb ? __ldg(&src[gx]) : 0.f;
-      s_x[r * TC_HX + xr] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-  // im2col: a thread builds whole rows (128-voxel tile row, all four 8-tap groups), so
-  // every tap offset is a compile-time constant
-  for (int e = tid; e < CF1_MT * 128; e += TC_NT) {
-    const int row = e % 128, mt = e / 128;
-    const int ty = mt % CF1_TY, tz = mt / CF1_TY;
-    const uint16_t* xs = s_x + (tz * CF1_HY + ty) * TC_HX + row;
-    unsigned char* arow = s_a + mt * CF1_A_BYTES + (row / 8) * 512 + (row % 8) * 16;
-#pragma unroll
-    for (int g = 0; g < 4; ++g) {
-      uint32_t w4[4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        uint32_t pair = 0;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int k = 8 * g + 2 * j + h;
-          if (k < 27) pair |= (uint32_t)xs[((k / 9) * CF1_HY + (k / 3) % 3) * TC_HX + k % 3] << (16 * h);
-        }
-        w4[j] = pair;
-      }
-      *reinterpret_cast<uint4*>(arow + g * 128) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-    }
-  }
-  tc::fence_proxy_async();
+  if ((int)blockIdx.x < ntiles) stage_raw(blockIdx.x);   // commits the weights with the first halo
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = *tslot;
-  if (tid == 0) {
-    const uint32_t a_s = tc::smem_addr(s_a), w_s = tc::smem_addr(s_w);
+  const uint32_t a_s = tc::smem_addr(s_a), w_s = tc::smem_addr(s_w);
+  uint32_t phase = 0;   // MMA commits completed so far (the mbarrier's phase parity)
+  bool aborted = false;
+
+#pragma unroll 1
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int x0, y0, z0;
+    origin(tile, x0, y0, z0);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");   // this tile's raw halo (and, first, the weights)
+    __syncthreads();
+    for (int e = tid; e < CF1_HROWS * TC_HX; e += TC_NT) s_x[e] = __bfloat16_as_ushort(__float2bfloat16_rn(s_raw[e]));
+    __syncthreads();   // s_raw is free again and s_x complete
+    if (tile + (int)gridDim.x < ntiles) stage_raw(tile + (int)gridDim.x);
+    // im2col: a thread builds whole rows (128-voxel tile row, all four 8-tap groups), so
+    // every tap offset is a compile-time constant.  s_a is free: the previous tile's MMAs
+    // completed before its epilogue.
+    for (int e = tid; e < CF1_MT * 128; e += TC_NT) {
+      const int row = e % 128, mt = e / 128;
+      const int ty = mt % CF1_TY, tz = mt / CF1_TY;
+      const uint16_t* xs = s_x + (tz * CF1_HY + ty) * TC_HX + row;
+      unsigned char* arow = s_a + mt * CF1_A_BYTES + (row / 8) * 512 + (row % 8) * 16;
 #pragma unroll
-    for (int mt = 0; mt < CF1_MT; ++mt)
+      for (int g = 0; g < 4; ++g) {
+        uint32_t w4[4];
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-        tc::mma_bf16(tbase + (uint32_t)(mt * C), tc::make_desc(a_s + mt * CF1_A_BYTES + h * 256, 128, 512),
-                     tc::make_desc(w_s + h * 256, 128, 512), TcKind<TC_BF16>::idesc(128, C), h ? 1u : 0u);
-    tc::mma_commit(mbar);
-  }
-  const bool done = tc::mbar_wait_bounded(mbar, 0u, kWaitLimit);
-  tc::fence_after_sync();
-  if (done) {
+        for (int j = 0; j < 4; ++j) {
+          uint32_t pair = 0;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int k = 8 * g + 2 * j + h;
+            if (k < 27) pair |= (uint32_t)xs[((k / 9) * CF1_HY + (k / 3) % 3) * TC_HX + k % 3] << (16 * h);
+          }
+          w4[j] = pair;
+        }
+        *reinterpret_cast<uint4*>(arow + g * 128) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+      }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int mt = 0; mt < CF1_MT; ++mt)
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+          tc::mma_bf16(tbase + (uint32_t)(mt * C), tc::make_desc(a_s + mt * CF1_A_BYTES + h * 256, 128, 512),
+                       tc::make_desc(w_s + h * 256, 128, 512), TcKind<TC_BF16>::idesc(128, C), h ? 1u : 0u);
+      tc::mma_commit(mbar);
+      if (!tc::mbar_wait_bounded(mbar, phase & 1u, kWaitLimit)) *abort_flag = 1;
+    }
+    __syncthreads();
+    if (*abort_flag) {
+      aborted = true;
+      break;
+    }
+    ++phase;
+    tc::fence_after_sync();
     const int q = warp & 3, hh = warp >> 2;
 #pragma unroll 1
     for (int mt = 0; mt < CF1_MT; ++mt) {
@@ -1131,9 +1178,14 @@ __global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict
           out[(long long)(col / 8) * n + vox] = o;
       }
     }
-  } else if (tid == 0) {
+    // TMEM reads complete before the next tile's MMAs overwrite the accumulators
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");   // a prefetch still in flight after an abort
+  if (aborted && tid == 0) {
     if (err) atomicOr(err, 2);
-    tc::mbar_wait_bounded(mbar, 0u, kWaitLimit);   // give the MMAs a bounded wait before TMEM is freed
+    tc::mbar_wait_bounded(mbar, phase & 1u, kWaitLimit);   // give the MMAs a bounded wait before TMEM is freed
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -1143,10 +1195,18 @@ __global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict
 template <int C>
 static cudaError_t run_first_tc(const float* in, const uint4* wpk, const float* b, uint4* out, int nx, int ny, int nz,
                                 int* err, cudaStream_t st) {
-  const size_t smem = cf1_smem(C);
+  // CTAs per SM: TMEM (512 columns) and shared memory (about 49 KB each) allow at most four;
+  // where TMEM allows fewer, the shared-memory request is raised so that no further CTA
+  // lands on an SM (it would wait for TMEM while other SMs idle)
+  constexpr int per_sm = 512 / pow2_cols(CF1_MT * C) < 4 ? 512 / pow2_cols(CF1_MT * C) : 4;
+  const size_t smem = std::max(cf1_smem(C), per_sm < 4 ? (size_t)(227 * 1024 / (per_sm + 1)) : (size_t)0);
   cudaError_t e = cudaFuncSetAttribute(k_conv_first_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int dev = 0, sms = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return e;
-  dim3 grid(nx / TCX, ny / CF1_TY, nz / CF1_TZ);
+  const long long ntiles = (long long)(nx / TCX) * (ny / CF1_TY) * (nz / CF1_TZ);
+  const int grid = (int)std::min<long long>(ntiles, (long long)sms * per_sm);
   k_conv_first_tc<C><<<grid, TC_NT, smem, st>>>(in, wpk, b, out, nx, ny, nz, err);
   return cudaGetLastError();
 }
@@ -1241,6 +1301,9 @@ __global__ void __launch_bounds__(TC_NT) k_last_taps_tc(const uint4* __restrict_
 }
 
 // out[v] = resid[v] + bias + sum over the 27 taps of P_tap[v + tap] inside the volume.
+// Branch-free: every tap loads at coordinates clamped into the volume (always a valid
+// address) and a tap outside the volume adds 0, so all 27 loads of a thread are issued
+// before the first add.  The sum runs in tap order.
 __global__ void __launch_bounds__(NT) k_last_gather(const float* __restrict__ P, const float* __restrict__ bias,
                                                     const float* __restrict__ resid, float* __restrict__ out, int nx,
                                                     int ny, int nz) {
@@ -1248,25 +1311,27 @@ __global__ void __launch_bounds__(NT) k_last_gather(const float* __restrict__ P,
   const long long v = (long long)blockIdx.x * NT + threadIdx.x;
   if (v >= n) return;
   const int x = (int)(v % nx), y = (int)((v / nx) % ny), z = (int)(v / plane);
-  float acc = __ldg(&bias[0]) + resid[v];
+  float t[27];
+  unsigned inside = 0u;   // bit tap: the tap's voxel lies in the volume
 #pragma unroll
   for (int dz = 0; dz < 3; ++dz) {
-    const int zz = z + dz - 1;
-    if (zz < 0 || zz >= nz) continue;
+    const int zz = z + dz - 1, zc = min(max(zz, 0), nz - 1);
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
-      const int yy = y + dy - 1;
-      if (yy < 0 || yy >= ny) continue;
+      const int yy = y + dy - 1, yc = min(max(yy, 0), ny - 1);
 #pragma unroll
       for (int dx = 0; dx < 3; ++dx) {
-        const int xx = x + dx - 1;
-        if (xx < 0 || xx >= nx) continue;
+        const int xx = x + dx - 1, xc = min(max(xx, 0), nx - 1);
         const int tap = 9 * dz + 3 * dy + dx;
-        const long long pi = (long long)tap * n + (long long)zz * plane + (long long)yy * nx + xx;
-        if (CLAMP_IN_BOUNDS(pi, 27 * n, 331)) acc += __ldg(&P[pi]);
+        const long long pi = (long long)tap * n + (long long)zc * plane + (long long)yc * nx + xc;
+        t[tap] = CLAMP_IN_BOUNDS(pi, 27 * n, 331) ? __ldg(&P[pi]) : 0.f;
+        if (zz == zc && yy == yc && xx == xc) inside |= 1u << tap;
       }
     }
   }
+  float acc = __ldg(&bias[0]) + resid[v];
+#pragma unroll
+  for (int tap = 0; tap < 27; ++tap) acc += (inside >> tap) & 1u ? t[tap] : 0.f;
   out[v] = acc;
 }
 
