@@ -45,6 +45,7 @@ FP32_LANES_PER_SM = 128
 #    prox/Mann pass's 16 B per voxel (the prior agent's r, w and wbar) grows with the looks.
 TRAFFIC = {("cfg3", "prior"): 11.06e9, ("cfg3", "agent", "band-limited"): 19.3e9}
 
+
 def measure_tf32_tflops(dev, seconds: float = 2.0, size: int = 8192) -> dict:
     """TF32 tensor-core rate on this GPU: a cuBLAS FP32 GEMM with TF32 math allowed, the best
     of 5 single calls (burst) and back to back for ``seconds`` (sustained), 2 size^3 FLOP
