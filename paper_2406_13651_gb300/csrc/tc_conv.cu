@@ -1029,13 +1029,16 @@ static cudaError_t run_first(const float* in, const float* w, const float* b, ui
 // measured slower).  Layouts (no-swizzle K-major): element (row, k) of A at
 // (row / 8) * 512 + (k / 8) * 128 + (row % 8) * 16 + (k % 8) * 2, the same for B with co.
 //
-// Persistent: TMEM (256 columns at 48 channels) admits two CTAs per SM, so each CTA takes
-// its TMEM and weights once and walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...;
-// the next tile's FP32 halo is copied (cp.async, 4-byte elements: the halo row starts at
-// x0 - 1) into a raw buffer while the current tile's im2col, MMAs and epilogue run.
+// Persistent: each CTA takes its TMEM and weights once and walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; the next tile's FP32 halo is copied (cp.async, 4-byte
+// elements: the halo row starts at x0 - 1) into a raw buffer while the current tile's
+// im2col, MMAs and epilogue run.  The four tile rows are multiplied and written in two
+// rounds of two, so a CTA holds 2 C TMEM columns (128 at 48 channels) and four CTAs share
+// an SM.
 constexpr int CF1_TY = 2, CF1_TZ = 2, CF1_MT = CF1_TY * CF1_TZ;
 constexpr int CF1_HY = CF1_TY + 2, CF1_HZ = CF1_TZ + 2, CF1_HROWS = CF1_HY * CF1_HZ;
 constexpr int CF1_A_BYTES = 128 * 64;                               // one im2col tile (K = 32)
+constexpr int CF1_HALF = CF1_MT / 2;   // tile rows per MMA round (their accumulators share TMEM)
 __host__ __device__ constexpr size_t cf1_smem(int C) {
   // im2col tiles, weights, BF16 halo, FP32 raw halo, mbarrier + TMEM slot + abort flag
   return 1024 + (size_t)CF1_MT * CF1_A_BYTES + (size_t)C * 64 + 2 * CF1_HROWS * TC_HX + 4 * CF1_HROWS * TC_HX + 64;
@@ -1046,7 +1049,7 @@ __global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict
                                                          const float* __restrict__ bias, uint4* __restrict__ out,
                                                          int nx, int ny, int nz, int* err) {
   static_assert(C % 16 == 0 && C <= 64, "channels");
-  constexpr int TMEM_COLS = pow2_cols(CF1_MT * C);
+  constexpr int TMEM_COLS = pow2_cols(CF1_HALF * C);
   extern __shared__ unsigned char tc_smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* s_a = base;                                            // [MT][8 KB]
@@ -1137,50 +1140,58 @@ __global__ void __launch_bounds__(TC_NT) k_conv_first_tc(const float* __restrict
     tc::fence_proxy_async();
     tc::fence_before_sync();
     __syncthreads();
-    if (tid == 0) {
-      tc::fence_after_sync();
-#pragma unroll
-      for (int mt = 0; mt < CF1_MT; ++mt)
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-          tc::mma_bf16(tbase + (uint32_t)(mt * C), tc::make_desc(a_s + mt * CF1_A_BYTES + h * 256, 128, 512),
-                       tc::make_desc(w_s + h * 256, 128, 512), TcKind<TC_BF16>::idesc(128, C), h ? 1u : 0u);
-      tc::mma_commit(mbar);
-      if (!tc::mbar_wait_bounded(mbar, phase & 1u, kWaitLimit)) *abort_flag = 1;
-    }
-    __syncthreads();
-    if (*abort_flag) {
-      aborted = true;
-      break;
-    }
-    ++phase;
-    tc::fence_after_sync();
-    const int q = warp & 3, hh = warp >> 2;
+    // two rounds of CF1_HALF tile rows: half the TMEM per CTA, so four CTAs share an SM
 #pragma unroll 1
-    for (int mt = 0; mt < CF1_MT; ++mt) {
-      const int gy = y0 + mt % CF1_TY, gz = z0 + mt / CF1_TY, gx = x0 + 32 * q + lane;
-      const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
-      const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(mt * C);
-      constexpr int HALF = C / 2;
+    for (int round = 0; round < CF1_MT / CF1_HALF; ++round) {
+      if (tid == 0) {
+        tc::fence_after_sync();
 #pragma unroll
-      for (int j = 0; j < HALF / 8; ++j) {
-        const int col = hh * HALF + 8 * j;
-        float v[8];
-        tc::tmem_ld_x8(trow + (uint32_t)col, v);
+        for (int m = 0; m < CF1_HALF; ++m) {
+          const int mt = round * CF1_HALF + m;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
-        uint4 o;
-        o.x = pack_bf16x2(v[0], v[1]);
-        o.y = pack_bf16x2(v[2], v[3]);
-        o.z = pack_bf16x2(v[4], v[5]);
-        o.w = pack_bf16x2(v[6], v[7]);
-        if (CLAMP_IN_BOUNDS((long long)(col / 8) * n + vox, (long long)(C / 8) * n, 312))
-          out[(long long)(col / 8) * n + vox] = o;
+          for (int h = 0; h < 2; ++h)
+            tc::mma_bf16(tbase + (uint32_t)(m * C), tc::make_desc(a_s + mt * CF1_A_BYTES + h * 256, 128, 512),
+                         tc::make_desc(w_s + h * 256, 128, 512), TcKind<TC_BF16>::idesc(128, C), h ? 1u : 0u);
+        }
+        tc::mma_commit(mbar);
+        if (!tc::mbar_wait_bounded(mbar, phase & 1u, kWaitLimit)) *abort_flag = 1;
       }
+      __syncthreads();
+      if (*abort_flag) {
+        aborted = true;
+        break;
+      }
+      ++phase;
+      tc::fence_after_sync();
+      const int q = warp & 3, hh = warp >> 2;
+#pragma unroll 1
+      for (int m = 0; m < CF1_HALF; ++m) {
+        const int mt = round * CF1_HALF + m;
+        const int gy = y0 + mt % CF1_TY, gz = z0 + mt / CF1_TY, gx = x0 + 32 * q + lane;
+        const long long vox = (long long)gz * plane + (long long)gy * nx + gx;
+        const uint32_t trow = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(m * C);
+        constexpr int HALF = C / 2;
+#pragma unroll
+        for (int j = 0; j < HALF / 8; ++j) {
+          const int col = hh * HALF + 8 * j;
+          float v[8];
+          tc::tmem_ld_x8(trow + (uint32_t)col, v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = fmaxf(v[i] + __ldg(&bias[col + i]), 0.f);
+          uint4 o;
+          o.x = pack_bf16x2(v[0], v[1]);
+          o.y = pack_bf16x2(v[2], v[3]);
+          o.z = pack_bf16x2(v[4], v[5]);
+          o.w = pack_bf16x2(v[6], v[7]);
+          if (CLAMP_IN_BOUNDS((long long)(col / 8) * n + vox, (long long)(C / 8) * n, 312))
+            out[(long long)(col / 8) * n + vox] = o;
+        }
+      }
+      // TMEM reads complete before the next round's MMAs overwrite the accumulators
+      tc::fence_before_sync();
+      __syncthreads();
     }
-    // TMEM reads complete before the next tile's MMAs overwrite the accumulators
-    tc::fence_before_sync();
-    __syncthreads();
+    if (aborted) break;
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");   // a prefetch still in flight after an abort
   if (aborted && tid == 0) {
@@ -1198,7 +1209,7 @@ static cudaError_t run_first_tc(const float* in, const uint4* wpk, const float* 
   // CTAs per SM: TMEM (512 columns) and shared memory (about 49 KB each) allow at most four;
   // where TMEM allows fewer, the shared-memory request is raised so that no further CTA
   // lands on an SM (it would wait for TMEM while other SMs idle)
-  constexpr int per_sm = 512 / pow2_cols(CF1_MT * C) < 4 ? 512 / pow2_cols(CF1_MT * C) : 4;
+  constexpr int per_sm = 512 / pow2_cols(CF1_HALF * C) < 4 ? 512 / pow2_cols(CF1_HALF * C) : 4;
   const size_t smem = std::max(cf1_smem(C), per_sm < 4 ? (size_t)(227 * 1024 / (per_sm + 1)) : (size_t)0);
   cudaError_t e = cudaFuncSetAttribute(k_conv_first_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int dev = 0, sms = 0;
