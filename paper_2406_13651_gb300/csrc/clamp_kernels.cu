@@ -811,14 +811,14 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
     bool bad = false;
     // two looks ahead in flight: slot a holds look l + 1, slot b look l + 2
     float2 w_n = Wi[vp], r_n = Ri[vp];
-    float4 m_n = MUi[vp], d_n = Di[vp];
+    float4 m_n = __ldcs(&MUi[vp]), d_n = __ldcs(&Di[vp]);
     float2 w_a = w_n, r_a = r_n;
     float4 m_a = m_n, d_a = d_n;
     if (L > 1) {
       w_a = Wi[n2 + vp];
       r_a = Ri[n2 + vp];
-      m_a = MUi[n2 + vp];
-      d_a = Di[n2 + vp];
+      m_a = __ldcs(&MUi[n2 + vp]);
+      d_a = __ldcs(&Di[n2 + vp]);
     }
     float kacc = 0.f;   // sum of K over the looks: non-finite iff some K (so some mu) is
     for (int l = 0; l < L; ++l) {
@@ -833,8 +833,8 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
       if (l + 2 < L && CLAMP_IN_BOUNDS(i + 2 * n2, look_ext, 201)) {
         w_a = Wi[i + 2 * n2];
         r_a = Ri[i + 2 * n2];
-        m_a = MUi[i + 2 * n2];
-        d_a = Di[i + 2 * n2];
+        m_a = __ldcs(&MUi[i + 2 * n2]);
+        d_a = __ldcs(&Di[i + 2 * n2]);
       }
       if (l + kPassCPrefetch < L) {   // look l + kPassCPrefetch into L2: no registers held
         const long long ip = i + kPassCPrefetch * n2;
@@ -851,7 +851,7 @@ __global__ void __launch_bounds__(NT) k_pass_c_pair(Geom g, PassC c) {
         m = make_float4(fmaf(gm, dd.x, m.x), fmaf(gm, dd.y, m.y), fmaf(gm, dd.z, m.z), fmaf(gm, dd.w, m.w));
       }
       const bool in_look = CLAMP_IN_BOUNDS(i, look_ext, 202);
-      if (in_look) MUo[i] = m;
+      if (in_look) __stcs(&MUo[i], m);   // mu and d are not read again here: evict first
       const float c0 = c.nv * rp.x * __frcp_rn(fmaf(c.alpha, rp.x, c.nv));
       const float c1 = c.nv * rp.y * __frcp_rn(fmaf(c.alpha, rp.y, c.nv));
       const float K0 = c0 + fmaf(m.x, m.x, m.y * m.y), K1 = c1 + fmaf(m.z, m.z, m.w * m.w);
