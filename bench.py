@@ -41,9 +41,9 @@ FP32_LANES_PER_SM = 128
 #    sums, gather) captured at 256x256x64 (5.53 GB) and doubled: every kernel streams its
 #    volume once, so the traffic grows with the voxel count.
 #  * cfg3 agent: one band-limited iteration's passes, line search and prox/Mann pass
-#    captured at 256x256x128 with L = 4 looks (2.53 GB) and scaled to L = 32: all but the
+#    captured at 256x256x128 with L = 4 looks (2.52 GB) and scaled to L = 32: all but the
 #    prox/Mann pass's 16 B per voxel (the prior agent's r, w and wbar) grows with the looks.
-TRAFFIC = {("cfg3", "prior"): 11.06e9, ("cfg3", "agent", "band-limited"): 19.3e9}
+TRAFFIC = {("cfg3", "prior"): 11.06e9, ("cfg3", "agent", "band-limited"): 19.26e9}
 
 
 def measure_tf32_tflops(dev, seconds: float = 2.0, size: int = 8192) -> dict:
