@@ -295,15 +295,15 @@ clamp_status clamp_reconstruct_host(const clamp_params* p, const float* y_host,
 void clamp_release_cache(void);
 
 /* Host staging memory for clamp_reconstruct_host: `bytes` of zeroed host memory backed by
- * transparent huge pages where the kernel offers them (mmap + madvise(MADV_HUGEPAGE),
- * rounded up to the huge-page size and touched before use) and page-locked for the
+ * transparent huge pages where the kernel offers them (an anonymous mapping started on a
+ * huge-page boundary, madvise(MADV_HUGEPAGE), touched before use) and page-locked for the
  * current CUDA device (cudaHostRegister).  Host-to-device copies from it need few I/O
  * translations; on GB300 hosts a 2 GB upload from it took 10.2 ms every time, where the
  * same upload from base-page pinned memory sometimes took 50-100 ms.  *out receives the
- * host pointer (2 MiB aligned at least); free it with clamp_host_free.  CLAMP_EINVAL for
- * bytes == 0 or out == NULL, CLAMP_ENOMEM if the mapping fails, CLAMP_ECUDA if the
- * registration fails (nothing is kept then).  Synchronous; not part of the paper's
- * method. */
+ * host pointer (huge-page aligned, 2 MiB at least), or NULL on failure; free it with
+ * clamp_host_free.  CLAMP_EINVAL for bytes == 0 or out == NULL, CLAMP_ENOMEM if the
+ * mapping fails, CLAMP_ECUDA if the registration fails (nothing is kept then).
+ * Synchronous; not part of the paper's method. */
 clamp_status clamp_host_alloc(size_t bytes, void** out);
 /* Unregisters and unmaps memory from clamp_host_alloc; NULL is ignored, and so is a
  * pointer the allocator did not return. */

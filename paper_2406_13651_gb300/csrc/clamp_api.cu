@@ -1115,8 +1115,8 @@ size_t huge_page_bytes() {
 }  // namespace
 
 extern "C" clamp_status clamp_host_alloc(size_t bytes, void** out) {
+  if (out) *out = nullptr;
   if (!out || bytes == 0) return api_fail(CLAMP_EINVAL, "clamp_host_alloc: bytes must be > 0 and out non-NULL");
-  *out = nullptr;
   const size_t page = (size_t)sysconf(_SC_PAGESIZE);
   const size_t hp = huge_page_bytes();
   const size_t len = (bytes + page - 1) / page * page;

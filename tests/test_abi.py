@@ -101,3 +101,32 @@ def test_l21_weight_validation(lib):
     for lam in (-1.0, float("nan"), float("inf")):
         assert lib.clamp_denoiser_create_l21(lam, ctypes.byref(h)) == 1
     assert lib.clamp_denoiser_create_l21(1.0, None) == 1
+
+
+def test_product_build_reports_no_bounds_record(lib):
+    """The product library is not the bounds-checking build: clamp_bounds_check returns 0 and
+    reports no site without touching the device."""
+    site = ctypes.c_uint32(123)
+    assert lib.clamp_bounds_check(1, ctypes.byref(site)) == 0
+    assert site.value == 0
+    assert lib.clamp_bounds_check(0, None) < 0   # NULL site: CLAMP_EINVAL, negated
+
+
+def test_host_alloc_rejects_bad_arguments(lib):
+    out = ctypes.c_void_p(7)
+    assert lib.clamp_host_alloc(0, ctypes.byref(out)) == 1   # CLAMP_EINVAL before any mapping
+    assert out.value is None
+    assert lib.clamp_host_alloc(64, None) == 1
+    lib.clamp_host_free(None)
+    lib.clamp_host_free(ctypes.c_void_p(4096))                # not from the allocator: ignored
+
+
+def test_checked_build_exports_every_declared_symbol():
+    """The bounds-checking variant (CLAMP_BOUNDS_CHECK) compiles from the same sources into its
+    own library and exports the same ABI."""
+    from paper_2406_13651_gb300 import build
+    path = build.build(checked=True)
+    assert path.endswith("libclamp_checked.so")
+    chk = ctypes.CDLL(path)
+    for nm in _declared():
+        assert hasattr(chk, nm), nm
